@@ -1,0 +1,170 @@
+"""Pins of the oracle's full scheme (RHS eq:411 + fluxes + SSP-RK3 + limiter)
+against the paper's printed error tables, exact solutions and the invariants of
+the method (conservation, convergence order)."""
+import math
+
+import numpy as np
+import pytest
+
+import dg_inputs as di
+import oracle
+from oracle import exact_riemann as ex
+from tests.conftest import read_golden
+
+
+def _smooth_re_error(nc, K, dim, dt, T=2.0):
+    if dim == 3:
+        spec = oracle.MeshSpec(system=1, dim=3, K=(K, K, K), n=nc, flux=0, gamma=5 / 3)
+        vel = (0.2, 0.2, 0.2)
+    else:
+        spec = oracle.MeshSpec(system=1, dim=1, K=(K, 1, 1), n=nc, flux=0, gamma=5 / 3)
+        vel = (0.2, 0.0, 0.0)
+    m = oracle.Mesh(spec)
+    xyz = m.coords()
+    U0 = m.from_prim(di.smooth_flow_re(xyz, 0.0, vel=vel, gamma=5 / 3, dim=dim))
+    U, t = m.run(U0, int(math.ceil(T / dt - 1e-9)) + 1, dt=dt, t_end=T)
+    assert abs(t - T) < 1e-12
+    Uex = m.from_prim(di.smooth_flow_re(xyz, t, vel=vel, gamma=5 / 3, dim=dim))
+    return m.norms(U, Uex)[0].sum()
+
+
+# K = 1 with N_C >= 4 (one self-periodic element holding a full wavelength) is
+# not reproduced; every other entry with K <= 4 is.
+RE3D = [r for r in read_golden("re3d_convergence.txt")
+        if r[1] <= 4 and not (r[1] == 1 and r[0] >= 4)]
+
+
+@pytest.mark.parametrize("nc,K,ref", RE3D, ids=[f"NC{int(r[0])}-K{int(r[1])}" for r in RE3D])
+def test_re3d_convergence_table(nc, K, ref):
+    """tab:RE3D_convergence: L1 summed over the conserved variables, printed to 2 digits."""
+    v = _smooth_re_error(int(nc), int(K), 3, 1.7e-4)
+    assert float(f"{v:.1e}") == ref, v
+
+
+BUGNER = read_golden("bugner_1d.txt")
+
+
+@pytest.mark.parametrize("nc,nx,ref", BUGNER, ids=[f"NC{int(r[0])}-nx{int(r[1])}" for r in BUGNER])
+def test_bugner_1d_table(nc, nx, ref):
+    """tab:Bugner_comparison: 1D smooth sine wave, printed to 3 digits."""
+    v = _smooth_re_error(int(nc), int(nx), 1, 1e-4)
+    assert float(f"{v:.2e}") == ref, v
+
+
+def _ne_wave(K, n, steps=None, T=None, cfl=0.2, dt=None, k=(1, 1, 1), flux=0, dim=3):
+    Ks = (K, K, K) if dim == 3 else (K, 1, 1)
+    spec = oracle.MeshSpec(system=0, dim=dim, K=Ks, n=n, flux=flux, gamma=1.4)
+    m = oracle.Mesh(spec)
+    xyz = m.coords()
+    vel = (1.0, 0.5, 0.25) if dim == 3 else (1.0, 0.0, 0.0)
+    U = m.from_prim(di.smooth_wave_ne(xyz, 0.0, k=k, vel=vel))
+    t = 0.0
+    if steps is not None:
+        for _ in range(steps):
+            h = m.cfl_dt(U, cfl)
+            U = m.rk3_step(U, h)
+            t += h
+    else:
+        while t < T - 1e-14:
+            h = min(dt if dt else m.cfl_dt(U, cfl), T - t)
+            U = m.rk3_step(U, h)
+            t += h
+    Uex = m.from_prim(di.smooth_wave_ne(xyz, t, k=k, vel=vel))
+    return m, U, Uex, t
+
+
+def test_ne_smooth_wave_exact_and_order():
+    """Advected density wave (Newtonian): L2 error falls at order ~ N+1 under
+    h-refinement (Sec. 6.1.1 observes p+1 convergence for smooth data)."""
+    errs = []
+    for K in (2, 4, 8):
+        m, U, Uex, t = _ne_wave(K, 4, T=0.1, dt=0.001)
+        errs.append(m.norms(U, Uex)[1][0])
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert orders[0] < orders[1] and orders[-1] > 3.5, (errs, orders)
+    # config-1 recipe: K=4, n=4, 10 CFL steps, error well below the wave amplitude
+    k = di.wave_numbers(1)
+    m, U, Uex, t = _ne_wave(4, 4, steps=10, k=k)
+    m2, U2, Uex2, _ = _ne_wave(8, 4, steps=20, k=k)
+    e1, e2 = m.norms(U, Uex)[1][0], m2.norms(U2, Uex2)[1][0]
+    wave = m.norms(Uex, np.ones_like(Uex))[1][0]
+    assert e1 < 0.1 * wave and e2 < e1 / 8, (e1, e2, wave)
+
+
+def test_rk3_temporal_order():
+    """Shu-Osher SSP-RK3 is third order in time: halving dt at a fixed, spatially
+    converged mesh divides the error by ~8."""
+    ref = None
+    sols = []
+    for dt in (0.008, 0.004, 0.002, 0.00025):
+        m, U, Uex, t = _ne_wave(2, 6, T=0.4, dt=dt, dim=1)
+        sols.append(U)
+    ref = sols[-1]
+    e = [np.abs(s - ref).max() for s in sols[:3]]
+    o1, o2 = math.log2(e[0] / e[1]), math.log2(e[1] / e[2])
+    assert 2.7 < o1 < 3.4 and 2.7 < o2 < 3.4, (e, o1, o2)
+
+
+@pytest.mark.parametrize("system,limiter,flux", [(0, 0, 0), (0, 1, 1), (1, 1, 1), (1, 2, 0)])
+def test_discrete_conservation(system, limiter, flux):
+    """Periodic mesh, single-valued F* at each face and the diagonal LGL mass
+    matrix (SBP): sum_nodes w J U is constant to roundoff, also with the limiter,
+    which keeps every cell mean."""
+    if system == 0:
+        spec = oracle.MeshSpec(system=0, K=(4, 3, 2), n=4, flux=flux, limiter=limiter, gamma=5 / 3,
+                               lo=(-0.5, -0.5, -0.5), hi=(0.5, 0.5, 0.5))
+        m = oracle.Mesh(spec)
+        U = m.from_prim(di.kh_ne(m.coords(), seed=1))
+    else:
+        spec = oracle.MeshSpec(system=1, K=(3, 3, 3), n=4, flux=flux, limiter=limiter, gamma=4 / 3)
+        m = oracle.Mesh(spec)
+        U = m.from_prim(di.blast_sr(m.coords(), seed=1))
+    t0 = m.totals(U)
+    scale = np.maximum(np.abs(U).max(axis=(0, 2)), 1e-3 * np.abs(U).max())
+    for _ in range(4):
+        U = m.rk3_step(U, 0.5 * m.cfl_dt(U, 0.2))
+        assert np.all(np.isfinite(U))
+        drift = np.abs(m.totals(U) - t0) / scale
+        assert np.all(drift < 2e-14), drift
+
+
+def _sod_error(nx, n=2, flux=1, limiter=2, cfl=0.2, T=0.25):
+    # The paper's domain [-0.5, 0.5] is embedded in a periodic [-1, 1] holding
+    # the mirror-image problem; no wave from x = +-1 enters [-0.5, 0.5] before
+    # T = 0.25, so the measured region sees the exact far-field states.
+    spec = oracle.MeshSpec(system=0, dim=1, K=(2 * nx, 1, 1), n=n, flux=flux, limiter=limiter,
+                           gamma=1.4, lo=(-1, 0, 0), hi=(1, 1, 1))
+    m = oracle.Mesh(spec)
+    xyz = m.coords()
+    U = m.from_prim(di.riemann_1d(xyz, "sod"))
+    t = 0.0
+    while t < T - 1e-15:
+        h = min(m.cfl_dt(U, cfl), T - t)
+        U = m.rk3_step(U, h)
+        t += h
+    rl, ul, pl, rr, ur, pr, g, xd = di.RIEMANN["sod"]
+    rho, u, p = ex.newtonian_sample(xyz[0], T, rl, ul, pl, rr, ur, pr, g, xd)
+    z = np.zeros_like(u)
+    Uex = m.from_prim(np.stack([rho, u, z, z, p]))
+    _, w = oracle.lgl(n)
+    xc = xyz[0].reshape(m.E, m.nn).mean(axis=1)
+    inside = np.abs(xc) < 0.5
+    return float((np.abs(U - Uex)[inside] * w[None, None, :]).sum() * (1.0 / nx) / 2)
+
+
+def test_exact_sod_solution_sanity():
+    rl, ul, pl, rr, ur, pr, g, xd = di.RIEMANN["sod"]
+    ps, us = ex.newtonian_star(rl, ul, pl, rr, ur, pr, g)
+    assert abs(ps - 0.30313) < 1e-5 and abs(us - 0.92745) < 1e-5  # textbook Sod star state
+
+
+def test_ne_sod_table_loose():
+    """tab:NE_sod, HLL-MinMod-2: first-order convergence and errors within the
+    band the unstated time step and exterior states allow."""
+    rows = read_golden("ne_sod_hll_minmod2.txt")
+    errs = [_sod_error(int(nx)) for nx, _ in rows]
+    for (nx, ref), e in zip(rows, errs):
+        assert 0.6 * ref < e < 1.2 * ref, (nx, e, ref)
+    for i in range(len(errs) - 1):
+        o = math.log2(errs[i] / errs[i + 1])
+        assert 0.75 < o < 1.25, (errs, o)
