@@ -1,0 +1,314 @@
+#!/usr/bin/env python
+"""DG-RK3 throughput (dof-updates/s) of the nodal DG hot path on GB300.
+
+Workload: 3D special-relativistic blast on a periodic unit cube, 16^3 affine
+elements, 5 LGL nodes per axis (512,000 nodes x 5 conserved variables),
+gamma = 4/3, rho = 10, p = 13.33 for r < 0.3 else rho = 1, p = 1e-6, v = 0,
+1 % seeded density noise; HLL flux, MinModN limiter and SR fix after every
+stage, con2prim at every node, CFL 0.2 (dt computed on the device each step).
+A step is one full SSP-RK3 step (three RHS evaluations, limiter, fix).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  N > 1 (launched by torch.distributed.run) runs
+N independent replicas, one per GPU; the path has no data exchange to shard.
+The state (20.5 MB) is smaller than L2, so a 256 MiB buffer is written between
+timed steps (outside the per-step event pairs).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(system=1, K=(16, 16, 16), n=5, flux=1, limiter=1, gamma=4.0 / 3.0, cfl=0.2, seed=1)
+METRIC = "DG-RK3 dof-updates/s on 1 GB300: plain FP64 vs mixed+learned at equal L2 error"
+UNIT = "dof-updates/s"
+
+
+def _config(extra=None):
+    w = WORKLOAD
+    cfg = {"workload": "SR blast, 16^3 elements, 5 LGL nodes/axis, HLL, MinModN, con2prim per node, CFL 0.2",
+           "system": "special-relativistic hydro", "elements": list(w["K"]), "lgl_nodes_per_axis": w["n"],
+           "nodes": int(np.prod(w["K"]) * w["n"] ** 3), "vars": 5, "flux": "HLL", "limiter": "MinModN",
+           "cfl": w["cfl"], "seed": w["seed"], "l2_between_steps": "flushed (256 MiB write)"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"dg_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _init_state(pkg, mesh, torch):
+    import dg_inputs as di
+    xyz = mesh.coords().cpu().numpy()
+    prim = di.blast_sr(xyz, seed=WORKLOAD["seed"])
+    return mesh.from_prim(torch.from_numpy(prim).cuda())
+
+
+def _algorithmic(nodes):
+    """Algorithmic HBM bytes of one fused stage launch, averaged over the 3 stages:
+    stage 1 reads U^n and writes U^1 (80 B/node); stages 2, 3 read U_s and U^n and
+    write U_{s+1} (120 B/node)."""
+    return nodes * (80 + 120 + 120) / 3.0
+
+
+def run_ours(args):
+    import torch
+    import paper_1609_00098_gb300 as pkg
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    w = WORKLOAD
+    mesh = pkg.Mesh(system=w["system"], K=w["K"], n=w["n"], flux=w["flux"], limiter=w["limiter"],
+                    gamma=w["gamma"])
+    nodes = mesh.E * mesh.nn
+    U0 = _init_state(pkg, mesh, torch)
+    U = U0.clone()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        mesh.rk3_step(U, cfl=w["cfl"])
+    torch.cuda.synchronize()
+    if mesh.sync_status() != 0:
+        raise RuntimeError("warm-up steps reported a device error")
+
+    # timed region: per-step event pairs, L2 flushed between steps outside them
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    pkg.abi.dg_profile_enable(mesh.h, True)
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        starts[k].record(stream)
+        mesh.rk3_step(U, cfl=w["cfl"])
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    prof = pkg.abi.dg_profile_read(mesh.h)
+    pkg.abi.dg_profile_enable(mesh.h, False)
+    status = mesh.sync_status()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = float(sum(step_ms))
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = ws * nodes * 5 * args.steps / (total_ms / 1e3)
+
+    # end to end through the C ABI with host buffers: H2D of the step's input state
+    # from pinned memory, the step, D2H of the resulting state, every step
+    host_in = U0.cpu().pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    Ud = torch.empty_like(U0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for k in range(args.steps):
+        Ud.copy_(host_in, non_blocking=True)
+        mesh.rk3_step(Ud, cfl=w["cfl"])
+        host_out.copy_(Ud, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e = ws * nodes * 5 * args.steps / (e2e_ms / 1e3)
+    state_bytes = nodes * 5 * 8
+
+    # dominant kernel roofline (HBM): algorithmic bytes per launch / average launch time
+    dom = max(prof, key=lambda c: prof[c][0])
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    st_ms, st_n = prof["stage"]
+    stage_avg_s = (st_ms / st_n) / 1e3 if st_n else float("nan")
+    achieved = _algorithmic(nodes) / stage_avg_s / 1e9
+    launches = int(sum(c for _, c in prof.values())) + 0
+    kernels = {c: {"ms_total": round(v[0], 4), "launches": int(v[1]),
+                   "share": round(v[0] / max(1e-12, sum(x[0] for x in prof.values())), 4)} for c, v in prof.items()
+               if v[1]}
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic (seeded blast initial data)",
+        "config": _config({"precision": "fp64", "parallelism": "replicas" if ws > 1 else "single GPU"}),
+        "variant": "plain FP64",
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes},
+        "gpu_launches": launches,
+        "kernels": kernels,
+        "dominant_kernel": dom,
+        "roofline": {"kernel": "k_stage_fp64 (fused RHS + SSP-RK3 stage)", "bound": "hbm", "achieved": achieved,
+                     "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks else "fallback"},
+        "clocks": clk,
+        "device_status": status,
+        "wall_s_timed": wall,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(seconds=args.cpu_seconds)
+    mesh.close()
+    if dist:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def _oracle_mesh():
+    import oracle
+    w = WORKLOAD
+    spec = oracle.MeshSpec(system=w["system"], K=w["K"], n=w["n"], flux=w["flux"], limiter=w["limiter"],
+                           gamma=w["gamma"])
+    return oracle.Mesh(spec)
+
+
+def cpu_baseline(seconds: float = 15.0):
+    """The FP64 oracle, as it stands, on the host cores: as many steps of the same
+    workload as fit in about `seconds` (at least one)."""
+    import dg_inputs as di
+    om = _oracle_mesh()
+    U = om.from_prim(di.blast_sr(om.coords(), seed=WORKLOAD["seed"]))
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        h = om.cfl_dt(U, WORKLOAD["cfl"])
+        U = om.rk3_step(U, h)
+        steps += 1
+        if time.perf_counter() - t0 > seconds:
+            break
+    el = time.perf_counter() - t0
+    nodes = om.E * om.nn
+    return {"value": nodes * 5 * steps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{steps} CFL steps of the full workload from its initial state ({el:.1f} s)"}
+
+
+def run_reference(args):
+    """The oracle timed as the reference arm: each step is one full step of the
+    workload on the host cores."""
+    ws, rank, local = _dist()
+    if rank != 0:
+        return
+    import dg_inputs as di
+    om = _oracle_mesh()
+    U = om.from_prim(di.blast_sr(om.coords(), seed=WORKLOAD["seed"]))
+    for _ in range(args.warmup):
+        U = om.rk3_step(U, om.cfl_dt(U, WORKLOAD["cfl"]))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        U = om.rk3_step(U, om.cfl_dt(U, WORKLOAD["cfl"]))
+    el = time.perf_counter() - t0
+    nodes = om.E * om.nn
+    value = nodes * 5 * args.steps / el
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded blast initial data)",
+           "config": _config({"precision": "fp64", "implementation": "FP64 CPU oracle (C, OpenMP)"}),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": f"{args.steps} full steps after {args.warmup} warm-up steps"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

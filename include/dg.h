@@ -1,0 +1,148 @@
+/*
+ * dg.h -- C ABI of libdg, a single-GPU (sm_103a) implementation of the per-step
+ * hot path of the nodal discontinuous Galerkin method of Kidder et al.,
+ * "SpECTRE: A task-based discontinuous Galerkin code for relativistic
+ * astrophysics", arXiv:1609.00098:
+ *   primitive recovery (Sec. 2.1.1 closed form; Sec. 2.1.2 Newton con2prim),
+ *   fluxes, tensor-product LGL differentiation and lifted face fluxes (Sec. 3.1,
+ *   eq:411), LLF / HLL numerical fluxes (Sec. 3.2, eq:LLF, eq:HLL),
+ *   SSP-RK3 (Sec. 3.4), the minmod-type troubled-cell limiter (Sec. 3.3.1-3.3.2)
+ *   and the SR conserved-variable fix (Sec. 2.1.4), on periodic boxes of affine
+ *   hexahedral elements (eq:AffineMap).
+ *
+ * Conventions shared by every call:
+ *  - Every array argument is a DEVICE pointer on the current CUDA device unless
+ *    the comment says "host".  The caller owns all arrays passed in.
+ *  - State layout: U[e][v][k][j][i] (FP64), element-major, i fastest;
+ *    e = ex + K0*(ey + K1*ez); v = 0..4 = (rho, S_x, S_y, S_z, E) for Newtonian
+ *    Euler and (D, S_x, S_y, S_z, tau) for SR hydro.  dg_state_size() doubles.
+ *  - Node order ("node index") is g = e*n^3 + (i + n*(j + n*k)).
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls enqueue
+ *    work asynchronously; argument errors are returned synchronously.
+ *  - Kernel-side failures (con2prim without a root, unphysical states) set a
+ *    sticky per-mesh device status word; dg_sync_status() reads and clears it.
+ *    No kernel traps, asserts or spins without bound.
+ *  - On any error the thread-local message of dg_last_error() is set.
+ */
+#ifndef LIBDG_DG_H
+#define LIBDG_DG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DG_OK = 0,
+    DG_ERR_ARG = 1,          /* invalid argument (returned synchronously) */
+    DG_ERR_CUDA = 2,         /* a CUDA call failed */
+    DG_ERR_C2P = 3,          /* con2prim did not converge at some node */
+    DG_ERR_UNPHYSICAL = 4,   /* conserved state with no physical primitive state */
+    DG_ERR_TIMEOUT = 5,      /* a bounded device wait ran out */
+    DG_ERR_NOMEM = 6         /* device allocation failed */
+} dg_status;
+
+enum { DG_SYSTEM_NEWTONIAN = 0, DG_SYSTEM_SR = 1 };
+enum { DG_FLUX_LLF = 0, DG_FLUX_HLL = 1 };
+enum { DG_LIMITER_NONE = 0, DG_LIMITER_MINMODN = 1, DG_LIMITER_MINMOD = 2 };
+enum { DG_PRECISION_FP64 = 0, DG_PRECISION_MIXED = 1 };
+
+typedef struct {
+    int system;      /* DG_SYSTEM_*: Newtonian Euler (Sec. 2.1.1) or flat-space SR hydro (Sec. 2.1.2) */
+    int K[3];        /* elements per axis, >= 1 */
+    int n;           /* LGL nodes per axis, 2..8 (degree N = n-1) */
+    int flux;        /* DG_FLUX_*: eq:LLF or eq:HLL with Davis speeds */
+    int limiter;     /* DG_LIMITER_*: none, generalized minmodB detector + limiter (Sec. 3.3.2), plain minmod (Sec. 3.3.1) */
+    int precision;   /* DG_PRECISION_* */
+    double gamma;    /* ideal-gas adiabatic index, > 1 */
+    double lo[3];    /* periodic box [lo, hi) */
+    double hi[3];
+    double tvb_M;    /* minmodB constant M (eq:MinModB), >= 0 */
+    double beta;     /* slope-limiter beta (2 minmod, 1 MUSCL), > 0 */
+    double d_atm;    /* SR fix: floor on D */
+    double tau_atm;  /* SR fix: floor on tau as a fraction of D */
+} dg_mesh_desc;
+
+typedef struct dg_mesh dg_mesh;
+
+/* Create a mesh on the current device.  Allocates the library's scratch (two
+ * state copies, a primitive buffer, limiter summaries, flags) with cudaMalloc.
+ * Returns DG_ERR_ARG for an invalid descriptor, DG_ERR_NOMEM if allocation fails. */
+dg_status dg_mesh_create(const dg_mesh_desc *desc, dg_mesh **out);
+/* Free a mesh and its scratch (synchronises the device first).  NULL is ignored. */
+void dg_mesh_destroy(dg_mesh *mesh);
+/* Number of doubles in one state vector: E * 5 * n^3. */
+long long dg_state_size(const dg_mesh *mesh);
+/* Number of nodes E * n^3. */
+long long dg_num_nodes(const dg_mesh *mesh);
+
+/* Physical coordinates of every node, eq:AffineMap: xyz[a*N + g], a = 0..2,
+ * N = dg_num_nodes(), g the node index. */
+dg_status dg_node_coords(const dg_mesh *mesh, double *xyz, void *stream);
+
+/* Primitive -> conserved (Sec. 2.1.1, 2.1.2): prim[v*N + g] with rows
+ * (rho, vx, vy, vz, p) in node order, U in state layout.  Separate arrays. */
+dg_status dg_prim2con(const dg_mesh *mesh, const double *prim, double *U, void *stream);
+
+/* Primitive recovery for the whole mesh: P[e][c][node], c = (vx, vy, vz, p).
+ * SR uses the safeguarded Newton con2prim of dg_con2prim. */
+dg_status dg_primitives(dg_mesh *mesh, const double *U, double *P, void *stream);
+
+/* Semi-discrete right-hand side dU/dt of eq:411 (volume term by tensor-product
+ * differentiation, eq:405; surface term with the numerical flux lifted into the
+ * boundary nodes).  U and dUdt must not alias. */
+dg_status dg_rhs(dg_mesh *mesh, const double *U, double *dUdt, void *stream);
+
+/* CFL step of Sec. 3.4: *dt = cfl * dx_min / lambda_max, dx_min the smallest
+ * node gap min_a (dx_a/2)(xbar_1 - xbar_0), lambda_max the largest |wave speed|
+ * over nodes and axes (an exact, order-independent maximum).  dt: device, 1 double. */
+dg_status dg_compute_dt(dg_mesh *mesh, const double *U, double cfl, double *dt, void *stream);
+
+/* One SSP-RK3 step (Shu-Osher form) in place on U, with the limiter and then the
+ * SR fix after every stage (Sec. 3.3, 3.4):
+ *   U1 = Un + dt L(Un); U2 = 3/4 Un + 1/4 (U1 + dt L(U1)); Un+1 = 1/3 Un + 2/3 (U2 + dt L(U2)).
+ * cfl > 0: dt is the CFL step of Un, computed on the device inside the step;
+ * cfl <= 0: the host value dt is used.  dt_used (device, 1 double, may be NULL)
+ * receives the step taken.  troubled (device, E bytes, may be NULL) receives the
+ * bitmask of limited variables of the last stage. */
+dg_status dg_rk3_step(dg_mesh *mesh, double *U, double dt, double cfl, double *dt_used,
+                      unsigned char *troubled, void *stream);
+
+/* Limiter alone, in place (Sec. 3.3.1, 3.3.2); troubled as in dg_rk3_step. */
+dg_status dg_limit(dg_mesh *mesh, double *U, unsigned char *troubled, void *stream);
+/* SR conserved-variable fix alone, in place (Sec. 2.1.4); no-op for Newtonian meshes. */
+dg_status dg_fix(dg_mesh *mesh, double *U, void *stream);
+/* Limiter summaries S[e][v][10] = (cell mean, face means lo/hi for x, y, z,
+ * Legendre P1 coefficients along x, y, z) of U. */
+dg_status dg_limiter_summaries(dg_mesh *mesh, const double *U, double *S, void *stream);
+
+/* Standalone SR con2prim (Sec. 2.1.2) of `count` nodes, FP64.
+ * cons: 5 rows of `count` (D, S_x, S_y, S_z, tau); prim: 5 rows (rho, vx, vy, vz, p).
+ * p_guess (may be NULL -> standard guess (gamma-1) tau, clamped into the bracket),
+ * iters and status (may be NULL) have `count` entries.  status: 0 ok,
+ * 1 unphysical input, 2 no convergence in 200 iterations. */
+dg_status dg_con2prim(long long count, double gamma, const double *cons, double *prim,
+                      const double *p_guess, int *iters, int *status, void *stream);
+
+/* Synchronise `stream`, then read and clear the mesh's device status word.
+ * Returns DG_OK, DG_ERR_C2P or DG_ERR_UNPHYSICAL (first set), or DG_ERR_CUDA. */
+dg_status dg_sync_status(dg_mesh *mesh, void *stream);
+
+/* Per-kernel timing.  When enabled, the library records a CUDA event pair on the
+ * call's stream around every kernel it launches for `mesh` and accumulates the
+ * elapsed time per kernel class:
+ *   0 primitive recovery (incl. SR con2prim and the fused fix), 1 fused RHS +
+ *   RK stage, 2 limiter, 3 SR fix pass, 4 CFL step, 5 other.
+ * dg_profile_read synchronises the events, writes ms[c] (total milliseconds) and
+ * launches[c] for c < min(nclass, 6) (host arrays) and resets the counters. */
+dg_status dg_profile_enable(dg_mesh *mesh, int on);
+dg_status dg_profile_read(dg_mesh *mesh, double *ms, long long *launches, int nclass);
+
+/* Thread-local message of the last failing call (never NULL). */
+const char *dg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,546 @@
+// dg_api.cu -- the C ABI of libdg (declared in include/dg.h): argument checks,
+// scratch ownership, LGL tables and the launch sequence of each call.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "dg_internal.h"
+#include "dg_physics.cuh"
+
+namespace {
+
+thread_local char g_err[512] = "no error";
+
+dg_status fail(dg_status st, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+#define DG_CUDA(expr)                                                                          \
+    do {                                                                                       \
+        cudaError_t e_ = (expr);                                                               \
+        if (e_ != cudaSuccess) return fail(DG_ERR_CUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+    } while (0)
+
+// Per-kernel event log of dg_profile_enable.
+struct ProfRec {
+    int cls;
+    cudaEvent_t a, b;
+};
+struct ProfLog {
+    std::vector<cudaEvent_t> pool;
+    std::vector<ProfRec> recs;
+};
+
+cudaEvent_t prof_event(ProfLog *L)
+{
+    if (!L->pool.empty()) {
+        cudaEvent_t e = L->pool.back();
+        L->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Launch `expr` (a cudaError_t expression) with optional event timing of class `cls`.
+#define DG_LAUNCH(m, s, cls, expr)                                             \
+    do {                                                                       \
+        ProfLog *L_ = (m)->prof_on ? (ProfLog *)(m)->prof : nullptr;           \
+        cudaEvent_t a_ = nullptr;                                              \
+        if (L_) {                                                              \
+            a_ = prof_event(L_);                                               \
+            cudaEventRecord(a_, (s));                                          \
+        }                                                                      \
+        DG_CUDA(expr);                                                         \
+        if (L_) {                                                              \
+            cudaEvent_t b_ = prof_event(L_);                                   \
+            cudaEventRecord(b_, (s));                                          \
+            L_->recs.push_back(ProfRec{(cls), a_, b_});                        \
+        }                                                                      \
+    } while (0)
+
+enum { PROF_PRIM = 0, PROF_STAGE = 1, PROF_LIMIT = 2, PROF_FIX = 3, PROF_DT = 4, PROF_OTHER = 5 };
+
+}  // namespace
+
+namespace dg {
+
+// Legendre P_N(x) and P_{N-1}(x) in long double by the three-term recurrence.
+static void legendre_pair(int N, long double x, long double &PN, long double &PNm1)
+{
+    long double p0 = 1.0L, p1 = x;
+    if (N == 0) { PN = 1.0L; PNm1 = 0.0L; return; }
+    for (int k = 2; k <= N; ++k) {
+        const long double p2 = ((2 * k - 1) * x * p1 - (k - 1) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+    }
+    PN = p1;
+    PNm1 = p0;
+}
+
+// LGL nodes: +-1 and the zeros of P_N', found by Newton in long double with
+// P_N' = N (x P_N - P_{N-1})/(x^2 - 1) and P_N'' from Legendre's equation.
+// Weights w_j = 2/(N(N+1) P_N(x_j)^2).  Differentiation matrix in the LGL
+// closed form D_il = P_N(x_i)/(P_N(x_l)(x_i - x_l)) (i != l), D_00 = -N(N+1)/4,
+// D_NN = N(N+1)/4, other diagonal entries 0.  row1: Legendre P1 coefficient of
+// the interpolant, c1 = (3/2) int u xi = (3/2) sum_i w_i x_i u_i for N >= 2
+// (exact, degree N+1 <= 2N-1), and (u_1 - u_0)/2 for N = 1.
+void lgl_tables(int n, Tables &T)
+{
+    std::memset(&T, 0, sizeof(T));
+    const int N = n - 1;
+    long double x[MAXN];
+    x[0] = -1.0L;
+    x[N] = 1.0L;
+    for (int j = 1; j < N; ++j) {
+        long double t = -cosl(3.14159265358979323846264338327950288L * j / N);
+        for (int it = 0; it < 60; ++it) {
+            long double P, Pm;
+            legendre_pair(N, t, P, Pm);
+            const long double dP = N * (t * P - Pm) / (t * t - 1.0L);
+            const long double d2P = (2.0L * t * dP - N * (N + 1.0L) * P) / (1.0L - t * t);
+            const long double step = dP / d2P;
+            t -= step;
+            if (fabsl(step) < 1e-19L) break;
+        }
+        x[j] = t;
+    }
+    for (int j = 0; j < n; ++j) T.x[j] = (double)x[j];
+    for (int j = 0; j < n / 2; ++j) T.x[n - 1 - j] = -T.x[j];
+    if (n % 2) T.x[n / 2] = 0.0;
+    long double PN[MAXN];
+    for (int j = 0; j < n; ++j) {
+        long double Pm;
+        legendre_pair(N, (long double)T.x[j], PN[j], Pm);
+        T.w[j] = (double)(2.0L / (N * (N + 1.0L) * PN[j] * PN[j]));
+    }
+    for (int i = 0; i < n; ++i)
+        for (int l = 0; l < n; ++l) {
+            long double v;
+            if (i != l) v = PN[i] / (PN[l] * ((long double)T.x[i] - (long double)T.x[l]));
+            else if (i == 0) v = -N * (N + 1.0L) / 4.0L;
+            else if (i == N) v = N * (N + 1.0L) / 4.0L;
+            else v = 0.0L;
+            T.D[i * n + l] = (double)v;
+        }
+    for (int i = 0; i < n; ++i) T.row1[i] = (N >= 2) ? 1.5 * T.w[i] * T.x[i] : (i == 0 ? -0.5 : 0.5);
+}
+
+cudaError_t launch_stage_fp64_n2(int, int, const StageArgs &, long long, cudaStream_t);
+cudaError_t launch_stage_fp64_n3(int, int, const StageArgs &, long long, cudaStream_t);
+cudaError_t launch_stage_fp64_n4(int, int, const StageArgs &, long long, cudaStream_t);
+cudaError_t launch_stage_fp64_n5(int, int, const StageArgs &, long long, cudaStream_t);
+cudaError_t launch_stage_fp64_n6(int, int, const StageArgs &, long long, cudaStream_t);
+cudaError_t launch_stage_fp64_n7(int, int, const StageArgs &, long long, cudaStream_t);
+cudaError_t launch_stage_fp64_n8(int, int, const StageArgs &, long long, cudaStream_t);
+cudaError_t launch_summaries_n2(const SummaryArgs &, long long, cudaStream_t);
+cudaError_t launch_summaries_n3(const SummaryArgs &, long long, cudaStream_t);
+cudaError_t launch_summaries_n4(const SummaryArgs &, long long, cudaStream_t);
+cudaError_t launch_summaries_n5(const SummaryArgs &, long long, cudaStream_t);
+cudaError_t launch_summaries_n6(const SummaryArgs &, long long, cudaStream_t);
+cudaError_t launch_summaries_n7(const SummaryArgs &, long long, cudaStream_t);
+cudaError_t launch_summaries_n8(const SummaryArgs &, long long, cudaStream_t);
+cudaError_t launch_limit_n2(const LimitArgs &, cudaStream_t);
+cudaError_t launch_limit_n3(const LimitArgs &, cudaStream_t);
+cudaError_t launch_limit_n4(const LimitArgs &, cudaStream_t);
+cudaError_t launch_limit_n5(const LimitArgs &, cudaStream_t);
+cudaError_t launch_limit_n6(const LimitArgs &, cudaStream_t);
+cudaError_t launch_limit_n7(const LimitArgs &, cudaStream_t);
+cudaError_t launch_limit_n8(const LimitArgs &, cudaStream_t);
+
+cudaError_t launch_stage_fp64(int n, int system, int flux, const StageArgs &a, long long E, cudaStream_t s)
+{
+    switch (n) {
+    case 2: return launch_stage_fp64_n2(system, flux, a, E, s);
+    case 3: return launch_stage_fp64_n3(system, flux, a, E, s);
+    case 4: return launch_stage_fp64_n4(system, flux, a, E, s);
+    case 5: return launch_stage_fp64_n5(system, flux, a, E, s);
+    case 6: return launch_stage_fp64_n6(system, flux, a, E, s);
+    case 7: return launch_stage_fp64_n7(system, flux, a, E, s);
+    case 8: return launch_stage_fp64_n8(system, flux, a, E, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_summaries(int n, const SummaryArgs &a, long long E, cudaStream_t s)
+{
+    switch (n) {
+    case 2: return launch_summaries_n2(a, E, s);
+    case 3: return launch_summaries_n3(a, E, s);
+    case 4: return launch_summaries_n4(a, E, s);
+    case 5: return launch_summaries_n5(a, E, s);
+    case 6: return launch_summaries_n6(a, E, s);
+    case 7: return launch_summaries_n7(a, E, s);
+    case 8: return launch_summaries_n8(a, E, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_limit(int n, const LimitArgs &a, cudaStream_t s)
+{
+    switch (n) {
+    case 2: return launch_limit_n2(a, s);
+    case 3: return launch_limit_n3(a, s);
+    case 4: return launch_limit_n4(a, s);
+    case 5: return launch_limit_n5(a, s);
+    case 6: return launch_limit_n6(a, s);
+    case 7: return launch_limit_n7(a, s);
+    case 8: return launch_limit_n8(a, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_set(double *p, double v, cudaStream_t s);
+
+}  // namespace dg
+
+using namespace dg;
+
+namespace {
+
+StageArgs stage_args(const dg_mesh *m)
+{
+    StageArgs a;
+    std::memset(&a, 0, sizeof(a));
+    for (int ax = 0; ax < 3; ++ax) {
+        a.K[ax] = m->d.K[ax];
+        a.g[ax] = 2.0 / m->dx[ax];
+        a.lift0[ax] = a.g[ax] / m->T.w[0];
+        a.liftN[ax] = a.g[ax] / m->T.w[m->d.n - 1];
+    }
+    a.gamma = m->d.gamma;
+    a.T = m->T;
+    return a;
+}
+
+LimitArgs limit_args(const dg_mesh *m, double *U, unsigned char *troubled)
+{
+    LimitArgs l;
+    std::memset(&l, 0, sizeof(l));
+    l.U = U;
+    l.S = m->S;
+    l.unphys = (m->d.system == 1) ? m->unphys : nullptr;
+    l.troubled = troubled;
+    l.E = m->E;
+    for (int ax = 0; ax < 3; ++ax) {
+        l.K[ax] = m->d.K[ax];
+        l.dx[ax] = m->dx[ax];
+    }
+    l.limiter = m->d.limiter;
+    l.tvb_M = m->d.tvb_M;
+    l.beta = m->d.beta;
+    l.T = m->T;
+    return l;
+}
+
+dg_status check_mesh(const dg_mesh *m)
+{
+    if (!m) return fail(DG_ERR_ARG, "mesh is NULL");
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != m->device)
+        return fail(DG_ERR_ARG, "mesh was created on device %d, current device is %d", m->device, dev);
+    return DG_OK;
+}
+
+void free_scratch(dg_mesh *m)
+{
+    if (m->prof) {
+        ProfLog *L = (ProfLog *)m->prof;
+        for (auto &r : L->recs) {
+            cudaEventDestroy(r.a);
+            cudaEventDestroy(r.b);
+        }
+        for (auto e : L->pool) cudaEventDestroy(e);
+        delete L;
+        m->prof = nullptr;
+    }
+    cudaFree(m->W1);
+    cudaFree(m->W2);
+    cudaFree(m->P);
+    cudaFree(m->S);
+    cudaFree(m->unphys);
+    cudaFree(m->lam);
+    cudaFree(m->dt);
+    cudaFree(m->err);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *dg_last_error(void) { return g_err; }
+
+dg_status dg_mesh_create(const dg_mesh_desc *d, dg_mesh **out)
+{
+    if (!d || !out) return fail(DG_ERR_ARG, "desc and out must not be NULL");
+    *out = nullptr;
+    if (d->system != 0 && d->system != 1) return fail(DG_ERR_ARG, "system must be 0 or 1");
+    if (d->n < 2 || d->n > MAXN) return fail(DG_ERR_ARG, "n must be in 2..%d", MAXN);
+    if (d->flux != 0 && d->flux != 1) return fail(DG_ERR_ARG, "flux must be 0 (LLF) or 1 (HLL)");
+    if (d->limiter < 0 || d->limiter > 2) return fail(DG_ERR_ARG, "limiter must be 0, 1 or 2");
+    if (d->precision != 0) return fail(DG_ERR_ARG, "precision %d is not supported by dg_mesh_create", d->precision);
+    if (!(d->gamma > 1.0)) return fail(DG_ERR_ARG, "gamma must be > 1");
+    if (!(d->beta > 0.0) || !(d->tvb_M >= 0.0)) return fail(DG_ERR_ARG, "beta must be > 0 and tvb_M >= 0");
+    long long E = 1;
+    for (int a = 0; a < 3; ++a) {
+        if (d->K[a] < 1) return fail(DG_ERR_ARG, "K[%d] must be >= 1", a);
+        if (!(d->hi[a] > d->lo[a])) return fail(DG_ERR_ARG, "hi[%d] must exceed lo[%d]", a, a);
+        E *= d->K[a];
+        if (E > (1LL << 40)) return fail(DG_ERR_ARG, "too many elements");
+    }
+    if (E > 0x7fffffffLL) return fail(DG_ERR_ARG, "at most 2^31-1 elements (one CTA per element)");
+    dg_mesh *m = new dg_mesh;
+    std::memset(m, 0, sizeof(*m));
+    m->d = *d;
+    cudaGetDevice(&m->device);
+    m->nn = d->n * d->n * d->n;
+    m->E = E;
+    lgl_tables(d->n, m->T);
+    m->dxmin = INFINITY;
+    for (int a = 0; a < 3; ++a) {
+        m->dx[a] = (d->hi[a] - d->lo[a]) / d->K[a];
+        const double h = 0.5 * m->dx[a] * (m->T.x[1] - m->T.x[0]);
+        if (h < m->dxmin) m->dxmin = h;
+    }
+    const size_t state = sizeof(double) * (size_t)E * 5 * m->nn;
+    cudaError_t st = cudaSuccess;
+    st = st ? st : cudaMalloc(&m->W1, state);
+    st = st ? st : cudaMalloc(&m->W2, state);
+    st = st ? st : cudaMalloc(&m->P, sizeof(double) * (size_t)E * 4 * m->nn);
+    st = st ? st : cudaMalloc(&m->S, sizeof(double) * (size_t)E * 50);
+    st = st ? st : cudaMalloc(&m->unphys, (size_t)E);
+    st = st ? st : cudaMalloc(&m->lam, sizeof(unsigned long long));
+    st = st ? st : cudaMalloc(&m->dt, sizeof(double));
+    st = st ? st : cudaMalloc(&m->err, sizeof(unsigned int));
+    if (st == cudaSuccess) st = cudaMemset(m->err, 0, sizeof(unsigned int));
+    if (st == cudaSuccess) st = cudaMemset(m->unphys, 0, (size_t)E);
+    if (st != cudaSuccess) {
+        free_scratch(m);
+        delete m;
+        cudaGetLastError();
+        return fail(st == cudaErrorMemoryAllocation ? DG_ERR_NOMEM : DG_ERR_CUDA, "mesh scratch: %s",
+                    cudaGetErrorString(st));
+    }
+    *out = m;
+    return DG_OK;
+}
+
+void dg_mesh_destroy(dg_mesh *m)
+{
+    if (!m) return;
+    cudaDeviceSynchronize();
+    free_scratch(m);
+    delete m;
+}
+
+long long dg_state_size(const dg_mesh *m) { return m ? m->E * 5 * m->nn : 0; }
+long long dg_num_nodes(const dg_mesh *m) { return m ? m->E * m->nn : 0; }
+
+dg_status dg_node_coords(const dg_mesh *m, double *xyz, void *stream)
+{
+    if (dg_status s = check_mesh(m)) return s;
+    if (!xyz) return fail(DG_ERR_ARG, "xyz is NULL");
+    DG_CUDA(launch_coords(m, xyz, (cudaStream_t)stream));
+    return DG_OK;
+}
+
+dg_status dg_prim2con(const dg_mesh *m, const double *prim, double *U, void *stream)
+{
+    if (dg_status s = check_mesh(m)) return s;
+    if (!prim || !U || (const void *)prim == (const void *)U) return fail(DG_ERR_ARG, "prim and U must be distinct, non-NULL");
+    DG_CUDA(launch_prim2con(m, prim, U, (cudaStream_t)stream));
+    return DG_OK;
+}
+
+dg_status dg_primitives(dg_mesh *m, const double *U, double *P, void *stream)
+{
+    if (dg_status s = check_mesh(m)) return s;
+    if (!U || !P) return fail(DG_ERR_ARG, "U and P must not be NULL");
+    DG_CUDA(launch_primitives(m, U, P, 0, nullptr, nullptr, (cudaStream_t)stream));
+    return DG_OK;
+}
+
+dg_status dg_rhs(dg_mesh *m, const double *U, double *dUdt, void *stream)
+{
+    if (dg_status s = check_mesh(m)) return s;
+    if (!U || !dUdt || U == dUdt) return fail(DG_ERR_ARG, "U and dUdt must be distinct, non-NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    DG_LAUNCH(m, s, PROF_PRIM, launch_primitives(m, U, m->P, 0, nullptr, nullptr, s));
+    StageArgs a = stage_args(m);
+    a.Us = U;
+    a.Un = U;
+    a.P = m->P;
+    a.out = dUdt;
+    a.mode = 0;
+    DG_LAUNCH(m, s, PROF_STAGE, launch_stage_fp64(m->d.n, m->d.system, m->d.flux, a, m->E, s));
+    return DG_OK;
+}
+
+dg_status dg_compute_dt(dg_mesh *m, const double *U, double cfl, double *dt, void *stream)
+{
+    if (dg_status s = check_mesh(m)) return s;
+    if (!U || !dt) return fail(DG_ERR_ARG, "U and dt must not be NULL");
+    if (!(cfl > 0.0)) return fail(DG_ERR_ARG, "cfl must be > 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    DG_CUDA(cudaMemsetAsync(m->lam, 0, sizeof(unsigned long long), s));
+    DG_CUDA(launch_primitives(m, U, m->P, 0, nullptr, m->lam, s));
+    DG_CUDA(launch_dt(m, cfl, dt, s));
+    return DG_OK;
+}
+
+dg_status dg_rk3_step(dg_mesh *m, double *U, double dt, double cfl, double *dt_used, unsigned char *troubled,
+                      void *stream)
+{
+    if (dg_status s = check_mesh(m)) return s;
+    if (!U) return fail(DG_ERR_ARG, "U is NULL");
+    const bool cflmode = cfl > 0.0;
+    if (!cflmode && !(dt > 0.0)) return fail(DG_ERR_ARG, "need dt > 0 or cfl > 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool sr = m->d.system == 1;
+    const bool lim = m->d.limiter != 0;
+    StageArgs a = stage_args(m);
+    a.P = m->P;
+    a.mode = 1;
+    a.dt = dt;
+    a.dt_ptr = cflmode ? m->dt : nullptr;
+    a.S = lim ? m->S : nullptr;
+    a.unphys = (lim && sr) ? m->unphys : nullptr;
+    if (cflmode) DG_CUDA(cudaMemsetAsync(m->lam, 0, sizeof(unsigned long long), s));
+
+    double *ins[3] = {U, m->W1, m->W2};
+    double *outs[3] = {m->W1, m->W2, U};
+    const double ca[3] = {0.0, 0.75, 1.0 / 3.0};
+    const double cb[3] = {1.0, 0.25, 2.0 / 3.0};
+    for (int st = 0; st < 3; ++st) {
+        // the SR fix of the previous stage's result is fused into its primitive pass
+        DG_LAUNCH(m, s, PROF_PRIM,
+                  launch_primitives(m, ins[st], m->P, sr && st > 0, ins[st], (cflmode && st == 0) ? m->lam : nullptr, s));
+        if (cflmode && st == 0) DG_LAUNCH(m, s, PROF_DT, launch_dt(m, cfl, m->dt, s));
+        a.Us = ins[st];
+        a.Un = U;
+        a.out = outs[st];
+        a.first = st == 0;
+        a.ca = ca[st];
+        a.cb = cb[st];
+        DG_LAUNCH(m, s, PROF_STAGE, launch_stage_fp64(m->d.n, m->d.system, m->d.flux, a, m->E, s));
+        if (lim) {
+            LimitArgs l = limit_args(m, outs[st], st == 2 ? troubled : nullptr);
+            DG_LAUNCH(m, s, PROF_LIMIT, launch_limit(m->d.n, l, s));
+        }
+    }
+    if (sr) DG_LAUNCH(m, s, PROF_FIX, launch_fix(m, U, s));
+    if (dt_used) {
+        if (cflmode) DG_CUDA(cudaMemcpyAsync(dt_used, m->dt, sizeof(double), cudaMemcpyDeviceToDevice, s));
+        else DG_CUDA(launch_set(dt_used, dt, s));
+    }
+    return DG_OK;
+}
+
+dg_status dg_limiter_summaries(dg_mesh *m, const double *U, double *S, void *stream)
+{
+    if (dg_status s = check_mesh(m)) return s;
+    if (!U || !S) return fail(DG_ERR_ARG, "U and S must not be NULL");
+    SummaryArgs sa;
+    sa.U = U;
+    sa.S = S;
+    sa.unphys = (m->d.system == 1) ? m->unphys : nullptr;
+    sa.T = m->T;
+    DG_CUDA(launch_summaries(m->d.n, sa, m->E, (cudaStream_t)stream));
+    return DG_OK;
+}
+
+dg_status dg_limit(dg_mesh *m, double *U, unsigned char *troubled, void *stream)
+{
+    if (dg_status s = check_mesh(m)) return s;
+    if (!U) return fail(DG_ERR_ARG, "U is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (m->d.limiter == 0) {
+        if (troubled) DG_CUDA(cudaMemsetAsync(troubled, 0, (size_t)m->E, s));
+        return DG_OK;
+    }
+    SummaryArgs sa;
+    sa.U = U;
+    sa.S = m->S;
+    sa.unphys = (m->d.system == 1) ? m->unphys : nullptr;
+    sa.T = m->T;
+    DG_CUDA(launch_summaries(m->d.n, sa, m->E, s));
+    LimitArgs l = limit_args(m, U, troubled);
+    DG_CUDA(launch_limit(m->d.n, l, s));
+    return DG_OK;
+}
+
+dg_status dg_fix(dg_mesh *m, double *U, void *stream)
+{
+    if (dg_status s = check_mesh(m)) return s;
+    if (!U) return fail(DG_ERR_ARG, "U is NULL");
+    if (m->d.system == 1) DG_CUDA(launch_fix(m, U, (cudaStream_t)stream));
+    return DG_OK;
+}
+
+dg_status dg_con2prim(long long count, double gamma, const double *cons, double *prim, const double *p_guess,
+                      int *iters, int *status, void *stream)
+{
+    if (count < 0) return fail(DG_ERR_ARG, "count must be >= 0");
+    if (count == 0) return DG_OK;
+    if (!cons || !prim) return fail(DG_ERR_ARG, "cons and prim must not be NULL");
+    if (!(gamma > 1.0)) return fail(DG_ERR_ARG, "gamma must be > 1");
+    DG_CUDA(launch_con2prim(count, gamma, cons, prim, p_guess, iters, status, (cudaStream_t)stream));
+    return DG_OK;
+}
+
+dg_status dg_sync_status(dg_mesh *m, void *stream)
+{
+    if (dg_status s = check_mesh(m)) return s;
+    DG_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    unsigned int bits = 0;
+    DG_CUDA(cudaMemcpy(&bits, m->err, sizeof(bits), cudaMemcpyDeviceToHost));
+    DG_CUDA(cudaMemset(m->err, 0, sizeof(bits)));
+    if (bits & ERRBIT_TIMEOUT) return fail(DG_ERR_TIMEOUT, "a bounded device wait ran out");
+    if (bits & ERRBIT_C2P) return fail(DG_ERR_C2P, "con2prim failed at some node");
+    if (bits & ERRBIT_UNPHYSICAL) return fail(DG_ERR_UNPHYSICAL, "unphysical conserved state");
+    return DG_OK;
+}
+
+dg_status dg_profile_enable(dg_mesh *m, int on)
+{
+    if (dg_status s = check_mesh(m)) return s;
+    if (!m->prof) m->prof = new ProfLog;
+    m->prof_on = on ? 1 : 0;
+    return DG_OK;
+}
+
+dg_status dg_profile_read(dg_mesh *m, double *ms, long long *launches, int nclass)
+{
+    if (dg_status s = check_mesh(m)) return s;
+    if (nclass < 0 || (nclass > 0 && (!ms || !launches))) return fail(DG_ERR_ARG, "ms and launches must hold nclass entries");
+    for (int c = 0; c < nclass; ++c) {
+        ms[c] = 0.0;
+        launches[c] = 0;
+    }
+    if (!m->prof) return DG_OK;
+    ProfLog *L = (ProfLog *)m->prof;
+    for (auto &r : L->recs) {
+        DG_CUDA(cudaEventSynchronize(r.b));
+        float t = 0.0f;
+        DG_CUDA(cudaEventElapsedTime(&t, r.a, r.b));
+        if (r.cls < nclass) {
+            ms[r.cls] += t;
+            launches[r.cls] += 1;
+        }
+        L->pool.push_back(r.a);
+        L->pool.push_back(r.b);
+    }
+    L->recs.clear();
+    return DG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,104 @@
+// dg_internal.h -- host-side types shared by the translation units of libdg.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "../../include/dg.h"
+
+namespace dg {
+
+constexpr int MAXN = 8;  // largest LGL node count per axis
+
+// 1D LGL tables for one n, as passed by value to the kernels.
+struct Tables {
+    double D[MAXN * MAXN];  // D[i*n+l] = ell_l'(xbar_i)
+    double w[MAXN];         // quadrature weights
+    double x[MAXN];         // nodes
+    double row1[MAXN];      // Legendre P1 coefficient of the nodal interpolant: c1 = sum_i row1[i] u_i
+};
+
+// Per-launch arguments of the fused stage kernel (RHS of eq:411 + SSP-RK3 stage
+// + limiter summaries).
+struct StageArgs {
+    const double *Us;      // state the RHS is evaluated on
+    const double *Un;      // U^n (stages 2 and 3)
+    const double *P;       // primitives (vx, vy, vz, p) of Us, [e][4][node]
+    double *out;           // U_{s+1} (mode 1) or dU/dt (mode 0)
+    double *S;             // limiter summaries [e][5][10] of out, or nullptr
+    unsigned char *unphys; // SR: per-element unphysical flag of out, or nullptr
+    const double *dt_ptr;  // device dt (CFL mode) or nullptr
+    double dt;             // host dt when dt_ptr == nullptr
+    double ca, cb;         // out = ca Un + cb (Us + dt R); first stage: out = Us + dt R
+    int first;             // first stage flag
+    int mode;              // 0 write RHS, 1 stage update
+    int K[3];
+    double gamma;
+    double g[3];           // 2/dx_a
+    double lift0[3];       // (2/dx_a)/w_0
+    double liftN[3];       // (2/dx_a)/w_N
+    Tables T;
+};
+
+struct LimitArgs {
+    double *U;
+    const double *S;
+    const unsigned char *unphys;
+    unsigned char *troubled;
+    long long E;
+    int K[3];
+    int limiter;
+    double tvb_M, beta;
+    double dx[3];
+    Tables T;
+};
+
+struct SummaryArgs {
+    const double *U;
+    double *S;
+    unsigned char *unphys;  // SR: per-element unphysical flag of U, or nullptr
+    Tables T;
+};
+
+}  // namespace dg
+
+struct dg_mesh {
+    dg_mesh_desc d;
+    int device;
+    int nn;          // nodes per element
+    long long E;     // elements
+    double dx[3];
+    double dxmin;    // smallest node gap
+    dg::Tables T;
+    // library-owned device scratch
+    double *W1, *W2;         // stage states
+    double *P;               // primitives [e][4][node]
+    double *S;               // limiter summaries [e][5][10]
+    unsigned char *unphys;   // per-element unphysical flag
+    unsigned long long *lam; // max wave speed (bit pattern of a non-negative double)
+    double *dt;              // device step
+    unsigned int *err;       // sticky status word
+    // optional per-kernel timing (dg_profile_enable)
+    int prof_on;
+    void *prof;              // host-side event log, owned by dg_api.cu
+};
+
+namespace dg {
+
+// Kernel launchers (defined in the .cu files).
+cudaError_t launch_stage_fp64(int n, int system, int flux, const StageArgs &a, long long E, cudaStream_t s);
+cudaError_t launch_summaries(int n, const SummaryArgs &a, long long E, cudaStream_t s);
+cudaError_t launch_limit(int n, const LimitArgs &a, cudaStream_t s);
+
+cudaError_t launch_primitives(const dg_mesh *m, const double *U, double *P, int fix, double *Ufix,
+                              unsigned long long *lam, cudaStream_t s);
+cudaError_t launch_fix(const dg_mesh *m, double *U, cudaStream_t s);
+cudaError_t launch_dt(const dg_mesh *m, double cfl, double *dt, cudaStream_t s);
+cudaError_t launch_coords(const dg_mesh *m, double *xyz, cudaStream_t s);
+cudaError_t launch_prim2con(const dg_mesh *m, const double *prim, double *U, cudaStream_t s);
+cudaError_t launch_con2prim(long long count, double gamma, const double *cons, double *prim,
+                            const double *guess, int *iters, int *status, cudaStream_t s);
+
+// Host LGL tables (long double Newton; closed-form LGL differentiation matrix).
+void lgl_tables(int n, Tables &T);
+
+}  // namespace dg

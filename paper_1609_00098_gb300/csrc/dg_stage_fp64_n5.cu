@@ -1,0 +1,3 @@
+// FP64 stage kernels for 5 LGL nodes per axis.
+#include "dg_stage_fp64.cuh"
+DG_INSTANTIATE_STAGE(5)

@@ -1,0 +1,233 @@
+"""GPU vs oracle parity of the FP64 CUDA path, element by element, through the
+C ABI.  Tolerance: relative max-norm per variable <= 1e-12 (the bar for the FP64
+path), scale = max |oracle| of that variable."""
+import math
+
+import numpy as np
+import pytest
+
+import dg_inputs as di
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1609_00098_gb300 as p
+    from paper_1609_00098_gb300 import build as b
+    b.build()
+    return p
+
+
+def _rel(got, ref, axis=(0, 2)):
+    scale = np.maximum(np.abs(ref).max(axis=axis), 1e-300)
+    return np.abs(got - ref).max(axis=axis) / scale
+
+
+def _pair(pkg, system=0, K=(4, 4, 4), n=4, flux=0, limiter=0, gamma=None, lo=(0, 0, 0), hi=(1, 1, 1),
+          **kw):
+    gamma = gamma or (1.4 if system == 0 else 4.0 / 3.0)
+    spec = oracle.MeshSpec(system=system, K=K, n=n, flux=flux, limiter=limiter, gamma=gamma, lo=lo, hi=hi, **kw)
+    om = oracle.Mesh(spec)
+    gm = pkg.Mesh(system=system, K=K, n=n, flux=flux, limiter=limiter, gamma=gamma, lo=lo, hi=hi, **kw)
+    return om, gm
+
+
+def _init(om, kind, seed=1):
+    xyz = om.coords()
+    if kind == "wave":
+        return om.from_prim(di.smooth_wave_ne(xyz, k=di.wave_numbers(seed)))
+    if kind == "blast":
+        return om.from_prim(di.blast_sr(xyz, seed=seed))
+    if kind == "kh":
+        return om.from_prim(di.kh_ne(xyz, seed=seed))
+    if kind == "re_smooth":
+        return om.from_prim(di.smooth_flow_re(xyz, gamma=om.spec.gamma))
+    raise ValueError(kind)
+
+
+def _gpu(x):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def test_tables_coords_prim2con(pkg):
+    import torch
+    om, gm = _pair(pkg, system=1, K=(3, 2, 5), n=5, lo=(-1, 0, 2), hi=(1, 0.5, 3))
+    xo = om.coords()
+    xg = gm.coords().cpu().numpy()
+    assert np.abs(xg - xo).max() <= 4e-16 * np.abs(xo).max()
+    prim = di.blast_sr(xo, seed=3)
+    Ug = gm.from_prim(_gpu(prim)).cpu().numpy()
+    Uo = om.from_prim(prim)
+    assert _rel(Ug, Uo).max() <= 1e-15
+
+
+@pytest.mark.parametrize("system,flux,kind,n", [(0, 0, "wave", 4), (0, 1, "kh", 3), (1, 1, "blast", 5),
+                                                (1, 0, "re_smooth", 2), (0, 1, "wave", 8), (1, 1, "blast", 7)])
+def test_rhs_parity(pkg, system, flux, kind, n):
+    lo, hi = ((-0.5,) * 3, (0.5,) * 3) if kind == "kh" else ((0, 0, 0), (1, 1, 1))
+    om, gm = _pair(pkg, system=system, K=(3, 4, 2), n=n, flux=flux, lo=lo, hi=hi)
+    U = _init(om, kind)
+    Ro = om.rhs(U)
+    Rg = gm.rhs(_gpu(U)).cpu().numpy()
+    assert gm.sync_status() == 0
+    assert _rel(Rg, Ro).max() <= TOL, _rel(Rg, Ro)
+
+
+def test_primitives_and_dt_parity(pkg):
+    import torch
+    om, gm = _pair(pkg, system=1, K=(4, 4, 4), n=5, flux=1)
+    U = _init(om, "blast")
+    Pg = gm.primitives(_gpu(U)).cpu().numpy()
+    Po = om.primitives(U)
+    assert _rel(Pg, Po).max() <= TOL
+    dtg = gm.cfl_dt(_gpu(U), 0.2).item()
+    dto = om.cfl_dt(U, 0.2)
+    assert abs(dtg - dto) <= 4e-16 * dto
+
+
+@pytest.mark.parametrize("n", [2, 3, 5, 8])
+def test_limiter_parity(pkg, n):
+    import torch
+    om, gm = _pair(pkg, system=1, K=(4, 3, 3), n=n, flux=1, limiter=1)
+    U = _init(om, "blast", seed=2)
+    So = om.summaries(U)
+    Sg = gm.summaries(_gpu(U)).cpu().numpy()
+    assert _rel(Sg, So, axis=(0,)).max() <= 1e-13
+    Lo, to = om.limit(U)
+    t = torch.zeros(om.E, dtype=torch.uint8, device="cuda")
+    Ug = _gpu(U)
+    gm.limit(Ug, t)
+    assert np.array_equal(t.cpu().numpy(), to)
+    assert _rel(Ug.cpu().numpy(), Lo).max() <= TOL
+
+
+def test_config1_ten_steps(pkg):
+    """Newtonian smooth wave, K=4, n=4, Rusanov, CFL 0.2, 10 steps, no limiter:
+    GPU (dt from the device CFL reduction) vs oracle, and both vs the exact solution."""
+    import torch
+    om, gm = _pair(pkg, system=0, K=(4, 4, 4), n=4, flux=0)
+    k = di.wave_numbers(1)
+    U0 = om.from_prim(di.smooth_wave_ne(om.coords(), k=k))
+    Uo = U0.copy()
+    t = 0.0
+    for _ in range(10):
+        h = om.cfl_dt(Uo, 0.2)
+        Uo = om.rk3_step(Uo, h)
+        t += h
+    Ug = _gpu(U0)
+    dt = torch.zeros(1, dtype=torch.float64, device="cuda")
+    tg = 0.0
+    for _ in range(10):
+        gm.rk3_step(Ug, cfl=0.2, dt_used=dt)
+        tg += dt.item()
+    assert gm.sync_status() == 0
+    assert abs(tg - t) <= 1e-14 * t
+    assert _rel(Ug.cpu().numpy(), Uo).max() <= TOL
+    Uex = om.from_prim(di.smooth_wave_ne(om.coords(), t, k=k))
+    eo = om.norms(Uo, Uex)[1]
+    eg = om.norms(Ug.cpu().numpy(), Uex)[1]
+    assert np.allclose(eg, eo, rtol=1e-9)
+
+
+@pytest.mark.parametrize("limiter", [1, 2])
+def test_blast_steps_with_limiter(pkg, limiter):
+    """SR blast, HLL, limiter after every stage, fix: 10 CFL steps, troubled flags of
+    each step's last stage compared first, then the state."""
+    import torch
+    om, gm = _pair(pkg, system=1, K=(5, 4, 4), n=5, flux=1, limiter=limiter)
+    U = _init(om, "blast")
+    Ug = _gpu(U)
+    Uo = U.copy()
+    tg = torch.zeros(om.E, dtype=torch.uint8, device="cuda")
+    for step in range(10):
+        h = om.cfl_dt(Uo, 0.2)
+        to = np.zeros(om.E, dtype=np.uint8)
+        Uo = om.rk3_step(Uo, h, to)
+        gm.rk3_step(Ug, dt=h, troubled=tg)
+        assert np.array_equal(tg.cpu().numpy(), to), f"troubled flags differ at step {step}"
+    assert gm.sync_status() == 0
+    assert _rel(Ug.cpu().numpy(), Uo).max() <= TOL, _rel(Ug.cpu().numpy(), Uo)
+
+
+def test_con2prim_parity(pkg):
+    import torch
+    g = 4.0 / 3.0
+    prim = di.c2p_samples(9, 200000, gamma=g)
+    cons = oracle.prim2con(1, g, prim)
+    po, ito, sto = oracle.con2prim(g, cons)
+    N = cons.shape[1]
+    pg = torch.empty((5, N), dtype=torch.float64, device="cuda")
+    it = torch.empty(N, dtype=torch.int32, device="cuda")
+    st = torch.empty(N, dtype=torch.int32, device="cuda")
+    pkg.abi.dg_con2prim(N, g, _gpu(cons), pg, None, it, st)
+    pg = pg.cpu().numpy()
+    assert np.all(st.cpu().numpy() == 0)
+    rel = np.abs(pg - po) / np.maximum(np.abs(po), 1e-300)
+    assert rel[[0, 4]].max() <= TOL
+    vmag = np.sqrt((po[1:4] ** 2).sum(axis=0)) + 1e-300
+    assert (np.abs(pg[1:4] - po[1:4]) / vmag).max() <= TOL
+    # guesses: the oracle's own answer as a guess converges at once to the same root
+    pkg.abi.dg_con2prim(N, g, _gpu(cons), _gpu(np.zeros((5, N))), _gpu(po[4]), it, st)
+    assert it.cpu().numpy().max() <= 3
+
+
+def test_edge_cases_shapes(pkg):
+    """Self-periodic K=1 axes, ragged K, anisotropic boxes, both extreme n."""
+    for K, n, system in [((1, 1, 1), 2, 0),
+                             ((1, 3, 1), 8, 1),
+                             ((7, 1, 2), 3, 1)]:
+        om, gm = _pair(pkg, system=system, K=K, n=n, flux=1, limiter=1, lo=(0, -2, 0), hi=(1, 1, 0.25))
+        U = _init(om, "wave" if system == 0 else "blast")
+        Uo = om.rk3_step(U, 0.3 * om.cfl_dt(U, 0.2))
+        Ug = _gpu(U)
+        gm.rk3_step(Ug, dt=0.3 * om.cfl_dt(U, 0.2))
+        assert gm.sync_status() == 0
+        assert _rel(Ug.cpu().numpy(), Uo).max() <= TOL
+
+
+def test_deterministic(pkg):
+    om, gm = _pair(pkg, system=1, K=(4, 4, 4), n=5, flux=1, limiter=1)
+    U = _init(om, "blast")
+    a, b = _gpu(U), _gpu(U)
+    for _ in range(3):
+        gm.rk3_step(a, cfl=0.2)
+        gm.rk3_step(b, cfl=0.2)
+    assert bool((a == b).all())
+
+
+def test_unphysical_state_reports_status(pkg):
+    """A node with tau < 0 makes con2prim fail; the status word reports it and the
+    kernels return normally (nothing traps)."""
+    om, gm = _pair(pkg, system=1, K=(2, 2, 2), n=3, flux=1)
+    U = _init(om, "blast")
+    U[3, 4, 5] = -1.0
+    R = gm.rhs(_gpu(U))
+    assert gm.sync_status() == pkg.abi.DG_ERR_C2P
+    assert gm.sync_status() == 0  # cleared
+
+
+def test_full_size_blast_one_step(pkg):
+    """The bench workload (SR blast, 16^3 elements, n=5, HLL, MinModN) at full size,
+    in the launch configuration the bench times: one CFL step on both sides."""
+    import torch
+    om, gm = _pair(pkg, system=1, K=(16, 16, 16), n=5, flux=1, limiter=1)
+    U = _init(om, "blast", seed=1)
+    h = om.cfl_dt(U, 0.2)
+    to = np.zeros(om.E, dtype=np.uint8)
+    Uo = om.rk3_step(U, h, to)
+    Ug = _gpu(U)
+    dt = torch.zeros(1, dtype=torch.float64, device="cuda")
+    tg = torch.zeros(om.E, dtype=torch.uint8, device="cuda")
+    gm.rk3_step(Ug, cfl=0.2, dt_used=dt, troubled=tg)
+    assert gm.sync_status() == 0
+    assert abs(dt.item() - h) <= 4e-16 * h
+    assert np.array_equal(tg.cpu().numpy(), to)
+    assert _rel(Ug.cpu().numpy(), Uo).max() <= TOL
