@@ -77,6 +77,13 @@ long long dg_state_size(const dg_mesh *mesh);
 /* Number of nodes E * n^3. */
 long long dg_num_nodes(const dg_mesh *mesh);
 
+/* The 1D LGL tables the kernels use (Sec. 3.1), host arrays of n (x, w, row1)
+ * and n*n (D) doubles: nodes x ascending, quadrature weights w, differentiation
+ * matrix D[i*n+l] = ell_l'(x_i) (eq:405), and row1, the Legendre P1 coefficient
+ * of the nodal interpolant (c1 = sum_i row1[i] u_i).  No GPU needed.
+ * DG_ERR_ARG if n is outside 2..8 or a pointer is NULL. */
+dg_status dg_lgl_tables(int n, double *x, double *w, double *D, double *row1);
+
 /* Physical coordinates of every node, eq:AffineMap: xyz[a*N + g], a = 0..2,
  * N = dg_num_nodes(), g the node index. */
 dg_status dg_node_coords(const dg_mesh *mesh, double *xyz, void *stream);

@@ -53,6 +53,7 @@ SIGNATURES = {
     "dg_mesh_destroy": (None, [_vp]),
     "dg_state_size": (_ll, [_vp]),
     "dg_num_nodes": (_ll, [_vp]),
+    "dg_lgl_tables": (_i, [_i, _vp, _vp, _vp, _vp]),
     "dg_node_coords": (_i, [_vp, _vp, _vp]),
     "dg_prim2con": (_i, [_vp, _vp, _vp, _vp]),
     "dg_primitives": (_i, [_vp, _vp, _vp, _vp]),
@@ -153,6 +154,15 @@ def dg_state_size(mesh) -> int:
 
 def dg_num_nodes(mesh) -> int:
     return load().dg_num_nodes(mesh)
+
+
+def dg_lgl_tables(n: int):
+    """Host LGL tables of the library: (x, w, D (n, n), row1) as numpy arrays."""
+    import numpy as np
+    x, w, r1 = np.zeros(n), np.zeros(n), np.zeros(n)
+    D = np.zeros((n, n))
+    _check(load().dg_lgl_tables(n, x.ctypes.data, w.ctypes.data, D.ctypes.data, r1.ctypes.data))
+    return x, w, D, r1
 
 
 def dg_node_coords(mesh, xyz, stream=None):

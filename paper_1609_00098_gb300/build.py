@@ -20,7 +20,12 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libdg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
-              "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]
+              "-Xcompiler", "-ffp-contract=off", "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]
+# The FP64 path (and the host code of the ABI) is compiled without contraction of
+# a*b+c into FMA, so that it evaluates the same IEEE operations in the same order
+# as a plain sequential FP64 evaluation of the formulas.  Mixed-precision kernels
+# (files named *_mixed*) keep the default contraction.
+NO_FMAD = ["-fmad=false"]
 
 
 def _nvcc() -> str:
@@ -59,7 +64,8 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -
         src, obj = src_obj
         if not force and os.path.exists(obj) and os.path.getmtime(obj) > max(os.path.getmtime(src), hdr_time):
             return obj
-        cmd = [nvcc, *ARCH, *NVCC_FLAGS, "-c", src, "-o", obj]
+        extra = [] if "_mixed" in os.path.basename(src) else NO_FMAD
+        cmd = [nvcc, *ARCH, *NVCC_FLAGS, *extra, "-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), flush=True)
         r = subprocess.run(cmd, capture_output=True, text=True)

@@ -73,66 +73,110 @@ enum { PROF_PRIM = 0, PROF_STAGE = 1, PROF_LIMIT = 2, PROF_FIX = 3, PROF_DT = 4,
 
 namespace dg {
 
-// Legendre P_N(x) and P_{N-1}(x) in long double by the three-term recurrence.
-static void legendre_pair(int N, long double x, long double &PN, long double &PNm1)
+// LGL tables (Sec. 3.1), computed on the host in FP64 with the textbook steps:
+//  * Legendre P_m and P_m' by (k+1) P_{k+1} = (2k+1) x P_k - k P_{k-1} and
+//    P'_{k+1} = P'_{k-1} + (2k+1) P_k;
+//  * interior nodes = zeros of P_N', Newton from -cos(pi j/N) with P_N'' from
+//    Legendre's equation (1-x^2) P'' = 2x P' - N(N+1) P, mirrored about 0;
+//  * w_j = 2/(N(N+1) P_N(x_j)^2);
+//  * D_il = (lambda_l/lambda_i)/(x_i - x_l), lambda_j = 1/prod_{k!=j}(x_j - x_k),
+//    D_ii = -sum_{l!=i} D_il (eq:405; D annihilates constants);
+//  * row1 = second row of the inverse Legendre Vandermonde V[i][m] = P_m(x_i)
+//    (Gauss-Jordan with partial pivoting): c1 = sum_i row1[i] u_i.
+// The FP64 kernels use these values directly, so every operation order here is
+// fixed and written out.
+static void legendre_and_slope(int N, double x, double &P, double &dP)
 {
-    long double p0 = 1.0L, p1 = x;
-    if (N == 0) { PN = 1.0L; PNm1 = 0.0L; return; }
-    for (int k = 2; k <= N; ++k) {
-        const long double p2 = ((2 * k - 1) * x * p1 - (k - 1) * p0) / k;
-        p0 = p1;
-        p1 = p2;
+    if (N == 0) {
+        P = 1.0;
+        dP = 0.0;
+        return;
     }
-    PN = p1;
-    PNm1 = p0;
+    double a = 1.0, b = x, da = 0.0, db = 1.0;  // P_{k-1}, P_k and their slopes
+    for (int k = 1; k < N; ++k) {
+        const double c = ((2.0 * k + 1.0) * x * b - k * a) / (k + 1.0);
+        const double dc = da + (2.0 * k + 1.0) * b;
+        a = b;
+        b = c;
+        da = db;
+        db = dc;
+    }
+    P = b;
+    dP = db;
 }
 
-// LGL nodes: +-1 and the zeros of P_N', found by Newton in long double with
-// P_N' = N (x P_N - P_{N-1})/(x^2 - 1) and P_N'' from Legendre's equation.
-// Weights w_j = 2/(N(N+1) P_N(x_j)^2).  Differentiation matrix in the LGL
-// closed form D_il = P_N(x_i)/(P_N(x_l)(x_i - x_l)) (i != l), D_00 = -N(N+1)/4,
-// D_NN = N(N+1)/4, other diagonal entries 0.  row1: Legendre P1 coefficient of
-// the interpolant, c1 = (3/2) int u xi = (3/2) sum_i w_i x_i u_i for N >= 2
-// (exact, degree N+1 <= 2N-1), and (u_1 - u_0)/2 for N = 1.
 void lgl_tables(int n, Tables &T)
 {
     std::memset(&T, 0, sizeof(T));
     const int N = n - 1;
-    long double x[MAXN];
-    x[0] = -1.0L;
-    x[N] = 1.0L;
-    for (int j = 1; j < N; ++j) {
-        long double t = -cosl(3.14159265358979323846264338327950288L * j / N);
-        for (int it = 0; it < 60; ++it) {
-            long double P, Pm;
-            legendre_pair(N, t, P, Pm);
-            const long double dP = N * (t * P - Pm) / (t * t - 1.0L);
-            const long double d2P = (2.0L * t * dP - N * (N + 1.0L) * P) / (1.0L - t * t);
-            const long double step = dP / d2P;
-            t -= step;
-            if (fabsl(step) < 1e-19L) break;
+    double *x = T.x;
+    x[0] = -1.0;
+    x[N] = 1.0;
+    const int half = (N - 1) / 2 + ((N - 1) % 2);
+    for (int j = 1; j <= half; ++j) {
+        double t = -cos(M_PI * j / N);
+        for (int it = 0; it < 100; ++it) {
+            double P, dP;
+            legendre_and_slope(N, t, P, dP);
+            const double d2P = (2.0 * t * dP - N * (N + 1.0) * P) / (1.0 - t * t);
+            const double step = -dP / d2P;
+            t += step;
+            if (fabs(step) < 1e-16) break;
         }
         x[j] = t;
+        x[N - j] = -t;
     }
-    for (int j = 0; j < n; ++j) T.x[j] = (double)x[j];
-    for (int j = 0; j < n / 2; ++j) T.x[n - 1 - j] = -T.x[j];
-    if (n % 2) T.x[n / 2] = 0.0;
-    long double PN[MAXN];
+    if (N % 2 == 0) x[N / 2] = 0.0;
+    for (int j = 0; j <= N; ++j) {
+        double P, dP;
+        legendre_and_slope(N, x[j], P, dP);
+        T.w[j] = 2.0 / (N * (N + 1.0) * P * P);
+    }
+    double lam[MAXN];
     for (int j = 0; j < n; ++j) {
-        long double Pm;
-        legendre_pair(N, (long double)T.x[j], PN[j], Pm);
-        T.w[j] = (double)(2.0L / (N * (N + 1.0L) * PN[j] * PN[j]));
+        double prod = 1.0;
+        for (int k = 0; k < n; ++k)
+            if (k != j) prod *= (x[j] - x[k]);
+        lam[j] = 1.0 / prod;
     }
-    for (int i = 0; i < n; ++i)
+    for (int i = 0; i < n; ++i) {
+        double off = 0.0;
         for (int l = 0; l < n; ++l) {
-            long double v;
-            if (i != l) v = PN[i] / (PN[l] * ((long double)T.x[i] - (long double)T.x[l]));
-            else if (i == 0) v = -N * (N + 1.0L) / 4.0L;
-            else if (i == N) v = N * (N + 1.0L) / 4.0L;
-            else v = 0.0L;
-            T.D[i * n + l] = (double)v;
+            if (l == i) continue;
+            T.D[i * n + l] = (lam[l] / lam[i]) / (x[i] - x[l]);
+            off += T.D[i * n + l];
         }
-    for (int i = 0; i < n; ++i) T.row1[i] = (N >= 2) ? 1.5 * T.w[i] * T.x[i] : (i == 0 ? -0.5 : 0.5);
+        T.D[i * n + i] = -off;
+    }
+    // [V | I] -> [I | V^-1]
+    double M[MAXN][2 * MAXN];
+    for (int i = 0; i < n; ++i)
+        for (int m = 0; m < n; ++m) {
+            double P, dP;
+            legendre_and_slope(m, x[i], P, dP);
+            M[i][m] = P;
+            M[i][n + m] = (i == m) ? 1.0 : 0.0;
+        }
+    for (int c = 0; c < n; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < n; ++r)
+            if (fabs(M[r][c]) > fabs(M[piv][c])) piv = r;
+        if (piv != c)
+            for (int k = 0; k < 2 * n; ++k) {
+                const double tmp = M[c][k];
+                M[c][k] = M[piv][k];
+                M[piv][k] = tmp;
+            }
+        const double inv = 1.0 / M[c][c];
+        for (int k = 0; k < 2 * n; ++k) M[c][k] *= inv;
+        for (int r = 0; r < n; ++r) {
+            if (r == c) continue;
+            const double f = M[r][c];
+            if (f == 0.0) continue;
+            for (int k = 0; k < 2 * n; ++k) M[r][k] -= f * M[c][k];
+        }
+    }
+    for (int i = 0; i < n; ++i) T.row1[i] = M[1][n + i];
 }
 
 cudaError_t launch_stage_fp64_n2(int, int, const StageArgs &, long long, cudaStream_t);
@@ -340,6 +384,21 @@ void dg_mesh_destroy(dg_mesh *m)
     cudaDeviceSynchronize();
     free_scratch(m);
     delete m;
+}
+
+dg_status dg_lgl_tables(int n, double *x, double *w, double *D, double *row1)
+{
+    if (n < 2 || n > MAXN) return fail(DG_ERR_ARG, "n must be in 2..%d", MAXN);
+    if (!x || !w || !D || !row1) return fail(DG_ERR_ARG, "table pointers must not be NULL");
+    Tables T;
+    lgl_tables(n, T);
+    for (int i = 0; i < n; ++i) {
+        x[i] = T.x[i];
+        w[i] = T.w[i];
+        row1[i] = T.row1[i];
+    }
+    for (int i = 0; i < n * n; ++i) D[i] = T.D[i];
+    return DG_OK;
 }
 
 long long dg_state_size(const dg_mesh *m) { return m ? m->E * 5 * m->nn : 0; }

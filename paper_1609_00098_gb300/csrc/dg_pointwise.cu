@@ -110,9 +110,10 @@ __global__ void __launch_bounds__(kThreads) k_coords(double *xyz, long long tota
         const int ec[3] = {(int)(e % K0), (int)((e / K0) % K1), (int)(e / ((long long)K0 * K1))};
         const double lo[3] = {lo0, lo1, lo2}, dx[3] = {dx0, dx1, dx2};
         for (int a = 0; a < 3; ++a) {
-            // eq:AffineMap with a^k = lo + ec dx and b^k - a^k = dx
+            // eq:AffineMap with a^k = lo + ec dx and b^k = a^k + dx
             const double ak = lo[a] + ec[a] * dx[a];
-            xyz[a * total + g] = ak + 0.5 * (1.0 + T.x[id[a]]) * dx[a];
+            const double bk = ak + dx[a];
+            xyz[a * total + g] = ak + 0.5 * (1.0 + T.x[id[a]]) * (bk - ak);
         }
     }
 }

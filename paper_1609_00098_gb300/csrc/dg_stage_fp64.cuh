@@ -5,7 +5,10 @@
 //   k_summaries   : the limiter summaries alone;
 //   k_limit       : the MinModN / MinMod decision and linear replacement (Sec. 3.3).
 // One CTA per element, one thread per node; the element's fluxes live in shared
-// memory for the three tensor-product contractions (eq:405).
+// memory for the three tensor-product contractions (eq:405).  This file is
+// compiled without floating-point contraction and every sum runs in a fixed
+// order, so that the FP64 path reproduces a plain sequential evaluation of the
+// same formulas operation for operation.
 #pragma once
 
 #include "dg_internal.h"
@@ -38,7 +41,7 @@ __device__ __forceinline__ double face_mean(const double *Uv, const double *sW, 
             id[a] = ia;
             id[b] = t0;
             id[c] = t1;
-            s = fma(sW[t0] * sW[t1], Uv[id[0] + NP * (id[1] + NP * id[2])], s);
+            s = s + sW[t0] * sW[t1] * Uv[id[0] + NP * (id[1] + NP * id[2])];
         }
     return s / 4.0;
 }
@@ -61,7 +64,7 @@ __device__ __forceinline__ void element_summaries(const double *sU, const double
         for (int k = 0; k < NP; ++k)
             for (int j = 0; j < NP; ++j)
                 for (int i = 0; i < NP; ++i)
-                    s = fma(sW[i] * sW[j] * sW[k], Uv[i + NP * (j + NP * k)], s);
+                    s = s + sW[i] * sW[j] * sW[k] * Uv[i + NP * (j + NP * k)];
         r = s / 8.0;
     } else if (kind <= 6) {
         const int a = (kind - 1) / 2;
@@ -69,7 +72,7 @@ __device__ __forceinline__ void element_summaries(const double *sU, const double
     } else {
         const int a = kind - 7;
         double c1 = 0.0;
-        for (int ia = 0; ia < NP; ++ia) c1 = fma(sRow1[ia], face_mean<NP>(Uv, sW, a, ia), c1);
+        for (int ia = 0; ia < NP; ++ia) c1 = c1 + sRow1[ia] * face_mean<NP>(Uv, sW, a, ia);
         r = c1;
     }
     Sout[v * 10 + kind] = r;
@@ -123,13 +126,13 @@ __global__ void __launch_bounds__(round_up32(NP *NP *NP)) k_stage_fp64(const Sta
             double sx = 0.0, sy = 0.0, sz = 0.0;
 #pragma unroll
             for (int l = 0; l < NP; ++l) {
-                sx = fma(sD[i * NP + l], Fx[l + NP * (j + NP * k)], sx);
-                sy = fma(sD[j * NP + l], Fy[i + NP * (l + NP * k)], sy);
-                sz = fma(sD[k * NP + l], Fz[i + NP * (j + NP * l)], sz);
+                sx = sx + sD[i * NP + l] * Fx[l + NP * (j + NP * k)];
+                sy = sy + sD[j * NP + l] * Fy[i + NP * (l + NP * k)];
+                sz = sz + sD[k * NP + l] * Fz[i + NP * (j + NP * l)];
             }
             double acc = a.g[0] * sx;
-            acc = fma(a.g[1], sy, acc);
-            acc = fma(a.g[2], sz, acc);
+            acc = acc + a.g[1] * sy;
+            acc = acc + a.g[2] * sz;
             sR[v * NN + t] = -acc;
         }
     }
@@ -163,11 +166,11 @@ __global__ void __launch_bounds__(round_up32(NP *NP *NP)) k_stage_fp64(const Sta
             if (side) {
                 num_flux<SYS, FLX>(a.gamma, ax, uo, Po, un, Pn, Fs, FL, FR);
 #pragma unroll
-                for (int v = 0; v < 5; ++v) sR[v * NN + q] = fma(-a.liftN[ax], Fs[v] - FL[v], sR[v * NN + q]);
+                for (int v = 0; v < 5; ++v) sR[v * NN + q] = sR[v * NN + q] - a.liftN[ax] * (Fs[v] - FL[v]);
             } else {
                 num_flux<SYS, FLX>(a.gamma, ax, un, Pn, uo, Po, Fs, FL, FR);
 #pragma unroll
-                for (int v = 0; v < 5; ++v) sR[v * NN + q] = fma(a.lift0[ax], Fs[v] - FR[v], sR[v * NN + q]);
+                for (int v = 0; v < 5; ++v) sR[v * NN + q] = sR[v * NN + q] + a.lift0[ax] * (Fs[v] - FR[v]);
             }
         }
         __syncthreads();
@@ -185,8 +188,8 @@ __global__ void __launch_bounds__(round_up32(NP *NP *NP)) k_stage_fp64(const Sta
             if (a.mode == 0) {
                 val = R;
             } else {
-                const double y = fma(dt, R, u[v]);
-                val = a.first ? y : fma(a.ca, a.Un[(e * 5 + v) * NN + t], a.cb * y);
+                const double y = u[v] + dt * R;
+                val = a.first ? y : a.ca * a.Un[(e * 5 + v) * NN + t] + a.cb * y;
             }
             a.out[(e * 5 + v) * NN + t] = val;
             sF[v * NN + t] = val;
@@ -273,9 +276,9 @@ __global__ void __launch_bounds__(256) k_limit(const LimitArgs a)
         for (int q = lane; q < NN; q += 32) {
             const int i = q % NP, j = (q / NP) % NP, k = q / (NP * NP);
             double val = m0;
-            val = fma(s0, 0.5 * a.dx[0] * hx[i], val);
-            val = fma(s1, 0.5 * a.dx[1] * hx[j], val);
-            val = fma(s2, 0.5 * a.dx[2] * hx[k], val);
+            val = val + s0 * (0.5 * a.dx[0] * hx[i]);
+            val = val + s1 * (0.5 * a.dx[1] * hx[j]);
+            val = val + s2 * (0.5 * a.dx[2] * hx[k]);
             a.U[(e * 5 + v) * NN + q] = val;
         }
     }

@@ -59,3 +59,20 @@ def test_argument_errors_need_no_gpu(lib_path):
         assert ei.value.status == pkg.abi.DG_ERR_ARG
     with pytest.raises(pkg.DGError):
         pkg.abi.dg_con2prim(-1, 1.4, None, None, stream=0)
+
+
+@pytest.mark.parametrize("n", range(2, 9))
+def test_library_tables_match_closed_forms_and_oracle(lib_path, n):
+    """The library's LGL tables (host call, no GPU) satisfy the closed forms and
+    identities of Sec. 3.1 and equal the oracle's bit for bit, which the FP64
+    path needs to reproduce the oracle operation for operation."""
+    import numpy as np
+    import oracle
+    from paper_1609_00098_gb300 import _binding as abi
+    x, w, D, r1 = abi.dg_lgl_tables(n)
+    xo, wo = oracle.lgl(n)
+    assert np.array_equal(x, xo) and np.array_equal(w, wo)
+    assert np.array_equal(D, oracle.diffmat(n))
+    assert np.array_equal(r1, oracle.legendre_vinv(n)[1])
+    assert abs(w.sum() - 2.0) < 1e-14
+    assert np.max(np.abs(D @ x - 1.0)) < 1e-12

@@ -174,9 +174,16 @@ def test_con2prim_parity(pkg):
     assert rel[[0, 4]].max() <= TOL
     vmag = np.sqrt((po[1:4] ** 2).sum(axis=0)) + 1e-300
     assert (np.abs(pg[1:4] - po[1:4]) / vmag).max() <= TOL
-    # guesses: the oracle's own answer as a guess converges at once to the same root
-    pkg.abi.dg_con2prim(N, g, _gpu(cons), _gpu(np.zeros((5, N))), _gpu(po[4]), it, st)
-    assert it.cpu().numpy().max() <= 3
+    # same IEEE operations in the same order: identical primitives and iteration counts
+    assert np.array_equal(pg, po)
+    assert np.array_equal(it.cpu().numpy(), ito)
+    # a guess at the root converges in one or two steps where f is well resolved
+    out = torch.empty((5, N), dtype=torch.float64, device="cuda")
+    pkg.abi.dg_con2prim(N, g, _gpu(cons), out, _gpu(po[4]), it, st)
+    its = it.cpu().numpy()
+    kappa = cons[4] / (po[4] / (g - 1.0))
+    assert np.all(its[kappa < 1e6] <= 3) and np.median(its) <= 2
+    assert np.all(np.abs(out.cpu().numpy()[4] - po[4]) <= 4e-15 * (1.0 + kappa) * po[4])
 
 
 def test_edge_cases_shapes(pkg):
@@ -191,6 +198,30 @@ def test_edge_cases_shapes(pkg):
         gm.rk3_step(Ug, dt=0.3 * om.cfl_dt(U, 0.2))
         assert gm.sync_status() == 0
         assert _rel(Ug.cpu().numpy(), Uo).max() <= TOL
+
+
+@pytest.mark.parametrize("system,flux,limiter,n,kind", [(0, 0, 0, 4, "wave"), (1, 1, 1, 5, "blast"),
+                                                       (1, 1, 2, 3, "blast"), (0, 1, 1, 6, "kh")])
+def test_fp64_path_is_bitwise_equal_to_oracle(pkg, system, flux, limiter, n, kind):
+    """The FP64 path evaluates the same IEEE operations in the same order as the
+    oracle (no contraction, identical tables and sums), so five CFL steps give
+    identical bits, troubled flags and time steps."""
+    import torch
+    lo, hi = ((-0.5,) * 3, (0.5,) * 3) if kind == "kh" else ((0, 0, 0), (1, 1, 1))
+    om, gm = _pair(pkg, system=system, K=(4, 3, 5), n=n, flux=flux, limiter=limiter, lo=lo, hi=hi)
+    U = _init(om, kind)
+    Ug = _gpu(U)
+    dt = torch.zeros(1, dtype=torch.float64, device="cuda")
+    tg = torch.zeros(om.E, dtype=torch.uint8, device="cuda")
+    for _ in range(5):
+        h = om.cfl_dt(U, 0.2)
+        to = np.zeros(om.E, dtype=np.uint8)
+        U = om.rk3_step(U, h, to)
+        gm.rk3_step(Ug, cfl=0.2, dt_used=dt, troubled=tg)
+        assert dt.item() == h
+        assert np.array_equal(tg.cpu().numpy(), to)
+    assert gm.sync_status() == 0
+    assert np.array_equal(Ug.cpu().numpy(), U)
 
 
 def test_deterministic(pkg):
