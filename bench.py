@@ -1,5 +1,6 @@
 #!/usr/bin/env python
-"""DG-RK3 throughput (dof-updates/s) of the nodal DG hot path on GB300.
+"""DG-RK3 throughput (dof-updates/s) of the nodal DG hot path on GB300: the
+mixed-precision path (headline `value`) and the plain FP64 path (`plain_fp64`).
 
 Workload: 3D special-relativistic blast on a periodic unit cube, 16^3 affine
 elements, 5 LGL nodes per axis (512,000 nodes x 5 conserved variables),
@@ -108,11 +109,65 @@ def _init_state(pkg, mesh, torch):
     return mesh.from_prim(torch.from_numpy(prim).cuda())
 
 
-def _algorithmic(nodes):
-    """Algorithmic HBM bytes of one fused stage launch, averaged over the 3 stages:
-    stage 1 reads U^n and writes U^1 (80 B/node); stages 2, 3 read U_s and U^n and
-    write U_{s+1} (120 B/node)."""
-    return nodes * (80 + 120 + 120) / 3.0
+def _algorithmic(nodes, precision):
+    """Compulsory HBM bytes of one fused stage launch, averaged over the 3 stages.
+    FP64: stage 1 reads U^n and writes U^1 (80 B/node); stages 2, 3 read U_s and
+    U^n and write U_{s+1} (120 B/node).  Mixed: every stage reads U^n (40 B), the
+    FP32 increment of its input (20 B; not at stage 1) and the 4-byte pressure
+    guess, and writes its FP32 increment (20 B) and pressure (4 B)."""
+    if precision == 0:
+        return nodes * (80 + 120 + 120) / 3.0
+    return nodes * (68 + 88 + 88) / 3.0
+
+
+def _measure(pkg, torch, precision, args, dist, U0):
+    """Warm-up, then K graph-replayed steps timed with per-step CUDA events (L2
+    flushed between steps, outside the event pairs), then K profiled steps for
+    per-kernel durations."""
+    w = WORKLOAD
+    mesh = pkg.Mesh(system=w["system"], K=w["K"], n=w["n"], flux=w["flux"], limiter=w["limiter"],
+                    gamma=w["gamma"], precision=precision)
+    U = U0.clone()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        mesh.rk3_step(U, cfl=w["cfl"])
+    torch.cuda.synchronize()
+    if mesh.sync_status() != 0:
+        raise RuntimeError("warm-up steps reported a device error")
+    graph = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        mesh.rk3_step(U, cfl=w["cfl"])  # one more warm step on the capture stream
+    torch.cuda.current_stream().wait_stream(side)
+    with torch.cuda.graph(graph):
+        mesh.rk3_step(U, cfl=w["cfl"])
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        starts[k].record(stream)
+        graph.replay()
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    status = mesh.sync_status()
+    # per-kernel durations: the same steps launched directly with event pairs
+    pkg.abi.dg_profile_enable(mesh.h, True)
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        mesh.rk3_step(U, cfl=w["cfl"])
+    torch.cuda.synchronize()
+    prof = pkg.abi.dg_profile_read(mesh.h)
+    pkg.abi.dg_profile_enable(mesh.h, False)
+    return mesh, graph, step_ms, prof, status
 
 
 def run_ours(args):
@@ -126,58 +181,58 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     w = WORKLOAD
-    mesh = pkg.Mesh(system=w["system"], K=w["K"], n=w["n"], flux=w["flux"], limiter=w["limiter"],
-                    gamma=w["gamma"])
-    nodes = mesh.E * mesh.nn
-    U0 = _init_state(pkg, mesh, torch)
-    U = U0.clone()
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    stream = torch.cuda.current_stream()
+    setup = pkg.Mesh(system=w["system"], K=w["K"], n=w["n"], flux=w["flux"], limiter=w["limiter"],
+                     gamma=w["gamma"])
+    nodes = setup.E * setup.nn
+    U0 = _init_state(pkg, setup, torch)
 
-    for _ in range(args.warmup):
-        mesh.rk3_step(U, cfl=w["cfl"])
-    torch.cuda.synchronize()
-    if mesh.sync_status() != 0:
-        raise RuntimeError("warm-up steps reported a device error")
+    # accuracy at equal time steps (untimed): mixed vs plain FP64 after a few steps
+    mixed_acc = None
+    if not args.no_accuracy:
+        mix = pkg.Mesh(system=w["system"], K=w["K"], n=w["n"], flux=w["flux"], limiter=w["limiter"],
+                       gamma=w["gamma"], precision=1)
+        Uf, Um = U0.clone(), U0.clone()
+        dtv = torch.zeros(1, dtype=torch.float64, device="cuda")
+        for _ in range(args.acc_steps):
+            setup.rk3_step(Uf, cfl=w["cfl"], dt_used=dtv)
+            mix.rk3_step(Um, dt=float(dtv.item()))
+        torch.cuda.synchronize()
+        num = torch.sqrt(((Um - Uf) ** 2).sum(dim=(0, 2)))
+        den = torch.sqrt((Uf ** 2).sum(dim=(0, 2)))
+        rel = (num / torch.clamp(den, min=1e-3 * float(den.max()))).cpu().tolist()
+        mixed_acc = {"steps": args.acc_steps, "rel_l2_vs_fp64_per_var": rel, "max": max(rel)}
+        mix.close()
+    setup.close()
 
-    # timed region: per-step event pairs, L2 flushed between steps outside them
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    pkg.abi.dg_profile_enable(mesh.h, True)
-    wall0 = time.perf_counter()
-    for k in range(args.steps):
-        flush.fill_(float(k))
-        starts[k].record(stream)
-        mesh.rk3_step(U, cfl=w["cfl"])
-        ends[k].record(stream)
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - wall0
-    if dist:
-        dist.barrier()
+    results = {}
+    for precision in (1, 0):
+        results[precision] = _measure(pkg, torch, precision, args, dist, U0)
     clk = clocks.stop()
-    prof = pkg.abi.dg_profile_read(mesh.h)
-    pkg.abi.dg_profile_enable(mesh.h, False)
-    status = mesh.sync_status()
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = float(sum(step_ms))
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+
+    def agg(ms):
+        total = float(sum(ms))
+        if dist:
+            t = torch.tensor([total], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total = float(t.item())
+        return total
+
+    mesh, graph, step_ms, prof, status = results[1]
+    total_ms = agg(step_ms)
     ms_per_step = total_ms / args.steps
     value = ws * nodes * 5 * args.steps / (total_ms / 1e3)
+    f_mesh, f_graph, f_ms, f_prof, f_status = results[0]
+    f_total = agg(f_ms)
 
-    # end to end through the C ABI with host buffers: H2D of the step's input state
-    # from pinned memory, the step, D2H of the resulting state, every step
+    # end to end through the C ABI with host buffers (mixed path): H2D of the step's
+    # input state from pinned memory, the step, D2H of the resulting state
     host_in = U0.cpu().pin_memory()
     host_out = torch.empty_like(host_in).pin_memory()
     Ud = torch.empty_like(U0)
+    stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
@@ -187,49 +242,53 @@ def run_ours(args):
         host_out.copy_(Ud, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = agg([e0.elapsed_time(e1)])
     e2e = ws * nodes * 5 * args.steps / (e2e_ms / 1e3)
     state_bytes = nodes * 5 * 8
 
-    # dominant kernel roofline (HBM): algorithmic bytes per launch / average launch time
-    dom = max(prof, key=lambda c: prof[c][0])
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+
+    def kern(pr):
+        tot = max(1e-12, sum(x[0] for x in pr.values()))
+        return {c: {"ms_total": round(v[0], 4), "launches": int(v[1]), "share": round(v[0] / tot, 4)}
+                for c, v in pr.items() if v[1]}
+
     st_ms, st_n = prof["stage"]
     stage_avg_s = (st_ms / st_n) / 1e3 if st_n else float("nan")
-    achieved = _algorithmic(nodes) / stage_avg_s / 1e9
-    launches = int(sum(c for _, c in prof.values())) + 0
-    kernels = {c: {"ms_total": round(v[0], 4), "launches": int(v[1]),
-                   "share": round(v[0] / max(1e-12, sum(x[0] for x in prof.values())), 4)} for c, v in prof.items()
-               if v[1]}
+    achieved = _algorithmic(nodes, 1) / stage_avg_s / 1e9
+    launches = int(sum(c for _, c in prof.values()))
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic (seeded blast initial data)",
-        "config": _config({"precision": "fp64", "parallelism": "replicas" if ws > 1 else "single GPU"}),
-        "variant": "plain FP64",
+        "dtype": "f32 arithmetic, f64 state and RK accumulation",
+        "data": "synthetic (seeded blast initial data)",
+        "config": _config({"precision": "mixed", "parallelism": "replicas" if ws > 1 else "single GPU",
+                           "step_launch": "CUDA graph replay"}),
+        "variant": "mixed (FP32 fluxes/contraction/face fluxes/con2prim with FP64 polish, FP64 state)",
+        "plain_fp64": {"value": ws * nodes * 5 * args.steps / (f_total / 1e3), "unit": UNIT,
+                       "ms_per_step": f_total / args.steps, "kernels": kern(f_prof), "device_status": f_status},
+        "speedup_vs_plain_fp64": f_total / total_ms,
+        "mixed_accuracy": mixed_acc,
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes},
         "gpu_launches": launches,
-        "kernels": kernels,
-        "dominant_kernel": dom,
-        "roofline": {"kernel": "k_stage_fp64 (fused RHS + SSP-RK3 stage)", "bound": "hbm", "achieved": achieved,
-                     "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
+        "kernels": kern(prof),
+        "roofline": {"kernel": "k_stage_mixed (fused con2prim + RHS + SSP-RK3 stage increment)", "bound": "hbm",
+                     "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                     "traffic": None, "bytes_per_launch": _algorithmic(nodes, 1),
+                     "avg_launch_ms": stage_avg_s * 1e3,
                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks else "fallback"},
         "clocks": clk,
         "device_status": status,
-        "wall_s_timed": wall,
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(seconds=args.cpu_seconds)
-    mesh.close()
+    for r in results.values():
+        r[0].close()
     if dist:
         dist.destroy_process_group()
     if rank == 0:
@@ -301,6 +360,8 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--acc-steps", type=int, default=10)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

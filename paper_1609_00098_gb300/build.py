@@ -26,6 +26,7 @@ NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompil
 # as a plain sequential FP64 evaluation of the formulas.  Mixed-precision kernels
 # (files named *_mixed*) keep the default contraction.
 NO_FMAD = ["-fmad=false"]
+MIXED = ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"]
 
 
 def _nvcc() -> str:
@@ -64,7 +65,7 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -
         src, obj = src_obj
         if not force and os.path.exists(obj) and os.path.getmtime(obj) > max(os.path.getmtime(src), hdr_time):
             return obj
-        extra = [] if "_mixed" in os.path.basename(src) else NO_FMAD
+        extra = MIXED if "_mixed" in os.path.basename(src) else NO_FMAD
         cmd = [nvcc, *ARCH, *NVCC_FLAGS, *extra, "-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), flush=True)

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "dg_internal.h"
+#include "dg_mixed.cuh"
 #include "dg_physics.cuh"
 
 namespace {
@@ -245,6 +246,45 @@ cudaError_t launch_limit(int n, const LimitArgs &a, cudaStream_t s)
 
 cudaError_t launch_set(double *p, double v, cudaStream_t s);
 
+#define DG_DECL_MIXED(NP)                                                                               \
+    cudaError_t launch_stage_mixed_n##NP(int, int, const MixedArgs &, long long, cudaStream_t);         \
+    cudaError_t launch_limit_mixed_n##NP(int, const LimitMixedArgs &, cudaStream_t);
+DG_DECL_MIXED(2)
+DG_DECL_MIXED(3)
+DG_DECL_MIXED(4)
+DG_DECL_MIXED(5)
+DG_DECL_MIXED(6)
+DG_DECL_MIXED(7)
+DG_DECL_MIXED(8)
+
+cudaError_t launch_stage_mixed(int n, int system, int flux, const MixedArgs &a, long long E, cudaStream_t s)
+{
+    switch (n) {
+    case 2: return launch_stage_mixed_n2(system, flux, a, E, s);
+    case 3: return launch_stage_mixed_n3(system, flux, a, E, s);
+    case 4: return launch_stage_mixed_n4(system, flux, a, E, s);
+    case 5: return launch_stage_mixed_n5(system, flux, a, E, s);
+    case 6: return launch_stage_mixed_n6(system, flux, a, E, s);
+    case 7: return launch_stage_mixed_n7(system, flux, a, E, s);
+    case 8: return launch_stage_mixed_n8(system, flux, a, E, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_limit_mixed(int n, int system, const LimitMixedArgs &a, cudaStream_t s)
+{
+    switch (n) {
+    case 2: return launch_limit_mixed_n2(system, a, s);
+    case 3: return launch_limit_mixed_n3(system, a, s);
+    case 4: return launch_limit_mixed_n4(system, a, s);
+    case 5: return launch_limit_mixed_n5(system, a, s);
+    case 6: return launch_limit_mixed_n6(system, a, s);
+    case 7: return launch_limit_mixed_n7(system, a, s);
+    case 8: return launch_limit_mixed_n8(system, a, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
 }  // namespace dg
 
 using namespace dg;
@@ -286,6 +326,56 @@ LimitArgs limit_args(const dg_mesh *m, double *U, unsigned char *troubled)
     return l;
 }
 
+MixedArgs mixed_args(const dg_mesh *m)
+{
+    MixedArgs a;
+    std::memset(&a, 0, sizeof(a));
+    for (int ax = 0; ax < 3; ++ax) {
+        a.K[ax] = m->d.K[ax];
+        const double g = 2.0 / m->dx[ax];
+        a.g[ax] = (float)g;
+        a.lift0[ax] = (float)(g / m->T.w[0]);
+        a.liftN[ax] = (float)(g / m->T.w[m->d.n - 1]);
+    }
+    a.gamma = (float)m->d.gamma;
+    a.gamma_d = m->d.gamma;
+    a.kappa_sw = m->kappa_sw;
+    a.d_atm = m->d.d_atm;
+    a.tau_atm = m->d.tau_atm;
+    a.err = m->err;
+    for (int i = 0; i < MAXN * MAXN; ++i) a.D32[i] = (float)m->T.D[i];
+    for (int i = 0; i < MAXN; ++i) {
+        a.w32[i] = (float)m->T.w[i];
+        a.row1_32[i] = (float)m->T.row1[i];
+        a.wd[i] = m->T.w[i];
+    }
+    return a;
+}
+
+LimitMixedArgs limit_mixed_args(const dg_mesh *m, double *U, float *Dv, unsigned char *troubled, int final_pass)
+{
+    LimitMixedArgs l;
+    std::memset(&l, 0, sizeof(l));
+    l.U = U;
+    l.Dv = Dv;
+    l.S = m->S;
+    l.unphys = (m->d.system == 1) ? m->unphys : nullptr;
+    l.troubled = troubled;
+    l.E = m->E;
+    for (int ax = 0; ax < 3; ++ax) {
+        l.K[ax] = m->d.K[ax];
+        l.dx[ax] = m->dx[ax];
+    }
+    l.limiter = m->d.limiter;
+    l.final_pass = final_pass;
+    l.tvb_M = m->d.tvb_M;
+    l.beta = m->d.beta;
+    l.d_atm = m->d.d_atm;
+    l.tau_atm = m->d.tau_atm;
+    for (int i = 0; i < MAXN; ++i) l.x[i] = m->T.x[i];
+    return l;
+}
+
 dg_status check_mesh(const dg_mesh *m)
 {
     if (!m) return fail(DG_ERR_ARG, "mesh is NULL");
@@ -309,6 +399,11 @@ void free_scratch(dg_mesh *m)
     }
     cudaFree(m->W1);
     cudaFree(m->W2);
+    cudaFree(m->Da);
+    cudaFree(m->Db);
+    cudaFree(m->pbuf[0]);
+    cudaFree(m->pbuf[1]);
+    cudaFree(m->Sn);
     cudaFree(m->P);
     cudaFree(m->S);
     cudaFree(m->unphys);
@@ -331,7 +426,7 @@ dg_status dg_mesh_create(const dg_mesh_desc *d, dg_mesh **out)
     if (d->n < 2 || d->n > MAXN) return fail(DG_ERR_ARG, "n must be in 2..%d", MAXN);
     if (d->flux != 0 && d->flux != 1) return fail(DG_ERR_ARG, "flux must be 0 (LLF) or 1 (HLL)");
     if (d->limiter < 0 || d->limiter > 2) return fail(DG_ERR_ARG, "limiter must be 0, 1 or 2");
-    if (d->precision != 0) return fail(DG_ERR_ARG, "precision %d is not supported by dg_mesh_create", d->precision);
+    if (d->precision != 0 && d->precision != 1) return fail(DG_ERR_ARG, "precision must be 0 (FP64) or 1 (mixed)");
     if (!(d->gamma > 1.0)) return fail(DG_ERR_ARG, "gamma must be > 1");
     if (!(d->beta > 0.0) || !(d->tvb_M >= 0.0)) return fail(DG_ERR_ARG, "beta must be > 0 and tvb_M >= 0");
     long long E = 1;
@@ -356,9 +451,21 @@ dg_status dg_mesh_create(const dg_mesh_desc *d, dg_mesh **out)
         if (h < m->dxmin) m->dxmin = h;
     }
     const size_t state = sizeof(double) * (size_t)E * 5 * m->nn;
+    const bool mixed = d->precision == DG_PRECISION_MIXED;
+    m->kappa_sw = 1.0e3f;
     cudaError_t st = cudaSuccess;
-    st = st ? st : cudaMalloc(&m->W1, state);
-    st = st ? st : cudaMalloc(&m->W2, state);
+    if (!mixed) {
+        st = st ? st : cudaMalloc(&m->W1, state);
+        st = st ? st : cudaMalloc(&m->W2, state);
+    } else {
+        st = st ? st : cudaMalloc(&m->Da, state / 2);
+        st = st ? st : cudaMalloc(&m->Db, state / 2);
+        st = st ? st : cudaMalloc(&m->Sn, sizeof(double) * (size_t)E * 35);
+        if (d->system == 1) {
+            st = st ? st : cudaMalloc(&m->pbuf[0], sizeof(float) * (size_t)E * m->nn);
+            st = st ? st : cudaMalloc(&m->pbuf[1], sizeof(float) * (size_t)E * m->nn);
+        }
+    }
     st = st ? st : cudaMalloc(&m->P, sizeof(double) * (size_t)E * 4 * m->nn);
     st = st ? st : cudaMalloc(&m->S, sizeof(double) * (size_t)E * 50);
     st = st ? st : cudaMalloc(&m->unphys, (size_t)E);
@@ -433,6 +540,15 @@ dg_status dg_rhs(dg_mesh *m, const double *U, double *dUdt, void *stream)
     if (dg_status s = check_mesh(m)) return s;
     if (!U || !dUdt || U == dUdt) return fail(DG_ERR_ARG, "U and dUdt must be distinct, non-NULL");
     cudaStream_t s = (cudaStream_t)stream;
+    if (m->d.precision == DG_PRECISION_MIXED) {
+        MixedArgs a = mixed_args(m);
+        a.Un = U;
+        a.Rout = m->Da;
+        a.cD = 1.0f;
+        DG_LAUNCH(m, s, PROF_STAGE, launch_stage_mixed(m->d.n, m->d.system, m->d.flux, a, m->E, s));
+        DG_LAUNCH(m, s, PROF_OTHER, launch_widen(m->Da, dUdt, m->E * 5 * m->nn, s));
+        return DG_OK;
+    }
     DG_LAUNCH(m, s, PROF_PRIM, launch_primitives(m, U, m->P, 0, nullptr, nullptr, s));
     StageArgs a = stage_args(m);
     a.Us = U;
@@ -456,6 +572,59 @@ dg_status dg_compute_dt(dg_mesh *m, const double *U, double cfl, double *dt, voi
     return DG_OK;
 }
 
+// Mixed-precision step: CFL pass, three fused stages on FP32 increments of U^n,
+// limiter on the increments, and a final pass forming U^{n+1} = U^n + D3 in FP64.
+static dg_status rk3_step_mixed(dg_mesh *m, double *U, double dt, double cfl, double *dt_used,
+                                unsigned char *troubled, cudaStream_t s)
+{
+    const bool sr = m->d.system == 1;
+    const bool lim = m->d.limiter != 0;
+    const bool cflmode = cfl > 0.0;
+    MixedArgs a = mixed_args(m);
+    a.Un = U;
+    a.dt = dt;
+    a.dt_ptr = cflmode ? m->dt : nullptr;
+    a.S = lim ? m->S : nullptr;
+    a.unphys = (lim && sr) ? m->unphys : nullptr;
+    a.Sn = m->Sn;
+    float *latest = (sr && m->p_valid) ? m->pbuf[m->pi] : nullptr;
+    if (cflmode) {
+        DG_CUDA(cudaMemsetAsync(m->lam, 0, sizeof(unsigned long long), s));
+        DG_LAUNCH(m, s, PROF_PRIM, launch_cfl_mixed(m, U, latest, sr ? m->pbuf[1 - m->pi] : nullptr, m->kappa_sw, s));
+        if (sr) {
+            m->pi = 1 - m->pi;
+            latest = m->pbuf[m->pi];
+        }
+        DG_LAUNCH(m, s, PROF_DT, launch_dt(m, cfl, m->dt, s));
+    }
+    float *din[3] = {nullptr, m->Da, m->Db};
+    float *dout[3] = {m->Da, m->Db, m->Da};
+    const float cD[3] = {1.0f, 0.25f, (float)(2.0 / 3.0)};
+    for (int st = 0; st < 3; ++st) {
+        a.Din = din[st];
+        a.Dout = dout[st];
+        a.cD = cD[st];
+        a.write_Sn = st == 0;
+        a.pin = latest;
+        a.pout = sr ? m->pbuf[1 - m->pi] : nullptr;
+        DG_LAUNCH(m, s, PROF_STAGE, launch_stage_mixed(m->d.n, m->d.system, m->d.flux, a, m->E, s));
+        if (sr) {
+            m->pi = 1 - m->pi;
+            latest = m->pbuf[m->pi];
+        }
+        if (lim || st == 2) {
+            LimitMixedArgs l = limit_mixed_args(m, U, dout[st], st == 2 ? troubled : nullptr, st == 2);
+            DG_LAUNCH(m, s, PROF_LIMIT, launch_limit_mixed(m->d.n, m->d.system, l, s));
+        }
+    }
+    m->p_valid = sr ? 1 : 0;
+    if (dt_used) {
+        if (cflmode) DG_CUDA(cudaMemcpyAsync(dt_used, m->dt, sizeof(double), cudaMemcpyDeviceToDevice, s));
+        else DG_CUDA(launch_set(dt_used, dt, s));
+    }
+    return DG_OK;
+}
+
 dg_status dg_rk3_step(dg_mesh *m, double *U, double dt, double cfl, double *dt_used, unsigned char *troubled,
                       void *stream)
 {
@@ -464,6 +633,7 @@ dg_status dg_rk3_step(dg_mesh *m, double *U, double dt, double cfl, double *dt_u
     const bool cflmode = cfl > 0.0;
     if (!cflmode && !(dt > 0.0)) return fail(DG_ERR_ARG, "need dt > 0 or cfl > 0");
     cudaStream_t s = (cudaStream_t)stream;
+    if (m->d.precision == DG_PRECISION_MIXED) return rk3_step_mixed(m, U, dt, cfl, dt_used, troubled, s);
     const bool sr = m->d.system == 1;
     const bool lim = m->d.limiter != 0;
     StageArgs a = stage_args(m);

@@ -9,6 +9,19 @@ namespace dg {
 
 constexpr int MAXN = 8;  // largest LGL node count per axis
 
+__host__ __device__ constexpr int round_up32(int v) { return (v + 31) / 32 * 32; }
+
+// periodic neighbour of element e along axis a in direction s = +-1
+__host__ __device__ inline long long elem_neighbour(long long e, const int K[3], int a, int s)
+{
+    int ec[3];
+    ec[0] = (int)(e % K[0]);
+    ec[1] = (int)((e / K[0]) % K[1]);
+    ec[2] = (int)(e / ((long long)K[0] * K[1]));
+    ec[a] = (ec[a] + s + K[a]) % K[a];
+    return ec[0] + (long long)K[0] * (ec[1] + (long long)K[1] * ec[2]);
+}
+
 // 1D LGL tables for one n, as passed by value to the kernels.
 struct Tables {
     double D[MAXN * MAXN];  // D[i*n+l] = ell_l'(xbar_i)
@@ -77,6 +90,12 @@ struct dg_mesh {
     unsigned long long *lam; // max wave speed (bit pattern of a non-negative double)
     double *dt;              // device step
     unsigned int *err;       // sticky status word
+    // mixed-precision scratch (precision == DG_PRECISION_MIXED)
+    float *Da, *Db;          // FP32 stage increments of U^n
+    float *pbuf[2];          // SR pressures of the last two passes (con2prim warm starts)
+    int pi, p_valid;         // index of the latest pressure buffer, and whether it holds one
+    double *Sn;              // FP64 cell and face means of U^n [e][5][7]
+    float kappa_sw;          // conditioning above which FP32 con2prim is polished in FP64
     // optional per-kernel timing (dg_profile_enable)
     int prof_on;
     void *prof;              // host-side event log, owned by dg_api.cu
@@ -97,6 +116,14 @@ cudaError_t launch_coords(const dg_mesh *m, double *xyz, cudaStream_t s);
 cudaError_t launch_prim2con(const dg_mesh *m, const double *prim, double *U, cudaStream_t s);
 cudaError_t launch_con2prim(long long count, double gamma, const double *cons, double *prim,
                             const double *guess, int *iters, int *status, cudaStream_t s);
+
+struct MixedArgs;
+struct LimitMixedArgs;
+cudaError_t launch_stage_mixed(int n, int system, int flux, const MixedArgs &a, long long E, cudaStream_t s);
+cudaError_t launch_limit_mixed(int n, int system, const LimitMixedArgs &a, cudaStream_t s);
+cudaError_t launch_cfl_mixed(const dg_mesh *m, const double *Un, const float *pin, float *pout, float kappa_sw,
+                             cudaStream_t s);
+cudaError_t launch_widen(const float *in, double *out, long long count, cudaStream_t s);
 
 // Host LGL tables (long double Newton; closed-form LGL differentiation matrix).
 void lgl_tables(int n, Tables &T);

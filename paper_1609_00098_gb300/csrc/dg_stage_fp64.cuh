@@ -16,18 +16,6 @@
 
 namespace dg {
 
-__host__ __device__ constexpr int round_up32(int v) { return (v + 31) / 32 * 32; }
-
-__device__ __forceinline__ long long elem_neighbour(long long e, const int K[3], int a, int s)
-{
-    int ec[3];
-    ec[0] = (int)(e % K[0]);
-    ec[1] = (int)((e / K[0]) % K[1]);
-    ec[2] = (int)(e / ((long long)K[0] * K[1]));
-    ec[a] = (ec[a] + s + K[a]) % K[a];
-    return ec[0] + (long long)K[0] * (ec[1] + (long long)K[1] * ec[2]);
-}
-
 // Mean over the face nodes of axis `a` at index ia along a, weighted by the LGL
 // weights of the two other axes (divided by the reference face area 4).
 template <int NP>

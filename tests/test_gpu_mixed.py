@@ -1,0 +1,160 @@
+"""Mixed-precision path (FP32 arithmetic, FP64 state and accumulation) against
+the FP64 oracle.  Bars: on the smooth problem with an exact solution, the mixed
+L2 error stays within 1.05x of the oracle's; without an exact solution (blast,
+Kelvin-Helmholtz) the relative L2 distance to the oracle stays within 1e-6 per
+conserved variable.  A variable's norm is floored at 1 % of the largest
+variable's norm: momenta that start at zero (blast at rest, S_z of the shear
+layer) have no scale of their own."""
+import numpy as np
+import pytest
+
+import dg_inputs as di
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1609_00098_gb300 as p
+    from paper_1609_00098_gb300 import build as b
+    b.build()
+    return p
+
+
+def _gpu(x):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def _pair(pkg, system, K, n, flux, limiter, lo=(0, 0, 0), hi=(1, 1, 1), gamma=None):
+    gamma = gamma or (1.4 if system == 0 else 4.0 / 3.0)
+    om = oracle.Mesh(oracle.MeshSpec(system=system, K=K, n=n, flux=flux, limiter=limiter, gamma=gamma, lo=lo, hi=hi))
+    gm = pkg.Mesh(system=system, K=K, n=n, flux=flux, limiter=limiter, gamma=gamma, lo=lo, hi=hi, precision=1)
+    return om, gm
+
+
+def _rel_l2(om, a, b):
+    """Per-variable relative L2 distance with LGL quadrature (norm floored at 1 %
+    of the largest variable's norm)."""
+    _, d = om.norms(a, b)
+    _, ref = om.norms(b, np.zeros_like(b))
+    scale = np.maximum(ref, 1e-2 * ref.max())
+    return d / scale
+
+
+def _scale(R):
+    m = np.abs(R).max(axis=(0, 2))
+    return np.maximum(m, 1e-2 * m.max())
+
+
+@pytest.mark.parametrize("system,flux,n,kind", [(0, 0, 4, "wave"), (1, 1, 5, "blast"), (0, 1, 6, "kh"),
+                                                (1, 0, 3, "re_smooth")])
+def test_mixed_rhs_close_to_oracle(pkg, system, flux, n, kind):
+    lo, hi = ((-0.5,) * 3, (0.5,) * 3) if kind == "kh" else ((0, 0, 0), (1, 1, 1))
+    om, gm = _pair(pkg, system, (4, 3, 3), n, flux, 0, lo, hi)
+    xyz = om.coords()
+    prim = {"wave": lambda: di.smooth_wave_ne(xyz, k=(1, 2, 1)), "blast": lambda: di.blast_sr(xyz, seed=1),
+            "kh": lambda: di.kh_ne(xyz, seed=1), "re_smooth": lambda: di.smooth_flow_re(xyz, gamma=4 / 3)}[kind]()
+    U = om.from_prim(prim)
+    Ro = om.rhs(U)
+    Rg = gm.rhs(_gpu(U)).cpu().numpy()
+    assert gm.sync_status() == 0
+    # FP32 arithmetic: relative max-norm error of the RHS at the level of a few FP32 ulps
+    # times the ratio of flux to RHS magnitudes
+    err = np.abs(Rg - Ro).max(axis=(0, 2)) / _scale(Ro)
+    assert err.max() < 5e-4, err
+
+
+def test_mixed_smooth_wave_error_within_5_percent_of_fp64(pkg):
+    """Configuration 1 (Newtonian smooth wave, K=4, n=4, Rusanov, 10 CFL steps):
+    the mixed path's L2 error against the exact solution is within 1.05x of the
+    FP64 oracle's."""
+    import torch
+    om, gm = _pair(pkg, 0, (4, 4, 4), 4, 0, 0)
+    k = di.wave_numbers(1)
+    U0 = om.from_prim(di.smooth_wave_ne(om.coords(), k=k))
+    Uo, t = U0.copy(), 0.0
+    dts = []
+    for _ in range(10):
+        h = om.cfl_dt(Uo, 0.2)
+        dts.append(h)
+        Uo = om.rk3_step(Uo, h)
+        t += h
+    Ug = _gpu(U0)
+    for h in dts:
+        gm.rk3_step(Ug, dt=h)
+    assert gm.sync_status() == 0
+    Uex = om.from_prim(di.smooth_wave_ne(om.coords(), t, k=k))
+    eo = om.norms(Uo, Uex)[1]
+    eg = om.norms(Ug.cpu().numpy(), Uex)[1]
+    assert np.all(eg <= 1.05 * eo + 1e-12), (eg, eo)
+    # and the CFL step computed on the device in FP32 agrees with the FP64 one
+    dt = torch.zeros(1, dtype=torch.float64, device="cuda")
+    Ug2 = _gpu(U0)
+    gm.rk3_step(Ug2, cfl=0.2, dt_used=dt)
+    assert abs(dt.item() - dts[0]) <= 1e-6 * dts[0]
+
+
+@pytest.mark.parametrize("limiter", [1, 2])
+def test_mixed_blast_close_to_oracle(pkg, limiter):
+    """SR blast with HLL and a limiter after every stage: after 10 steps with the
+    oracle's time steps, relative L2 distance to the FP64 oracle <= 1e-6."""
+    om, gm = _pair(pkg, 1, (6, 5, 5), 5, 1, limiter)
+    U = om.from_prim(di.blast_sr(om.coords(), seed=1))
+    Ug = _gpu(U)
+    for _ in range(10):
+        h = om.cfl_dt(U, 0.2)
+        U = om.rk3_step(U, h)
+        gm.rk3_step(Ug, dt=h)
+    assert gm.sync_status() == 0
+    d = _rel_l2(om, Ug.cpu().numpy(), U)
+    assert np.all(d <= 1e-6), d
+
+
+def test_mixed_kh_close_to_oracle(pkg):
+    om, gm = _pair(pkg, 0, (4, 4, 4), 6, 1, 1, lo=(-0.5,) * 3, hi=(0.5,) * 3, gamma=5 / 3)
+    U = om.from_prim(di.kh_ne(om.coords(), seed=1))
+    Ug = _gpu(U)
+    for _ in range(10):
+        h = om.cfl_dt(U, 0.2)
+        U = om.rk3_step(U, h)
+        gm.rk3_step(Ug, dt=h)
+    assert gm.sync_status() == 0
+    d = _rel_l2(om, Ug.cpu().numpy(), U)
+    assert np.all(d <= 1e-6), d
+
+
+def test_mixed_conservation(pkg):
+    """FP64 state: totals drift only by the FP32 rounding of the fluxes and of the
+    stage increments (relative to the largest total)."""
+    om, gm = _pair(pkg, 1, (4, 4, 4), 4, 1, 1)
+    U = om.from_prim(di.blast_sr(om.coords(), seed=2))
+    t0 = om.totals(U)
+    Ug = _gpu(U)
+    for _ in range(5):
+        gm.rk3_step(Ug, cfl=0.2)
+    t1 = om.totals(Ug.cpu().numpy())
+    assert gm.sync_status() == 0
+    drift = np.abs(t1 - t0) / np.abs(t0).max()
+    assert np.all(drift < 1e-7), drift
+
+
+def test_mixed_ill_conditioned_nodes(pkg):
+    """Fast cold flow (W ~ 8, eps ~ 1e-6): FP32 con2prim alone would lose the
+    pressure; the FP64 polish keeps the RHS at FP32 accuracy."""
+    om, gm = _pair(pkg, 1, (3, 3, 3), 4, 1, 0)
+    x, y, z = om.coords()
+    v = 0.99 + 0.002 * np.sin(2 * np.pi * x)
+    rho = 1.0 + 0.1 * np.sin(2 * np.pi * y)
+    p = (1.0 / 3.0) * rho * 1e-6
+    prim = np.stack([rho, v, 0 * v, 0 * v, p])
+    U = om.from_prim(prim)
+    Ro = om.rhs(U)
+    Rg = gm.rhs(_gpu(U)).cpu().numpy()
+    assert gm.sync_status() == 0
+    err = np.abs(Rg - Ro).max(axis=(0, 2)) / _scale(Ro)
+    assert err.max() < 1e-3, err
