@@ -132,6 +132,38 @@ dg_status dg_limiter_summaries(dg_mesh *mesh, const double *U, double *S, void *
 dg_status dg_con2prim(long long count, double gamma, const double *cons, double *prim,
                       const double *p_guess, int *iters, int *status, void *stream);
 
+/* ---- Learned starting guess for SR con2prim (BASELINE addition on top of Sec. 2.1.2) ----
+ * A 3 -> 64 -> 64 -> 1 SiLU MLP maps three scaled invariants of (D, S, tau) to a
+ * scaled log pressure; dg_con2prim's safeguarded Newton starts from it, so results
+ * change only in iteration count.  Parameters are FP32, laid out flat as
+ * W1[64][3], b1[64], W2[64][64], b2[64], W3[64], b3 (DG_C2P_NET_PARAMS floats;
+ * W[j][i] maps input i to output j).  With E = tau + D and s = |S| the features are
+ * x1 = 2 (log10(tau/D) - lo1)/(hi1 - lo1) - 1, x2 = 2 s/E - 1,
+ * x3 = 2 (log10 D - lo3)/(hi3 - lo3) - 1, and the target y = (log10(p/E) - y_shift)/y_scale;
+ * scales = (lo1, hi1, lo3, hi3, y_shift, y_scale).  The 64 x 64 layer runs on the
+ * tensor cores in BF16 with FP32 accumulation (forward and backward). */
+#define DG_C2P_NET_PARAMS 4481
+typedef struct dg_c2p_net dg_c2p_net;
+/* Create on the current device from host arrays params[DG_C2P_NET_PARAMS] and
+ * scales[6] (copied).  Adam state starts at zero. */
+dg_status dg_c2p_net_create(const float *params, const double *scales, dg_c2p_net **out);
+void dg_c2p_net_destroy(dg_c2p_net *net);
+/* Copy the current FP32 parameters to the host array params[DG_C2P_NET_PARAMS]. */
+dg_status dg_c2p_net_get_params(const dg_c2p_net *net, float *params);
+/* Pressure guesses E 10^(y y_scale + y_shift), clamped into [max(0, s-E), (gamma-1) tau],
+ * for `count` conserved states (5 device rows as in dg_con2prim) into p_guess (device). */
+dg_status dg_c2p_net_guess(dg_c2p_net *net, long long count, double gamma, const double *cons, double *p_guess,
+                           void *stream);
+/* Mean squared error of the scaled target over `count` states with true pressures p
+ * (device), and its gradient: grad (device, DG_C2P_NET_PARAMS floats), loss (device, 1). */
+dg_status dg_c2p_net_grad(dg_c2p_net *net, long long count, const double *cons, const double *p, float *grad,
+                          float *loss, void *stream);
+/* `epochs` passes over the data in order, mini-batches of `batch`, one Adam step
+ * (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) per mini-batch.
+ * loss_per_epoch (device, `epochs` floats, may be NULL) gets each epoch's mean loss. */
+dg_status dg_c2p_net_train(dg_c2p_net *net, long long count, const double *cons, const double *p, int epochs,
+                           int batch, float lr, float *loss_per_epoch, void *stream);
+
 /* Synchronise `stream`, then read and clear the mesh's device status word.
  * Returns DG_OK, DG_ERR_C2P or DG_ERR_UNPHYSICAL (first set), or DG_ERR_CUDA. */
 dg_status dg_sync_status(dg_mesh *mesh, void *stream);

@@ -65,6 +65,12 @@ SIGNATURES = {
     "dg_limiter_summaries": (_i, [_vp, _vp, _vp, _vp]),
     "dg_con2prim": (_i, [_ll, _d, _vp, _vp, _vp, _vp, _vp, _vp]),
     "dg_sync_status": (_i, [_vp, _vp]),
+    "dg_c2p_net_create": (_i, [_vp, _vp, ctypes.POINTER(_vp)]),
+    "dg_c2p_net_destroy": (None, [_vp]),
+    "dg_c2p_net_get_params": (_i, [_vp, _vp]),
+    "dg_c2p_net_guess": (_i, [_vp, _ll, _d, _vp, _vp, _vp]),
+    "dg_c2p_net_grad": (_i, [_vp, _ll, _vp, _vp, _vp, _vp, _vp]),
+    "dg_c2p_net_train": (_i, [_vp, _ll, _vp, _vp, _i, _i, ctypes.c_float, _vp, _vp]),
     "dg_profile_enable": (_i, [_vp, _i]),
     "dg_profile_read": (_i, [_vp, ctypes.POINTER(_d), ctypes.POINTER(_ll), _i]),
     "dg_last_error": (ctypes.c_char_p, []),
@@ -233,6 +239,52 @@ def dg_con2prim(count, gamma, cons, prim, p_guess=None, iters=None, status=None,
 def dg_sync_status(mesh, stream=None) -> int:
     """Returns the status code (does not raise for kernel-side failures)."""
     return load().dg_sync_status(mesh, _stream(stream))
+
+
+N_NET_PARAMS = 4481
+
+
+def dg_c2p_net_create(params, scales):
+    """params: host float32 array of 4481; scales: 6 floats (host)."""
+    import numpy as np
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    sc = np.ascontiguousarray(scales, dtype=np.float64)
+    if p.size != N_NET_PARAMS or sc.size != 6:
+        raise ValueError("need 4481 parameters and 6 scales")
+    h = ctypes.c_void_p()
+    _check(load().dg_c2p_net_create(p.ctypes.data, sc.ctypes.data, ctypes.byref(h)))
+    return h
+
+
+def dg_c2p_net_destroy(net):
+    load().dg_c2p_net_destroy(net)
+
+
+def dg_c2p_net_get_params(net):
+    import numpy as np
+    p = np.zeros(N_NET_PARAMS, dtype=np.float32)
+    _check(load().dg_c2p_net_get_params(net, p.ctypes.data))
+    return p
+
+
+def dg_c2p_net_guess(net, count, gamma, cons, p_guess, stream=None):
+    import torch
+    _check(load().dg_c2p_net_guess(net, int(count), float(gamma), _ptr(cons, 5 * count, torch.float64, "cons"),
+                                   _ptr(p_guess, count, torch.float64, "p_guess"), _stream(stream)))
+
+
+def dg_c2p_net_grad(net, count, cons, p, grad, loss, stream=None):
+    import torch
+    _check(load().dg_c2p_net_grad(net, int(count), _ptr(cons, 5 * count, torch.float64, "cons"),
+                                  _ptr(p, count, torch.float64, "p"), _ptr(grad, N_NET_PARAMS, torch.float32, "grad"),
+                                  _ptr(loss, 1, torch.float32, "loss"), _stream(stream)))
+
+
+def dg_c2p_net_train(net, count, cons, p, epochs, batch, lr, loss_per_epoch=None, stream=None):
+    import torch
+    _check(load().dg_c2p_net_train(net, int(count), _ptr(cons, 5 * count, torch.float64, "cons"),
+                                   _ptr(p, count, torch.float64, "p"), int(epochs), int(batch), float(lr),
+                                   _ptr(loss_per_epoch, epochs, torch.float32, "loss_per_epoch"), _stream(stream)))
 
 
 PROFILE_CLASSES = ("primitives", "stage", "limit", "fix", "dt", "other")

@@ -74,6 +74,9 @@ enum { PROF_PRIM = 0, PROF_STAGE = 1, PROF_LIMIT = 2, PROF_FIX = 3, PROF_DT = 4,
 
 namespace dg {
 
+// error reporting shared with the other translation units of the library
+dg_status set_error(dg_status st, const char *msg) { return fail(st, "%s", msg); }
+
 // LGL tables (Sec. 3.1), computed on the host in FP64 with the textbook steps:
 //  * Legendre P_m and P_m' by (k+1) P_{k+1} = (2k+1) x P_k - k P_{k-1} and
 //    P'_{k+1} = P'_{k-1} + (2k+1) P_k;

@@ -62,22 +62,26 @@ __device__ __forceinline__ void flux_axis32(const float u[5], const float P[4], 
     F[4] = (u[4] + p) * va;
 }
 
+// Same operations and the same treatment of negative or NaN intermediate values
+// as the FP64 path (a negative pressure gives NaN speeds, which fmin/fmax then
+// ignore), so both paths agree on states that leave the physical range.
 template <int SYS>
 __device__ __forceinline__ void speeds_axis32(float g, const float u[5], const float P[4], int a, float &lmin,
                                               float &lmax)
 {
     const float va = P[a], p = P[3];
     if (SYS == 0) {
-        const float c = sqrtf(fmaxf(g * p / u[0], 0.0f));
+        const float c = sqrtf(g * p / u[0]);
         lmin = va - c;
         lmax = va + c;
         return;
     }
     const float v2 = P[0] * P[0] + P[1] * P[1] + P[2] * P[2];
     const float rhoh = (u[4] + u[0] + p) * (1.0f - v2);
-    const float cs2 = fminf(fmaxf(g * p / rhoh, 0.0f), 1.0f);
+    const float cs2 = g * p / rhoh;
     const float cs = sqrtf(cs2);
-    const float disc = fmaxf((1.0f - v2) * (1.0f - v2 * cs2 - va * va * (1.0f - cs2)), 0.0f);
+    float disc = (1.0f - v2) * (1.0f - v2 * cs2 - va * va * (1.0f - cs2));
+    if (disc < 0.0f) disc = 0.0f;
     const float root = cs * sqrtf(disc);
     const float inv = 1.0f / (1.0f - v2 * cs2);
     lmin = (va * (1.0f - cs2) - root) * inv;
@@ -278,9 +282,10 @@ __device__ __forceinline__ void node_prims_mixed(const MixedArgs &a, long long e
     int st64 = 1;
     if (st == 0) st64 = sr_polish64(a.gamma_d, u64, f32_to_f64(P[3]), Pd);
     if (st64 != 0) {
-        // unphysical in FP32 or in FP64: recover from the fixed FP64 state
+        // unphysical in FP32 or in FP64: recover from the fixed FP64 state,
+        // starting from the previous pass's pressure
         sr_fix(a.d_atm, a.tau_atm, u64);
-        st64 = sr_polish64(a.gamma_d, u64, -1.0, Pd);
+        st64 = sr_polish64(a.gamma_d, u64, guess >= 0.0f ? f32_to_f64(guess) : -1.0, Pd);
     }
     if (st64) errs |= ERRBIT_C2P;
 #pragma unroll
@@ -558,6 +563,14 @@ struct LimitMixedArgs {
     double x[MAXN];
 };
 
+// FP32 screen of the conserved-fix bounds; nodes that fail it are decided in FP64.
+__device__ __forceinline__ bool sr_fix_screen32(const float u[5], float d_atm, float tau_atm)
+{
+    const float s2 = u[1] * u[1] + u[2] * u[2] + u[3] * u[3];
+    return !(u[0] > 2.0f * d_atm) || !(u[4] > 2.0f * tau_atm * u[0]) ||
+           !(s2 < 0.999f * u[4] * (u[4] + 2.0f * u[0]));
+}
+
 template <int NP, int SYS>
 __global__ void __launch_bounds__(256) k_limit_mixed(const LimitMixedArgs a)
 {
@@ -592,49 +605,59 @@ __global__ void __launch_bounds__(256) k_limit_mixed(const LimitMixedArgs a)
     if (uf & 1) mask = 0x1fu;
     if (lane == 0 && a.troubled) a.troubled[e] = (unsigned char)mask;
     if (!mask && !(uf & 2) && !a.final_pass) return;
-    double m0[5], s0[5], s1[5], s2[5];
+    // the replacement U0 + sum_a slope_a (x_a - x_a0) (eq:MinModSol) is formed as an
+    // FP32 increment of U^n about the FP64 anchor U0 - U^n
+    double m0[5];
+    float s0[5], s1[5], s2[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
         m0[v] = __shfl_sync(0xffffffffu, U0, v);
-        s0[v] = __shfl_sync(0xffffffffu, sl[0], v);
-        s1[v] = __shfl_sync(0xffffffffu, sl[1], v);
-        s2[v] = __shfl_sync(0xffffffffu, sl[2], v);
+        s0[v] = f64_to_f32(__shfl_sync(0xffffffffu, sl[0], v));
+        s1[v] = f64_to_f32(__shfl_sync(0xffffffffu, sl[1], v));
+        s2[v] = f64_to_f32(__shfl_sync(0xffffffffu, sl[2], v));
     }
+    const float hx0 = f64_to_f32(0.5 * a.dx[0]), hx1 = f64_to_f32(0.5 * a.dx[1]), hx2 = f64_to_f32(0.5 * a.dx[2]);
     for (int q = lane; q < NN; q += 32) {
         const int i = q % NP, j = (q / NP) % NP, k = q / (NP * NP);
-        double u[5];
+        const float xi = f64_to_f32(a.x[i]) * hx0, xj = f64_to_f32(a.x[j]) * hx1, xk = f64_to_f32(a.x[k]) * hx2;
+        double un[5];
+        float d[5], u32[5];
+        unsigned nm = mask;
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
             const long long ix = (e * 5 + v) * NN + q;
+            un[v] = a.U[ix];
             if (mask & (1u << v))
-                u[v] = m0[v] + s0[v] * (0.5 * a.dx[0] * a.x[i]) + s1[v] * (0.5 * a.dx[1] * a.x[j]) +
-                       s2[v] * (0.5 * a.dx[2] * a.x[k]);
+                d[v] = f64_to_f32(m0[v] - un[v]) + (s0[v] * xi + s1[v] * xj + s2[v] * xk);
             else
-                u[v] = a.U[ix] + f32_to_f64(a.Dv[ix]);
+                d[v] = a.Dv[ix];
+            u32[v] = f64_to_f32(un[v]) + d[v];
         }
-        if (a.final_pass) {
-            if (SYS == 1) sr_fix(a.d_atm, a.tau_atm, u);
+        double u64[5];
+        bool exact = false;
+        if (SYS == 1 && sr_fix_screen32(u32, (float)a.d_atm, (float)a.tau_atm)) {
+            // the conserved fix after the replacement (Sec. 2.1.4, Sec. 3.3), in FP64
 #pragma unroll
-            for (int v = 0; v < 5; ++v) a.U[(e * 5 + v) * NN + q] = u[v];
-        } else {
-            unsigned nm = mask;  // variables of this node to rewrite
-            if (SYS == 1) {
-                // the conserved fix after the replacement (Sec. 2.1.4, Sec. 3.3)
-                double w[5];
+            for (int v = 0; v < 5; ++v) u64[v] = un[v] + f32_to_f64(d[v]);
+            double w[5] = {u64[0], u64[1], u64[2], u64[3], u64[4]};
+            if (sr_fix(a.d_atm, a.tau_atm, w)) {
+                exact = a.final_pass != 0;
 #pragma unroll
-                for (int v = 0; v < 5; ++v) w[v] = u[v];
-                if (sr_fix(a.d_atm, a.tau_atm, w))
-#pragma unroll
-                    for (int v = 0; v < 5; ++v)
-                        if (w[v] != u[v]) nm |= 1u << v;
-#pragma unroll
-                for (int v = 0; v < 5; ++v) u[v] = w[v];
+                for (int v = 0; v < 5; ++v)
+                    if (w[v] != u64[v]) {
+                        nm |= 1u << v;
+                        d[v] = f64_to_f32(w[v] - un[v]);
+                        u64[v] = w[v];
+                    }
             }
+        }
 #pragma unroll
-            for (int v = 0; v < 5; ++v) {
-                const long long ix = (e * 5 + v) * NN + q;
-                if (nm & (1u << v)) a.Dv[ix] = f64_to_f32(u[v] - a.U[ix]);
-            }
+        for (int v = 0; v < 5; ++v) {
+            const long long ix = (e * 5 + v) * NN + q;
+            if (a.final_pass)
+                a.U[ix] = exact ? u64[v] : un[v] + f32_to_f64(d[v]);
+            else if (nm & (1u << v))
+                a.Dv[ix] = d[v];
         }
     }
 }

@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(kThreads) k_cfl_mixed(const double *Un, const 
                 if (st == 0) st64 = sr_polish64(gamma_d, u64, f32_to_f64(P[3]), Pd);
                 if (st64 != 0) {
                     sr_fix(d_atm, tau_atm, u64);
-                    st64 = sr_polish64(gamma_d, u64, -1.0, Pd);
+                    st64 = sr_polish64(gamma_d, u64, (pin && pin[g] >= 0.0f) ? f32_to_f64(pin[g]) : -1.0, Pd);
                 }
                 if (st64) errs |= ERRBIT_C2P;
 #pragma unroll
