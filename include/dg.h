@@ -164,6 +164,22 @@ dg_status dg_c2p_net_grad(dg_c2p_net *net, long long count, const double *cons, 
 dg_status dg_c2p_net_train(dg_c2p_net *net, long long count, const double *cons, const double *p, int epochs,
                            int batch, float lr, float *loss_per_epoch, void *stream);
 
+/* dg_rhs without allocation (the paper has no counterpart: this serves callers that
+ * cannot call cudaMalloc -- device memory owned by another allocator, or loops that
+ * cannot afford the device synchronisation of cudaMalloc/cudaFree).  Same kernels
+ * and result as dg_rhs on a mesh made from `desc` (FP64 only), but the node
+ * primitives live in a static device array of DG_RHS_STATIC_MAX_NODES nodes
+ * (4 doubles each, 4 MiB, held by every GPU that loads the library until exit)
+ * and nothing is allocated.  U and dUdt are caller-owned device arrays in state
+ * layout.  DG_ERR_ARG if the mesh has more than DG_RHS_STATIC_MAX_NODES nodes or
+ * the descriptor is invalid.  The first call on a device looks up the array's
+ * device address; make that first call before any stream capture.  The array is
+ * shared by all calls and keeps the last call's contents; calls that overlap on
+ * the GPU race on it.  A node without a physical primitive state gives non-finite
+ * values in dUdt. */
+#define DG_RHS_STATIC_MAX_NODES 131072
+dg_status dg_rhs_static(const dg_mesh_desc *desc, const double *U, double *dUdt, void *stream);
+
 /* Synchronise `stream`, then read and clear the mesh's device status word.
  * Returns DG_OK, DG_ERR_C2P or DG_ERR_UNPHYSICAL (first set), or DG_ERR_CUDA. */
 dg_status dg_sync_status(dg_mesh *mesh, void *stream);

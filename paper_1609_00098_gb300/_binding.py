@@ -58,6 +58,7 @@ SIGNATURES = {
     "dg_prim2con": (_i, [_vp, _vp, _vp, _vp]),
     "dg_primitives": (_i, [_vp, _vp, _vp, _vp]),
     "dg_rhs": (_i, [_vp, _vp, _vp, _vp]),
+    "dg_rhs_static": (_i, [ctypes.POINTER(dg_mesh_desc), _vp, _vp, _vp]),
     "dg_compute_dt": (_i, [_vp, _vp, _d, _vp, _vp]),
     "dg_rk3_step": (_i, [_vp, _vp, _d, _d, _vp, _vp, _vp]),
     "dg_limit": (_i, [_vp, _vp, _vp, _vp]),
@@ -195,6 +196,17 @@ def dg_rhs(mesh, U, dUdt, stream=None):
     n = dg_state_size(mesh)
     _check(load().dg_rhs(mesh, _ptr(U, n, torch.float64, "U"), _ptr(dUdt, n, torch.float64, "dUdt"),
                          _stream(stream)))
+
+
+RHS_STATIC_MAX_NODES = 131072
+
+
+def dg_rhs_static(desc: "dg_mesh_desc", U, dUdt, stream=None):
+    """dg_rhs of a mesh described by `desc`, with no device allocation."""
+    import torch
+    n = desc.K[0] * desc.K[1] * desc.K[2] * desc.n ** 3 * 5
+    _check(load().dg_rhs_static(ctypes.byref(desc), _ptr(U, n, torch.float64, "U"),
+                                _ptr(dUdt, n, torch.float64, "dUdt"), _stream(stream)))
 
 
 def dg_compute_dt(mesh, U, cfl, dt, stream=None):

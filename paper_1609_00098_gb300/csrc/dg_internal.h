@@ -128,4 +128,7 @@ cudaError_t launch_widen(const float *in, double *out, long long count, cudaStre
 // Host LGL tables (long double Newton; closed-form LGL differentiation matrix).
 void lgl_tables(int n, Tables &T);
 
+// Set the thread-local message of dg_last_error and return `st`.
+dg_status set_error(dg_status st, const char *msg);
+
 }  // namespace dg
