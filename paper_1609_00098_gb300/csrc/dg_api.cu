@@ -348,34 +348,31 @@ MixedArgs mixed_args(const dg_mesh *m)
     a.err = m->err;
     for (int i = 0; i < MAXN * MAXN; ++i) a.D32[i] = (float)m->T.D[i];
     for (int i = 0; i < MAXN; ++i) {
-        a.w32[i] = (float)m->T.w[i];
-        a.row1_32[i] = (float)m->T.row1[i];
-        a.wd[i] = m->T.w[i];
+        a.w64[i] = m->T.w[i];
+        a.row1_64[i] = m->T.row1[i];
     }
     return a;
 }
 
-LimitMixedArgs limit_mixed_args(const dg_mesh *m, double *U, float *Dv, unsigned char *troubled, int final_pass)
+LimitMixedArgs limit_mixed_args(const dg_mesh *m, double *U, unsigned char *troubled)
 {
     LimitMixedArgs l;
     std::memset(&l, 0, sizeof(l));
     l.U = U;
-    l.Dv = Dv;
     l.S = m->S;
-    l.unphys = (m->d.system == 1) ? m->unphys : nullptr;
+    l.flags = (m->d.system == 1) ? m->unphys : nullptr;
     l.troubled = troubled;
     l.E = m->E;
     for (int ax = 0; ax < 3; ++ax) {
         l.K[ax] = m->d.K[ax];
         l.dx[ax] = m->dx[ax];
+        for (int i = 0; i < MAXN; ++i) l.hx[ax][i] = 0.5 * m->dx[ax] * m->T.x[i];
     }
     l.limiter = m->d.limiter;
-    l.final_pass = final_pass;
     l.tvb_M = m->d.tvb_M;
     l.beta = m->d.beta;
     l.d_atm = m->d.d_atm;
     l.tau_atm = m->d.tau_atm;
-    for (int i = 0; i < MAXN; ++i) l.x[i] = m->T.x[i];
     return l;
 }
 
@@ -402,11 +399,8 @@ void free_scratch(dg_mesh *m)
     }
     cudaFree(m->W1);
     cudaFree(m->W2);
-    cudaFree(m->Da);
-    cudaFree(m->Db);
     cudaFree(m->pbuf[0]);
     cudaFree(m->pbuf[1]);
-    cudaFree(m->Sn);
     cudaFree(m->P);
     cudaFree(m->S);
     cudaFree(m->unphys);
@@ -455,19 +449,13 @@ dg_status dg_mesh_create(const dg_mesh_desc *d, dg_mesh **out)
     }
     const size_t state = sizeof(double) * (size_t)E * 5 * m->nn;
     const bool mixed = d->precision == DG_PRECISION_MIXED;
-    m->kappa_sw = 1.0e3f;
+    m->kappa_sw = 10.0f;
     cudaError_t st = cudaSuccess;
-    if (!mixed) {
-        st = st ? st : cudaMalloc(&m->W1, state);
-        st = st ? st : cudaMalloc(&m->W2, state);
-    } else {
-        st = st ? st : cudaMalloc(&m->Da, state / 2);
-        st = st ? st : cudaMalloc(&m->Db, state / 2);
-        st = st ? st : cudaMalloc(&m->Sn, sizeof(double) * (size_t)E * 35);
-        if (d->system == 1) {
-            st = st ? st : cudaMalloc(&m->pbuf[0], sizeof(float) * (size_t)E * m->nn);
-            st = st ? st : cudaMalloc(&m->pbuf[1], sizeof(float) * (size_t)E * m->nn);
-        }
+    st = st ? st : cudaMalloc(&m->W1, state);
+    st = st ? st : cudaMalloc(&m->W2, state);
+    if (mixed && d->system == 1) {
+        st = st ? st : cudaMalloc(&m->pbuf[0], sizeof(float) * (size_t)E * m->nn);
+        st = st ? st : cudaMalloc(&m->pbuf[1], sizeof(float) * (size_t)E * m->nn);
     }
     st = st ? st : cudaMalloc(&m->P, sizeof(double) * (size_t)E * 4 * m->nn);
     st = st ? st : cudaMalloc(&m->S, sizeof(double) * (size_t)E * 50);
@@ -545,11 +533,11 @@ dg_status dg_rhs(dg_mesh *m, const double *U, double *dUdt, void *stream)
     cudaStream_t s = (cudaStream_t)stream;
     if (m->d.precision == DG_PRECISION_MIXED) {
         MixedArgs a = mixed_args(m);
+        a.Us = U;
         a.Un = U;
-        a.Rout = m->Da;
-        a.cD = 1.0f;
+        a.out = dUdt;
+        a.mode = 0;
         DG_LAUNCH(m, s, PROF_STAGE, launch_stage_mixed(m->d.n, m->d.system, m->d.flux, a, m->E, s));
-        DG_LAUNCH(m, s, PROF_OTHER, launch_widen(m->Da, dUdt, m->E * 5 * m->nn, s));
         return DG_OK;
     }
     DG_LAUNCH(m, s, PROF_PRIM, launch_primitives(m, U, m->P, 0, nullptr, nullptr, s));
@@ -575,8 +563,9 @@ dg_status dg_compute_dt(dg_mesh *m, const double *U, double cfl, double *dt, voi
     return DG_OK;
 }
 
-// Mixed-precision step: CFL pass, three fused stages on FP32 increments of U^n,
-// limiter on the increments, and a final pass forming U^{n+1} = U^n + D3 in FP64.
+// Mixed-precision step: an optional CFL pass, then three fused stages on FP64
+// stage states, U -> W1 -> W2 -> U, each followed by the limiter when one is
+// selected (the limiter pass also applies the SR conserved fix).
 static dg_status rk3_step_mixed(dg_mesh *m, double *U, double dt, double cfl, double *dt_used,
                                 unsigned char *troubled, cudaStream_t s)
 {
@@ -588,8 +577,8 @@ static dg_status rk3_step_mixed(dg_mesh *m, double *U, double dt, double cfl, do
     a.dt = dt;
     a.dt_ptr = cflmode ? m->dt : nullptr;
     a.S = lim ? m->S : nullptr;
-    a.unphys = (lim && sr) ? m->unphys : nullptr;
-    a.Sn = m->Sn;
+    a.flags = (lim && sr) ? m->unphys : nullptr;
+    a.mode = 1;
     float *latest = (sr && m->p_valid) ? m->pbuf[m->pi] : nullptr;
     if (cflmode) {
         DG_CUDA(cudaMemsetAsync(m->lam, 0, sizeof(unsigned long long), s));
@@ -600,14 +589,16 @@ static dg_status rk3_step_mixed(dg_mesh *m, double *U, double dt, double cfl, do
         }
         DG_LAUNCH(m, s, PROF_DT, launch_dt(m, cfl, m->dt, s));
     }
-    float *din[3] = {nullptr, m->Da, m->Db};
-    float *dout[3] = {m->Da, m->Db, m->Da};
-    const float cD[3] = {1.0f, 0.25f, (float)(2.0 / 3.0)};
+    double *ins[3] = {U, m->W1, m->W2};
+    double *outs[3] = {m->W1, m->W2, U};
+    const float ca[3] = {0.0f, 0.75f, (float)(1.0 / 3.0)};
+    const float cb[3] = {1.0f, 0.25f, (float)(2.0 / 3.0)};
     for (int st = 0; st < 3; ++st) {
-        a.Din = din[st];
-        a.Dout = dout[st];
-        a.cD = cD[st];
-        a.write_Sn = st == 0;
+        a.Us = ins[st];
+        a.out = outs[st];
+        a.first = st == 0;
+        a.ca = ca[st];
+        a.cb = cb[st];
         a.pin = latest;
         a.pout = sr ? m->pbuf[1 - m->pi] : nullptr;
         DG_LAUNCH(m, s, PROF_STAGE, launch_stage_mixed(m->d.n, m->d.system, m->d.flux, a, m->E, s));
@@ -615,8 +606,8 @@ static dg_status rk3_step_mixed(dg_mesh *m, double *U, double dt, double cfl, do
             m->pi = 1 - m->pi;
             latest = m->pbuf[m->pi];
         }
-        if (lim || st == 2) {
-            LimitMixedArgs l = limit_mixed_args(m, U, dout[st], st == 2 ? troubled : nullptr, st == 2);
+        if (lim) {
+            LimitMixedArgs l = limit_mixed_args(m, outs[st], st == 2 ? troubled : nullptr);
             DG_LAUNCH(m, s, PROF_LIMIT, launch_limit_mixed(m->d.n, m->d.system, l, s));
         }
     }

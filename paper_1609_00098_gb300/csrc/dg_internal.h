@@ -86,15 +86,13 @@ struct dg_mesh {
     double *W1, *W2;         // stage states
     double *P;               // primitives [e][4][node]
     double *S;               // limiter summaries [e][5][10]
-    unsigned char *unphys;   // per-element unphysical flag
+    unsigned char *unphys;   // per-element SR flags (bit 0: an unphysical node; mixed path bit 1: a node needs the fix)
     unsigned long long *lam; // max wave speed (bit pattern of a non-negative double)
     double *dt;              // device step
     unsigned int *err;       // sticky status word
     // mixed-precision scratch (precision == DG_PRECISION_MIXED)
-    float *Da, *Db;          // FP32 stage increments of U^n
     float *pbuf[2];          // SR pressures of the last two passes (con2prim warm starts)
     int pi, p_valid;         // index of the latest pressure buffer, and whether it holds one
-    double *Sn;              // FP64 cell and face means of U^n [e][5][7]
     float kappa_sw;          // conditioning above which FP32 con2prim is polished in FP64
     // optional per-kernel timing (dg_profile_enable)
     int prof_on;
@@ -123,7 +121,6 @@ cudaError_t launch_stage_mixed(int n, int system, int flux, const MixedArgs &a, 
 cudaError_t launch_limit_mixed(int n, int system, const LimitMixedArgs &a, cudaStream_t s);
 cudaError_t launch_cfl_mixed(const dg_mesh *m, const double *Un, const float *pin, float *pout, float kappa_sw,
                              cudaStream_t s);
-cudaError_t launch_widen(const float *in, double *out, long long count, cudaStream_t s);
 
 // Host LGL tables (long double Newton; closed-form LGL differentiation matrix).
 void lgl_tables(int n, Tables &T);

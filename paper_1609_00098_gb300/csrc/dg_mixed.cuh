@@ -1,20 +1,15 @@
 // dg_mixed.cuh -- mixed-precision DG stage kernels (templated on the number of
 // LGL nodes per axis NP).
 //
-// State and accumulation stay FP64: U^n is read in FP64 and U^{n+1} = U^n + D3 is
-// formed in FP64 once per step.  Inside a step the SSP-RK3 stages (Sec. 3.4) are
-// carried as FP32 increments of U^n:
-//   D1 = dt L(U^n),  D2 = (D1 + dt L(U^n + D1)) / 4,  D3 = 2/3 (D2 + dt L(U^n + D2)),
-// which is the Shu-Osher form rewritten about U^n (U1 = U^n + D1, U2 = U^n + D2,
-// U^{n+1} = U^n + D3).  Fluxes, the tensor-product contraction (eq:405), the
-// numerical fluxes (eq:LLF, eq:HLL) and the lift (eq:411) run in FP32.  SR
-// con2prim runs in FP32 from the previous pass's pressure; where the conditioning
-// estimate tau/(rho eps) exceeds kappa_sw the pressure is polished by FP64 Newton
-// on the FP64 conserved state.  The limiter's cell and face means are the FP64
-// means of U^n (computed at stage 1) plus FP32 means of the increment, so the
-// 1e-8 detector of Sec. 3.3.2 and conservation by the limiter keep FP64 anchors.
-// FP64<->FP32 conversions are done with integer operations: on this GPU the
-// conversion instructions issue at the FP64 rate.
+// The state and every SSP-RK3 stage state stay FP64 (Sec. 3.4), and so do the
+// limiter's replacement and the conserved fix acting on them; the right-hand side
+// (eq:411) is evaluated in FP32: SR con2prim from the previous pass's pressure,
+// fluxes, the tensor-product contraction (eq:405), the numerical fluxes (eq:LLF,
+// eq:HLL) and the lift.  The stage update adds an FP32 increment to the FP64 state,
+// U_{s+1} = U_s + [ca (U^n - U_s) + cb dt R].  FP64 work is kept warp-uniform
+// (a warp-wide FP64 instruction costs the whole SM's FP64 pipe for ~17 cycles on
+// this GPU, with or without inactive lanes); FP64<->FP32 conversions use integer
+// operations because the conversion instructions issue at the FP64 rate.
 #pragma once
 
 #include "dg_internal.h"
@@ -49,9 +44,13 @@ __device__ __forceinline__ double f32_to_f64(float f)
 }
 
 // ---------------------------------------------------------------------------
-// FP32 physics (same formulas as the FP64 path)
+// FP32 physics.  Node primitives are held as P = (vx, vy, vz, p, 1 - v^2); the
+// last entry is 1 for the Newtonian system.  1 - v^2 comes from FP64 wherever the
+// Lorentz factor is large enough for FP32 to lose it (see sr_prims_mixed).
 
-__device__ __forceinline__ void flux_axis32(const float u[5], const float P[4], int a, float F[5])
+constexpr int NPRIM = 5;
+
+__device__ __forceinline__ void flux_axis32(const float u[5], const float P[NPRIM], int a, float F[5])
 {
     const float va = P[a], p = P[3];
     F[0] = u[0] * va;
@@ -62,11 +61,15 @@ __device__ __forceinline__ void flux_axis32(const float u[5], const float P[4], 
     F[4] = (u[4] + p) * va;
 }
 
-// Same operations and the same treatment of negative or NaN intermediate values
-// as the FP64 path (a negative pressure gives NaN speeds, which fmin/fmax then
-// ignore), so both paths agree on states that leave the physical range.
+// Wave speeds along axis a: Newtonian v_a -+ c_s; SR the eigenvalues of Sec. 2.1.2
+//   lambda = [v_a (1 - cs^2) -+ cs sqrt((1 - v^2)(1 - v^2 cs^2 - v_a^2 (1 - cs^2)))] / (1 - v^2 cs^2),
+// with the two factors that cancel as v -> 1 rewritten as sums of non-negative terms,
+//   1 - v^2 cs^2 = (1 - v^2) + v^2 (1 - cs^2),
+//   1 - v^2 cs^2 - v_a^2 (1 - cs^2) = (1 - v^2) + (1 - cs^2)(v_b^2 + v_c^2),
+// so the FP32 speeds keep their accuracy at large Lorentz factors.  A negative
+// pressure gives NaN speeds, as in the FP64 path, which fmin/fmax then ignore.
 template <int SYS>
-__device__ __forceinline__ void speeds_axis32(float g, const float u[5], const float P[4], int a, float &lmin,
+__device__ __forceinline__ void speeds_axis32(float g, const float u[5], const float P[NPRIM], int a, float &lmin,
                                               float &lmax)
 {
     const float va = P[a], p = P[3];
@@ -76,16 +79,19 @@ __device__ __forceinline__ void speeds_axis32(float g, const float u[5], const f
         lmax = va + c;
         return;
     }
+    const float w2i = P[4];
+    const float vb = P[a == 0 ? 1 : 0], vc = P[a == 2 ? 1 : 2];
     const float v2 = P[0] * P[0] + P[1] * P[1] + P[2] * P[2];
-    const float rhoh = (u[4] + u[0] + p) * (1.0f - v2);
+    const float rhoh = (u[4] + u[0] + p) * w2i;
     const float cs2 = g * p / rhoh;
     const float cs = sqrtf(cs2);
-    float disc = (1.0f - v2) * (1.0f - v2 * cs2 - va * va * (1.0f - cs2));
+    const float om = 1.0f - cs2;
+    float disc = w2i * (w2i + om * (vb * vb + vc * vc));
     if (disc < 0.0f) disc = 0.0f;
     const float root = cs * sqrtf(disc);
-    const float inv = 1.0f / (1.0f - v2 * cs2);
-    lmin = (va * (1.0f - cs2) - root) * inv;
-    lmax = (va * (1.0f - cs2) + root) * inv;
+    const float inv = 1.0f / (w2i + v2 * om);
+    lmin = (va * om - root) * inv;
+    lmax = (va * om + root) * inv;
 }
 
 // Numerical flux along +e_a minus each side's physical flux, in jump form:
@@ -96,8 +102,8 @@ __device__ __forceinline__ void speeds_axis32(float g, const float u[5], const f
 // Algebraically the eq:LLF / eq:HLL fluxes; in FP32 the differences are taken
 // before they are scaled, so equal states give exactly zero.
 template <int SYS, int FLX>
-__device__ __forceinline__ void num_flux_jump32(float g, int a, const float uL[5], const float PL[4],
-                                                const float uR[5], const float PR[4], float dL[5], float dR[5])
+__device__ __forceinline__ void num_flux_jump32(float g, int a, const float uL[5], const float PL[NPRIM],
+                                                const float uR[5], const float PR[NPRIM], float dL[5], float dR[5])
 {
     float FL[5], FR[5], lminL, lmaxL, lminR, lmaxR;
     flux_axis32(uL, PL, a, FL);
@@ -136,20 +142,21 @@ __device__ __forceinline__ void num_flux_jump32(float g, int a, const float uL[5
     }
 }
 
-__device__ __forceinline__ void ne_primitives32(float g, const float u[5], float P[4])
+__device__ __forceinline__ void ne_primitives32(float g, const float u[5], float P[NPRIM])
 {
     const float inv = 1.0f / u[0];
     P[0] = u[1] * inv;
     P[1] = u[2] * inv;
     P[2] = u[3] * inv;
     P[3] = (g - 1.0f) * (u[4] - 0.5f * (u[1] * P[0] + u[2] * P[1] + u[3] * P[2]));
+    P[4] = 1.0f;
 }
 
 // FP32 SR con2prim: the safeguarded Newton of the FP64 path in FP32, stopping
 // when the step is below 2^-21 p or the residual is at the FP32 noise level of
 // its terms.  Returns 0 ok, 1 unphysical in FP32, 2 no convergence; kappa gets
 // tau/(rho eps), the amplification of input rounding into p.
-__device__ __forceinline__ int sr_con2prim32(float g, const float u[5], float guess, float P[4], float &kappa)
+__device__ __forceinline__ int sr_con2prim32(float g, const float u[5], float guess, float P[NPRIM], float &kappa)
 {
     const float D = u[0], tau = u[4];
     const float s2 = u[1] * u[1] + u[2] * u[2] + u[3] * u[3];
@@ -183,6 +190,7 @@ __device__ __forceinline__ int sr_con2prim32(float g, const float u[5], float gu
     P[1] = u[2] * inv;
     P[2] = u[3] * inv;
     P[3] = p;
+    P[4] = 1.0f - (P[0] * P[0] + P[1] * P[1] + P[2] * P[2]);
     kappa = tau / fmaxf(rhoeps, 1e-30f);
     return status;
 }
@@ -232,64 +240,98 @@ __device__ __forceinline__ int sr_polish64(double g, const double u[5], double p
 // ---------------------------------------------------------------------------
 
 struct MixedArgs {
-    const double *Un;       // U^n (state layout)
-    const float *Din;       // increment of the stage input (nullptr: the input is U^n)
-    float *Dout;            // increment of the stage output (nullptr: RHS-only mode writes R)
-    float *Rout;            // RHS output (RHS-only mode) or nullptr
+    const double *Us;       // stage input (state layout, FP64)
+    const double *Un;       // U^n (stages 2, 3)
+    double *out;            // stage output U_{s+1} (mode 1) or dU/dt (mode 0)
     const float *pin;       // SR pressures of the previous pass [e][node] (guesses), or nullptr
-    float *pout;            // SR pressures of this stage's input [e][node]
-    double *Sn;             // FP64 means of U^n, [e][5][7]: written when write_Sn, read otherwise
+    float *pout;            // SR pressures of this stage's input [e][node], or nullptr
     double *S;              // limiter summaries of the output [e][5][10], or nullptr
-    unsigned char *unphys;  // SR: per-element unphysical flag of the output, or nullptr
+    unsigned char *flags;   // SR: bit 0 unphysical node, bit 1 a node needs the fix (limiter on)
     unsigned int *err;
     const double *dt_ptr;
     double dt;
-    float cD;               // Dout = cD (Din + dt R)
-    int write_Sn;
+    float ca, cb;           // U_{s+1} = ca U^n + cb (U_s + dt R) = U_s + ca (U^n - U_s) + cb dt R
+    int first;              // first stage: U_{s+1} = U_s + dt R
+    int mode;               // 0: dU/dt, 1: stage update
     int K[3];
     float gamma;
     double gamma_d;
     float g[3], lift0[3], liftN[3];
     float kappa_sw;
     double d_atm, tau_atm;
-    float D32[MAXN * MAXN], w32[MAXN], row1_32[MAXN];
-    double wd[MAXN];
+    float D32[MAXN * MAXN];
+    double w64[MAXN], row1_64[MAXN];
 };
 
-// Primitives of one node of the stage input (FP32), with the FP64 polish or the
-// FP64 fall-back (fix of a local copy, full FP64 con2prim) where FP32 is not enough.
+// SR primitives of one node, u the FP32 copy of the FP64 state Ub[v * stride]:
+// FP32 con2prim from `guess`; where the conditioning estimate tau/(rho eps)
+// exceeds kappa_sw (this covers every large Lorentz factor too:
+// tau/(rho eps) = W(W-1)/eps + W^2 + (gamma-1)(W^2-1) >= W^2), or FP32 cannot
+// resolve physicality, FP64
+// Newton on the FP64 state finishes it and 1 - v^2 is formed in FP64.  Cold
+// states whose pressure bracket (gamma-1) tau is below 2^-20 E keep the FP32
+// value: any pressure in that bracket leaves the fluxes unchanged at FP32
+// accuracy, and such states have v^2 < 2 tau / D, so 1 - v^2 is exact enough.
+// Returns ERRBIT_C2P where FP64 Newton fails too, else 0.
+__device__ __forceinline__ unsigned sr_prims_mixed(float g, double gd, float kappa_sw, double d_atm, double tau_atm,
+                                                   const float u[5], const double *Ub, long long stride, float guess,
+                                                   float P[NPRIM])
+{
+    float kappa = 1.0f;
+    const int st = sr_con2prim32(g, u, guess, P, kappa);
+    if (st == 0 && kappa <= kappa_sw) return 0u;
+    if ((g - 1.0f) * u[4] <= 0x1p-20f * (u[4] + u[0]) && u[0] > 0.0f && u[4] >= 0.0f) {
+        if (st != 0) {
+            // cold and unresolved in FP32: mid-bracket pressure, v = S/(E+p)
+            const float p = 0.5f * (g - 1.0f) * u[4];
+            const float inv = 1.0f / (u[4] + u[0] + p);
+            P[0] = u[1] * inv;
+            P[1] = u[2] * inv;
+            P[2] = u[3] * inv;
+            P[3] = p;
+            P[4] = 1.0f - (P[0] * P[0] + P[1] * P[1] + P[2] * P[2]);
+        }
+        return 0u;
+    }
+    double u64[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) u64[v] = Ub[v * stride];
+    double Pd[4];
+    int st64 = 1;
+    if (st == 0) st64 = sr_polish64(gd, u64, f32_to_f64(P[3]), Pd);
+    if (st64 != 0) {
+        // unphysical in FP32 or in FP64: recover from the fixed FP64 state,
+        // starting from the previous pass's pressure
+        sr_fix(d_atm, tau_atm, u64);
+        st64 = sr_polish64(gd, u64, guess >= 0.0f ? f32_to_f64(guess) : -1.0, Pd);
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) P[c] = f64_to_f32(Pd[c]);
+    P[4] = f64_to_f32(1.0 - (Pd[0] * Pd[0] + Pd[1] * Pd[1] + Pd[2] * Pd[2]));
+    return st64 ? ERRBIT_C2P : 0u;
+}
+
+// Primitives of one node of the stage input (element e, node q).
 template <int NP, int SYS>
-__device__ __forceinline__ void node_prims_mixed(const MixedArgs &a, long long e, int q, const float u[5], float P[4],
-                                                 unsigned &errs)
+__device__ __forceinline__ void node_prims_mixed(const MixedArgs &a, long long e, int q, const float u[5],
+                                                 float P[NPRIM], unsigned &errs)
 {
     constexpr int NN = NP * NP * NP;
     if (SYS == 0) {
         ne_primitives32(a.gamma, u, P);
         return;
     }
-    const float guess = a.pin ? a.pin[e * NN + q] : -1.0f;
-    float kappa = 1.0f;
-    const int st = sr_con2prim32(a.gamma, u, guess, P, kappa);
-    if (st == 0 && kappa <= a.kappa_sw) return;
-    // FP64 conserved state of the node
-    double u64[5];
-#pragma unroll
-    for (int v = 0; v < 5; ++v) {
-        u64[v] = a.Un[(e * 5 + v) * NN + q];
-        if (a.Din) u64[v] += f32_to_f64(a.Din[(e * 5 + v) * NN + q]);
-    }
-    double Pd[4];
-    int st64 = 1;
-    if (st == 0) st64 = sr_polish64(a.gamma_d, u64, f32_to_f64(P[3]), Pd);
-    if (st64 != 0) {
-        // unphysical in FP32 or in FP64: recover from the fixed FP64 state,
-        // starting from the previous pass's pressure
-        sr_fix(a.d_atm, a.tau_atm, u64);
-        st64 = sr_polish64(a.gamma_d, u64, guess >= 0.0f ? f32_to_f64(guess) : -1.0, Pd);
-    }
-    if (st64) errs |= ERRBIT_C2P;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) P[c] = f64_to_f32(Pd[c]);
+    errs |= sr_prims_mixed(a.gamma, a.gamma_d, a.kappa_sw, a.d_atm, a.tau_atm, u, a.Us + e * 5 * NN + q, NN,
+                           a.pin ? a.pin[e * NN + q] : -1.0f, P);
+}
+
+// FP32 screen of the bounds of the conserved fix (Sec. 2.1.4) and of physicality;
+// nodes that fail it are decided in FP64.
+__device__ __forceinline__ bool sr_screen32(const float u[5], float d_atm, float tau_atm)
+{
+    const float s2 = u[1] * u[1] + u[2] * u[2] + u[3] * u[3];
+    return !(u[0] > 2.0f * d_atm) || !(u[4] > 2.0f * tau_atm * u[0]) ||
+           !(s2 < 0.999f * u[4] * (u[4] + 2.0f * u[0]));
 }
 
 template <int NP, int SYS, int FLX>
@@ -297,20 +339,20 @@ __global__ void __launch_bounds__(round_up32(NP *NP *NP)) k_stage_mixed(const Mi
 {
     constexpr int NN = NP * NP * NP;
     extern __shared__ float smem_mixed[];
-    float *sF = smem_mixed;     // [3][5][NN] fluxes, later the output increment [5][NN]
+    float *sF = smem_mixed;     // [3][5][NN] fluxes, later FP32 deviations of the output [5][NN]
     float *sR = sF + 15 * NN;   // [5][NN] right-hand side
-    float *sU = sR + 5 * NN;    // [5][NN] stage input state, later the output state
-    float *sP = sU + 5 * NN;    // [4][NN] primitives of the input
-    __shared__ float sD[NP * NP], sW[NP], sRow1[NP];
-    __shared__ double sSn[35];
+    float *sU = sR + 5 * NN;    // [5][NN] stage input state (FP32)
+    float *sP = sU + 5 * NN;    // [NPRIM][NN] primitives of the input
+    __shared__ float sD[NP * NP];
+    __shared__ double sW64[NP], sRow164[NP], sQ[3 * NP * 5];
     __shared__ long long sNb[6];
 
     const int t = threadIdx.x;
     const long long e = blockIdx.x;
     for (int i = t; i < NP * NP; i += blockDim.x) sD[i] = a.D32[i];
     if (t < NP) {
-        sW[t] = a.w32[t];
-        sRow1[t] = a.row1_32[t];
+        sW64[t] = a.w64[t];
+        sRow164[t] = a.row1_64[t];
     }
     if (t < 6) sNb[t] = elem_neighbour(e, a.K, t >> 1, (t & 1) ? 1 : -1);
     unsigned errs = 0;
@@ -319,55 +361,20 @@ __global__ void __launch_bounds__(round_up32(NP *NP *NP)) k_stage_mixed(const Mi
         float u[5];
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
-            u[v] = f64_to_f32(a.Un[(e * 5 + v) * NN + t]);
-            if (a.Din) u[v] += a.Din[(e * 5 + v) * NN + t];
+            u[v] = f64_to_f32(a.Us[(e * 5 + v) * NN + t]);
             sU[v * NN + t] = u[v];
         }
-        float P[4];
+        float P[NPRIM];
         node_prims_mixed<NP, SYS>(a, e, t, u, P, errs);
         if (SYS == 1 && a.pout) a.pout[e * NN + t] = P[3];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) sP[c * NN + t] = P[c];
+        for (int c = 0; c < NPRIM; ++c) sP[c * NN + t] = P[c];
 #pragma unroll
         for (int ax = 0; ax < 3; ++ax) {
             float f[5];
             flux_axis32(u, P, ax, f);
 #pragma unroll
             for (int v = 0; v < 5; ++v) sF[(ax * 5 + v) * NN + t] = f[v];
-        }
-    }
-    // FP64 cell and face means of U^n (stage 1), or their stored values
-    if (a.S) {
-        for (int id = t; id < 35; id += blockDim.x) {
-            const int v = id / 7, kind = id % 7;
-            double r;
-            if (a.write_Sn) {
-                const double *Uv = a.Un + (e * 5 + v) * NN;
-                if (kind == 0) {
-                    double s = 0.0;
-                    for (int k = 0; k < NP; ++k)
-                        for (int j = 0; j < NP; ++j)
-                            for (int i = 0; i < NP; ++i) s += a.wd[i] * a.wd[j] * a.wd[k] * Uv[i + NP * (j + NP * k)];
-                    r = s * 0.125;
-                } else {
-                    const int ax = (kind - 1) / 2, ia = ((kind - 1) % 2) ? NP - 1 : 0;
-                    const int b = (ax + 1) % 3, c = (ax + 2) % 3;
-                    double s = 0.0;
-                    for (int t1 = 0; t1 < NP; ++t1)
-                        for (int t0 = 0; t0 < NP; ++t0) {
-                            int id3[3];
-                            id3[ax] = ia;
-                            id3[b] = t0;
-                            id3[c] = t1;
-                            s += a.wd[t0] * a.wd[t1] * Uv[id3[0] + NP * (id3[1] + NP * id3[2])];
-                        }
-                    r = s * 0.25;
-                }
-                a.Sn[e * 35 + id] = r;
-            } else {
-                r = a.Sn[e * 35 + id];
-            }
-            sSn[id] = r;
         }
     }
     __syncthreads();
@@ -405,7 +412,7 @@ __global__ void __launch_bounds__(round_up32(NP *NP *NP)) k_stage_mixed(const Mi
     }
     __syncthreads();
 
-    // surface terms; the neighbour's face node is recovered here from U^n + Din
+    // surface terms; the neighbour's face node is recovered here from its FP64 state
     for (int ax = 0; ax < 3; ++ax) {
         for (int fp = t; fp < 2 * NP * NP; fp += blockDim.x) {
             const int side = fp / (NP * NP);
@@ -418,15 +425,14 @@ __global__ void __launch_bounds__(round_up32(NP *NP *NP)) k_stage_mixed(const Mi
             id[ax] = side ? 0 : NP - 1;
             const int qn = id[0] + NP * (id[1] + NP * id[2]);
             const long long en = sNb[2 * ax + side];
-            float uo[5], Po[4], un[5], Pn[4];
+            float uo[5], Po[NPRIM], un[5], Pn[NPRIM];
 #pragma unroll
             for (int v = 0; v < 5; ++v) {
                 uo[v] = sU[v * NN + q];
-                un[v] = f64_to_f32(a.Un[(en * 5 + v) * NN + qn]);
-                if (a.Din) un[v] += a.Din[(en * 5 + v) * NN + qn];
+                un[v] = f64_to_f32(a.Us[(en * 5 + v) * NN + qn]);
             }
 #pragma unroll
-            for (int c = 0; c < 4; ++c) Po[c] = sP[c * NN + q];
+            for (int c = 0; c < NPRIM; ++c) Po[c] = sP[c * NN + q];
             node_prims_mixed<NP, SYS>(a, en, qn, un, Pn, errs);
             float dL[5], dR[5];
             if (side) {
@@ -443,133 +449,127 @@ __global__ void __launch_bounds__(round_up32(NP *NP *NP)) k_stage_mixed(const Mi
     }
     if (errs) atomicOr(a.err, errs);
 
-    // stage increment and FP32 output state.  The limiter summaries and the
-    // unphysical flag see the output before the conserved fix (Sec. 3.3: limit,
-    // then fix); the stored increment carries the fix, which is exact for elements
-    // the limiter leaves alone, and the limiter re-applies it where it rewrites.
+    // Stage update in FP64: U_{s+1} = U_s + [ca (U^n - U_s) + cb dt R], the bracket
+    // in FP32 (it carries the FP32 RHS), the accumulation in FP64.  The limiter
+    // summaries and the SR flags see the output before the conserved fix (Sec. 3.3:
+    // limit, then fix); with the limiter on the fix is left to the limiter pass,
+    // which visits the flagged elements.
+    double val[5];
     bool bad = false, needfix = false;
     if (t < NN) {
         const float dt = (float)(a.dt_ptr ? *a.dt_ptr : a.dt);
-        float d[5], un[5], dfix[5];
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
+            const long long ix = (e * 5 + v) * NN + t;
             const float R = sR[v * NN + t];
-            if (a.Rout) a.Rout[(e * 5 + v) * NN + t] = R;
-            const float din = a.Din ? a.Din[(e * 5 + v) * NN + t] : 0.0f;
-            d[v] = a.cD * (din + dt * R);
-            un[v] = f64_to_f32(a.Un[(e * 5 + v) * NN + t]) + d[v];
-            dfix[v] = d[v];
-        }
-        if (SYS == 1) {
-            // decided on the FP64 state wherever FP32 cannot rule the bounds out
-            const float s2 = un[1] * un[1] + un[2] * un[2] + un[3] * un[3];
-            if (!(un[0] > 2.0f * (float)a.d_atm) || !(un[4] > 2.0f * (float)a.tau_atm * un[0]) ||
-                !(s2 < 0.999f * un[4] * (un[4] + 2.0f * un[0]))) {
-                double u64[5], f64v[5];
-#pragma unroll
-                for (int v = 0; v < 5; ++v) {
-                    u64[v] = a.Un[(e * 5 + v) * NN + t] + f32_to_f64(d[v]);
-                    f64v[v] = u64[v];
-                }
-                bad = sr_unphysical(u64);
-                if (a.Dout && sr_fix(a.d_atm, a.tau_atm, f64v)) {
-                    needfix = true;
-#pragma unroll
-                    for (int v = 0; v < 5; ++v)
-                        if (f64v[v] != u64[v]) dfix[v] = f64_to_f32(f64v[v] - a.Un[(e * 5 + v) * NN + t]);
-                }
+            if (a.mode == 0) {
+                a.out[ix] = f32_to_f64(R);
+                continue;
             }
-        }
-        // with the limiter on, the fix waits for it (flagged elements only)
-        const bool defer = a.S != nullptr;
-#pragma unroll
-        for (int v = 0; v < 5; ++v) {
-            if (a.Dout) a.Dout[(e * 5 + v) * NN + t] = defer ? d[v] : dfix[v];
-            sF[v * NN + t] = d[v];
-            sU[v * NN + t] = un[v];
+            const double us = a.Us[ix];
+            float inc;
+            if (a.first) {
+                inc = dt * R;
+            } else {
+                const float dn = f64_to_f32(a.Un[ix] - us);
+                inc = a.ca * dn + a.cb * (dt * R);
+            }
+            val[v] = us + f32_to_f64(inc);
         }
     }
+    if (a.mode == 0) return;
+    if (t < NN && SYS == 1) {
+        float u32[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) u32[v] = f64_to_f32(val[v]);
+        if (sr_screen32(u32, (float)a.d_atm, (float)a.tau_atm)) {
+            bad = sr_unphysical(val);
+            double w[5] = {val[0], val[1], val[2], val[3], val[4]};
+            if (sr_fix(a.d_atm, a.tau_atm, w)) {
+                needfix = true;
+                if (a.S == nullptr)
+#pragma unroll
+                    for (int v = 0; v < 5; ++v) val[v] = w[v];
+            }
+        }
+    }
+    if (t < NN)
+#pragma unroll
+        for (int v = 0; v < 5; ++v) a.out[(e * 5 + v) * NN + t] = val[v];
     if (a.S == nullptr) return;
+
+    // Limiter summaries of the output in FP64 (the limiter's decisions and its
+    // replacement, and through them the conserved fix at the replaced nodes, are
+    // sensitive to them at the FP64 level).  Plane sums
+    //   Q_a[i][v] = sum_{t0,t1} w_t0 w_t1 U_v(node with index i along axis a)
+    // give the cell mean sum_i w_i Q_0[i] / 8, the face means Q_a[0] / 4 and
+    // Q_a[NP-1] / 4, and the P1 coefficients sum_i row1_i Q_a[i] / 4.  The FP64 copy
+    // of the output overlays the flux array, which is no longer read.
+    double *sV = reinterpret_cast<double *>(smem_mixed);
+    if (t < NN)
+#pragma unroll
+        for (int v = 0; v < 5; ++v) sV[v * NN + t] = val[v];
     const int anybad = __syncthreads_or(bad);
     const int anyfix = __syncthreads_or(needfix);
-    // summaries: FP64 means of U^n + FP32 means of the increment; FP32 slopes
+    for (int id = t; id < 15 * NP; id += blockDim.x) {
+        const int ax = id / (5 * NP), ia = (id / 5) % NP, v = id % 5;
+        const int b = (ax + 1) % 3, c = (ax + 2) % 3;
+        const double *Vv = sV + v * NN;
+        double q = 0.0;
+        for (int t1 = 0; t1 < NP; ++t1) {
+            double r = 0.0;
+            for (int t0 = 0; t0 < NP; ++t0) {
+                int id3[3];
+                id3[ax] = ia;
+                id3[b] = t0;
+                id3[c] = t1;
+                r = fma(sW64[t0], Vv[id3[0] + NP * (id3[1] + NP * id3[2])], r);
+            }
+            q = fma(sW64[t1], r, q);
+        }
+        sQ[(ax * NP + ia) * 5 + v] = q;
+    }
+    __syncthreads();
     for (int id = t; id < 50; id += blockDim.x) {
         const int v = id / 10, kind = id % 10;
-        const float *Dv = sF + v * NN;
         double r;
         if (kind == 0) {
-            float s = 0.0f;
-            for (int k = 0; k < NP; ++k)
-                for (int j = 0; j < NP; ++j)
-                    for (int i = 0; i < NP; ++i) s = fmaf(sW[i] * sW[j] * sW[k], Dv[i + NP * (j + NP * k)], s);
-            r = sSn[v * 7] + f32_to_f64(s * 0.125f);
+            double s = 0.0;
+            for (int i = 0; i < NP; ++i) s = fma(sW64[i], sQ[i * 5 + v], s);
+            r = s * 0.125;
         } else if (kind <= 6) {
             const int ax = (kind - 1) / 2, ia = ((kind - 1) % 2) ? NP - 1 : 0;
-            const int b = (ax + 1) % 3, c = (ax + 2) % 3;
-            float s = 0.0f;
-            for (int t1 = 0; t1 < NP; ++t1)
-                for (int t0 = 0; t0 < NP; ++t0) {
-                    int id3[3];
-                    id3[ax] = ia;
-                    id3[b] = t0;
-                    id3[c] = t1;
-                    s = fmaf(sW[t0] * sW[t1], Dv[id3[0] + NP * (id3[1] + NP * id3[2])], s);
-                }
-            r = sSn[v * 7 + kind] + f32_to_f64(s * 0.25f);
+            r = sQ[(ax * NP + ia) * 5 + v] * 0.25;
         } else {
             const int ax = kind - 7;
-            const int b = (ax + 1) % 3, c = (ax + 2) % 3;
-            const float *Uv = sU + v * NN;
-            float c1 = 0.0f;
-            for (int ia = 0; ia < NP; ++ia) {
-                float s = 0.0f;
-                for (int t1 = 0; t1 < NP; ++t1)
-                    for (int t0 = 0; t0 < NP; ++t0) {
-                        int id3[3];
-                        id3[ax] = ia;
-                        id3[b] = t0;
-                        id3[c] = t1;
-                        s = fmaf(sW[t0] * sW[t1], Uv[id3[0] + NP * (id3[1] + NP * id3[2])], s);
-                    }
-                c1 = fmaf(sRow1[ia], s * 0.25f, c1);
-            }
-            r = f32_to_f64(c1);
+            double s = 0.0;
+            for (int i = 0; i < NP; ++i) s = fma(sRow164[i], sQ[(ax * NP + i) * 5 + v], s);
+            r = s * 0.25;
         }
         a.S[e * 50 + id] = r;
     }
-    // bit 0: an unphysical node (limit every variable); bit 1: a node needs the fix
-    if (SYS == 1 && t == 0 && a.unphys) a.unphys[e] = (anybad ? 1 : 0) | (anyfix ? 2 : 0);
+    if (SYS == 1 && t == 0 && a.flags) a.flags[e] = (anybad ? 1 : 0) | (anyfix ? 2 : 0);
 }
 
 // ---------------------------------------------------------------------------
-// Limiter of the mixed path, one warp per element (decision as in k_limit).
-// final_pass == 0: stage outputs held as increments; troubled variables get
-//   D = (U0 + sum_a slope_a (x_a - x_a0)) - U^n.
-// final_pass == 1: U^{n+1} = U^n + D3 at every node (FP64), the linear
-//   replacement in troubled variables, then the SR fix in FP64, in place.
+// Limiter of the mixed path on FP64 stage states, one warp per element: the
+// decision of k_limit (FP64 comparisons on the summaries), the linear replacement
+// U0 + sum_a slope_a (x_a - x_a0) (eq:MinModSol) in FP64, then (SR) the conserved
+// fix on every node of the visited element.  Elements that are neither troubled
+// nor flagged as needing the fix are left alone.
 struct LimitMixedArgs {
-    double *U;              // U^n in, U^{n+1} out (final pass)
-    float *Dv;              // increments of the stage output
+    double *U;
     const double *S;
-    const unsigned char *unphys;
+    const unsigned char *flags;
     unsigned char *troubled;
     long long E;
     int K[3];
     int limiter;
-    int final_pass;
     double tvb_M, beta;
     double dx[3];
     double d_atm, tau_atm;
-    double x[MAXN];
+    double hx[3][MAXN];     // 0.5 dx_a xbar_i
 };
-
-// FP32 screen of the conserved-fix bounds; nodes that fail it are decided in FP64.
-__device__ __forceinline__ bool sr_fix_screen32(const float u[5], float d_atm, float tau_atm)
-{
-    const float s2 = u[1] * u[1] + u[2] * u[2] + u[3] * u[3];
-    return !(u[0] > 2.0f * d_atm) || !(u[4] > 2.0f * tau_atm * u[0]) ||
-           !(s2 < 0.999f * u[4] * (u[4] + 2.0f * u[0]));
-}
 
 template <int NP, int SYS>
 __global__ void __launch_bounds__(256) k_limit_mixed(const LimitMixedArgs a)
@@ -582,7 +582,7 @@ __global__ void __launch_bounds__(256) k_limit_mixed(const LimitMixedArgs a)
     int flag = 0;
     double sl[3] = {0.0, 0.0, 0.0};
     double U0 = 0.0;
-    if (lane < 5 && a.limiter != 0) {
+    if (lane < 5) {
         const int v = lane;
         const double *Se = a.S + (e * 5 + v) * 10;
         U0 = Se[0];
@@ -601,64 +601,41 @@ __global__ void __launch_bounds__(256) k_limit_mixed(const LimitMixedArgs a)
         }
     }
     unsigned mask = __ballot_sync(0xffffffffu, flag) & 0x1fu;
-    const unsigned char uf = (a.limiter != 0 && a.unphys) ? a.unphys[e] : 0;
-    if (uf & 1) mask = 0x1fu;
+    const unsigned char fl = a.flags ? a.flags[e] : 0;
+    if (fl & 1) mask = 0x1fu;
     if (lane == 0 && a.troubled) a.troubled[e] = (unsigned char)mask;
-    if (!mask && !(uf & 2) && !a.final_pass) return;
-    // the replacement U0 + sum_a slope_a (x_a - x_a0) (eq:MinModSol) is formed as an
-    // FP32 increment of U^n about the FP64 anchor U0 - U^n
-    double m0[5];
-    float s0[5], s1[5], s2[5];
+    if (!mask && !(fl & 2)) return;
+    double m0[5], s0[5], s1[5], s2[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
         m0[v] = __shfl_sync(0xffffffffu, U0, v);
-        s0[v] = f64_to_f32(__shfl_sync(0xffffffffu, sl[0], v));
-        s1[v] = f64_to_f32(__shfl_sync(0xffffffffu, sl[1], v));
-        s2[v] = f64_to_f32(__shfl_sync(0xffffffffu, sl[2], v));
+        s0[v] = __shfl_sync(0xffffffffu, sl[0], v);
+        s1[v] = __shfl_sync(0xffffffffu, sl[1], v);
+        s2[v] = __shfl_sync(0xffffffffu, sl[2], v);
     }
-    const float hx0 = f64_to_f32(0.5 * a.dx[0]), hx1 = f64_to_f32(0.5 * a.dx[1]), hx2 = f64_to_f32(0.5 * a.dx[2]);
     for (int q = lane; q < NN; q += 32) {
         const int i = q % NP, j = (q / NP) % NP, k = q / (NP * NP);
-        const float xi = f64_to_f32(a.x[i]) * hx0, xj = f64_to_f32(a.x[j]) * hx1, xk = f64_to_f32(a.x[k]) * hx2;
-        double un[5];
-        float d[5], u32[5];
+        double u[5];
         unsigned nm = mask;
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
             const long long ix = (e * 5 + v) * NN + q;
-            un[v] = a.U[ix];
-            if (mask & (1u << v))
-                d[v] = f64_to_f32(m0[v] - un[v]) + (s0[v] * xi + s1[v] * xj + s2[v] * xk);
-            else
-                d[v] = a.Dv[ix];
-            u32[v] = f64_to_f32(un[v]) + d[v];
+            u[v] = (mask & (1u << v)) ? m0[v] + s0[v] * a.hx[0][i] + s1[v] * a.hx[1][j] + s2[v] * a.hx[2][k]
+                                      : a.U[ix];
         }
-        double u64[5];
-        bool exact = false;
-        if (SYS == 1 && sr_fix_screen32(u32, (float)a.d_atm, (float)a.tau_atm)) {
-            // the conserved fix after the replacement (Sec. 2.1.4, Sec. 3.3), in FP64
-#pragma unroll
-            for (int v = 0; v < 5; ++v) u64[v] = un[v] + f32_to_f64(d[v]);
-            double w[5] = {u64[0], u64[1], u64[2], u64[3], u64[4]};
-            if (sr_fix(a.d_atm, a.tau_atm, w)) {
-                exact = a.final_pass != 0;
+        if (SYS == 1) {
+            double w[5] = {u[0], u[1], u[2], u[3], u[4]};
+            if (sr_fix(a.d_atm, a.tau_atm, w))
 #pragma unroll
                 for (int v = 0; v < 5; ++v)
-                    if (w[v] != u64[v]) {
+                    if (w[v] != u[v]) {
                         nm |= 1u << v;
-                        d[v] = f64_to_f32(w[v] - un[v]);
-                        u64[v] = w[v];
+                        u[v] = w[v];
                     }
-            }
         }
 #pragma unroll
-        for (int v = 0; v < 5; ++v) {
-            const long long ix = (e * 5 + v) * NN + q;
-            if (a.final_pass)
-                a.U[ix] = exact ? u64[v] : un[v] + f32_to_f64(d[v]);
-            else if (nm & (1u << v))
-                a.Dv[ix] = d[v];
-        }
+        for (int v = 0; v < 5; ++v)
+            if (nm & (1u << v)) a.U[(e * 5 + v) * NN + q] = u[v];
     }
 }
 
@@ -666,7 +643,7 @@ template <int NP>
 cudaError_t launch_stage_mixed_np(int system, int flux, const MixedArgs &a, long long E, cudaStream_t s)
 {
     const dim3 grid((unsigned)E), block(round_up32(NP * NP * NP));
-    const size_t smem = sizeof(float) * 29 * NP * NP * NP;
+    const size_t smem = sizeof(float) * (25 + NPRIM) * NP * NP * NP;
     void (*kern)(const MixedArgs);
     if (system == 0 && flux == 0) kern = k_stage_mixed<NP, 0, 0>;
     else if (system == 0) kern = k_stage_mixed<NP, 0, 1>;

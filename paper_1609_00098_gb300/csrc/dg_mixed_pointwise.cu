@@ -1,6 +1,6 @@
 // dg_mixed_pointwise.cu -- node-wise kernels of the mixed-precision path: the
-// CFL pass (FP32 primitives of U^n, the largest wave speed, and the pressures
-// that warm-start the first stage's con2prim) and FP32 -> FP64 widening.
+// CFL pass: FP32 primitives of U^n, the largest wave speed, and the pressures
+// that warm-start the first stage's con2prim.
 #include "dg_mixed.cuh"
 
 namespace dg {
@@ -21,28 +21,14 @@ __global__ void __launch_bounds__(kThreads) k_cfl_mixed(const double *Un, const 
          g += (long long)gridDim.x * blockDim.x) {
         const long long e = g / nn;
         const int q = (int)(g - e * nn);
-        float u[5], P[4];
+        float u[5], P[NPRIM];
 #pragma unroll
         for (int v = 0; v < 5; ++v) u[v] = f64_to_f32(Un[(e * 5 + v) * nn + q]);
         if (SYS == 0) {
             ne_primitives32(gamma, u, P);
         } else {
-            float kappa = 1.0f;
-            const int st = sr_con2prim32(gamma, u, pin ? pin[g] : -1.0f, P, kappa);
-            if (st != 0 || kappa > kappa_sw) {
-                double u64[5], Pd[4];
-#pragma unroll
-                for (int v = 0; v < 5; ++v) u64[v] = Un[(e * 5 + v) * nn + q];
-                int st64 = 1;
-                if (st == 0) st64 = sr_polish64(gamma_d, u64, f32_to_f64(P[3]), Pd);
-                if (st64 != 0) {
-                    sr_fix(d_atm, tau_atm, u64);
-                    st64 = sr_polish64(gamma_d, u64, (pin && pin[g] >= 0.0f) ? f32_to_f64(pin[g]) : -1.0, Pd);
-                }
-                if (st64) errs |= ERRBIT_C2P;
-#pragma unroll
-                for (int c = 0; c < 4; ++c) P[c] = f64_to_f32(Pd[c]);
-            }
+            errs |= sr_prims_mixed(gamma, gamma_d, kappa_sw, d_atm, tau_atm, u, Un + e * 5 * nn + q, nn,
+                                   pin ? pin[g] : -1.0f, P);
             pout[g] = P[3];
         }
 #pragma unroll
@@ -62,13 +48,6 @@ __global__ void __launch_bounds__(kThreads) k_cfl_mixed(const double *Un, const 
         for (int w = 1; w < kThreads / 32; ++w) m = fmaxf(m, red[w]);
         atomicMax(lam, (unsigned long long)__double_as_longlong(f32_to_f64(m)));
     }
-}
-
-__global__ void __launch_bounds__(kThreads) k_widen(const float *in, double *out, long long count)
-{
-    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < count;
-         g += (long long)gridDim.x * blockDim.x)
-        out[g] = f32_to_f64(in[g]);
 }
 
 unsigned grid_for(long long count)
@@ -92,12 +71,6 @@ cudaError_t launch_cfl_mixed(const dg_mesh *m, const double *Un, const float *pi
         k_cfl_mixed<1><<<grid_for(total), kThreads, 0, s>>>(Un, pin, pout, m->lam, m->err, total, m->nn,
                                                             (float)m->d.gamma, m->d.gamma, kappa_sw, m->d.d_atm,
                                                             m->d.tau_atm);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_widen(const float *in, double *out, long long count, cudaStream_t s)
-{
-    k_widen<<<grid_for(count), kThreads, 0, s>>>(in, out, count);
     return cudaGetLastError();
 }
 
