@@ -132,7 +132,7 @@ dg_status dg_limiter_summaries(dg_mesh *mesh, const double *U, double *S, void *
 dg_status dg_con2prim(long long count, double gamma, const double *cons, double *prim,
                       const double *p_guess, int *iters, int *status, void *stream);
 
-/* ---- Learned starting guess for SR con2prim (BASELINE addition on top of Sec. 2.1.2) ----
+/* ---- Learned starting guess for SR con2prim (an addition to the method of Sec. 2.1.2; the paper has no counterpart) ----
  * A 3 -> 64 -> 64 -> 1 SiLU MLP maps three scaled invariants of (D, S, tau) to a
  * scaled log pressure; dg_con2prim's safeguarded Newton starts from it, so results
  * change only in iteration count.  Parameters are FP32, laid out flat as

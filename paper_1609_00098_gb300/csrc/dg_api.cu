@@ -365,12 +365,12 @@ LimitMixedArgs limit_mixed_args(const dg_mesh *m, double *U, unsigned char *trou
     l.E = m->E;
     for (int ax = 0; ax < 3; ++ax) {
         l.K[ax] = m->d.K[ax];
-        l.dx[ax] = m->dx[ax];
+        l.tvb[ax] = m->d.tvb_M * m->dx[ax] * m->dx[ax];
+        l.inv_dx[ax] = 1.0 / m->dx[ax];
+        l.beta_dx[ax] = m->d.beta / m->dx[ax];
         for (int i = 0; i < MAXN; ++i) l.hx[ax][i] = 0.5 * m->dx[ax] * m->T.x[i];
     }
     l.limiter = m->d.limiter;
-    l.tvb_M = m->d.tvb_M;
-    l.beta = m->d.beta;
     l.d_atm = m->d.d_atm;
     l.tau_atm = m->d.tau_atm;
     return l;

@@ -552,11 +552,14 @@ __global__ void __launch_bounds__(round_up32(NP *NP *NP)) k_stage_mixed(const Mi
 }
 
 // ---------------------------------------------------------------------------
-// Limiter of the mixed path on FP64 stage states, one warp per element: the
-// decision of k_limit (FP64 comparisons on the summaries), the linear replacement
-// U0 + sum_a slope_a (x_a - x_a0) (eq:MinModSol) in FP64, then (SR) the conserved
-// fix on every node of the visited element.  Elements that are neither troubled
-// nor flagged as needing the fix are left alone.
+// Limiter of the mixed path on FP64 stage states, one warp per element.  Lane
+// 3v + a (v < 5, a < 3) decides variable v along axis a: the MinModN face tests
+// of Sec. 3.3.2 (tolerance 1e-8, M = 0) and the m_B slope (eq:MinModB) in FP64,
+// with the divisions by dx and dx/beta taken as products with host reciprocals.
+// A limited variable becomes U0 + sum_a slope_a (x_a - x_a0) (eq:MinModSol) in
+// FP64; then (SR) the conserved fix of Sec. 2.1.4 runs in FP64 on every node that
+// an FP32 screen of its bounds does not clear.  Elements that are neither
+// troubled nor flagged by the stage kernel as needing the fix are left alone.
 struct LimitMixedArgs {
     double *U;
     const double *S;
@@ -565,8 +568,9 @@ struct LimitMixedArgs {
     long long E;
     int K[3];
     int limiter;
-    double tvb_M, beta;
-    double dx[3];
+    double tvb[3];          // M dx_a^2
+    double inv_dx[3];       // 1 / dx_a
+    double beta_dx[3];      // beta / dx_a
     double d_atm, tau_atm;
     double hx[3][MAXN];     // 0.5 dx_a xbar_i
 };
@@ -580,27 +584,28 @@ __global__ void __launch_bounds__(256) k_limit_mixed(const LimitMixedArgs a)
     if (warp >= a.E) return;
     const long long e = warp;
     int flag = 0;
-    double sl[3] = {0.0, 0.0, 0.0};
-    double U0 = 0.0;
-    if (lane < 5) {
-        const int v = lane;
+    double sl = 0.0, U0 = 0.0;
+    if (lane < 15) {
+        const int v = lane / 3, ax = lane % 3;
         const double *Se = a.S + (e * 5 + v) * 10;
         U0 = Se[0];
+        const double U0m = a.S[(elem_neighbour(e, a.K, ax, -1) * 5 + v) * 10];
+        const double U0p = a.S[(elem_neighbour(e, a.K, ax, +1) * 5 + v) * 10];
         flag = (a.limiter == 2);
-        for (int ax = 0; ax < 3; ++ax) {
-            const double U0m = a.S[(elem_neighbour(e, a.K, ax, -1) * 5 + v) * 10];
-            const double U0p = a.S[(elem_neighbour(e, a.K, ax, +1) * 5 + v) * 10];
+        if (a.limiter == 1) {
             const double ulo = Se[1 + 2 * ax], uhi = Se[2 + 2 * ax];
-            if (a.limiter == 1) {
-                const double vl = U0 - minmodB(U0 - ulo, U0 - U0m, U0p - U0, 0.0, a.dx[ax]);
-                const double vr = U0 + minmodB(uhi - U0, U0 - U0m, U0p - U0, 0.0, a.dx[ax]);
-                if (fabs(vl - ulo) > 1e-8 || fabs(vr - uhi) > 1e-8) flag = 1;
-            }
-            const double h = a.dx[ax] / a.beta;
-            sl[ax] = minmodB(2.0 * Se[7 + ax] / a.dx[ax], (U0p - U0) / h, (U0 - U0m) / h, a.tvb_M, a.dx[ax]);
+            const double vl = U0 - minmod3(U0 - ulo, U0 - U0m, U0p - U0);
+            const double vr = U0 + minmod3(uhi - U0, U0 - U0m, U0p - U0);
+            if (fabs(vl - ulo) > 1e-8 || fabs(vr - uhi) > 1e-8) flag = 1;
         }
+        const double s1 = 2.0 * Se[7 + ax] * a.inv_dx[ax];
+        sl = (fabs(s1) <= a.tvb[ax]) ? s1 : minmod3(s1, (U0p - U0) * a.beta_dx[ax], (U0 - U0m) * a.beta_dx[ax]);
     }
-    unsigned mask = __ballot_sync(0xffffffffu, flag) & 0x1fu;
+    const unsigned fb = __ballot_sync(0xffffffffu, flag);
+    unsigned mask = 0;
+#pragma unroll
+    for (int v = 0; v < 5; ++v)
+        if ((fb >> (3 * v)) & 7u) mask |= 1u << v;
     const unsigned char fl = a.flags ? a.flags[e] : 0;
     if (fl & 1) mask = 0x1fu;
     if (lane == 0 && a.troubled) a.troubled[e] = (unsigned char)mask;
@@ -608,30 +613,35 @@ __global__ void __launch_bounds__(256) k_limit_mixed(const LimitMixedArgs a)
     double m0[5], s0[5], s1[5], s2[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
-        m0[v] = __shfl_sync(0xffffffffu, U0, v);
-        s0[v] = __shfl_sync(0xffffffffu, sl[0], v);
-        s1[v] = __shfl_sync(0xffffffffu, sl[1], v);
-        s2[v] = __shfl_sync(0xffffffffu, sl[2], v);
+        m0[v] = __shfl_sync(0xffffffffu, U0, 3 * v);
+        s0[v] = __shfl_sync(0xffffffffu, sl, 3 * v);
+        s1[v] = __shfl_sync(0xffffffffu, sl, 3 * v + 1);
+        s2[v] = __shfl_sync(0xffffffffu, sl, 3 * v + 2);
     }
     for (int q = lane; q < NN; q += 32) {
         const int i = q % NP, j = (q / NP) % NP, k = q / (NP * NP);
         double u[5];
-        unsigned nm = mask;
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
             const long long ix = (e * 5 + v) * NN + q;
             u[v] = (mask & (1u << v)) ? m0[v] + s0[v] * a.hx[0][i] + s1[v] * a.hx[1][j] + s2[v] * a.hx[2][k]
                                       : a.U[ix];
         }
+        unsigned nm = mask;
         if (SYS == 1) {
-            double w[5] = {u[0], u[1], u[2], u[3], u[4]};
-            if (sr_fix(a.d_atm, a.tau_atm, w))
+            float u32[5];
 #pragma unroll
-                for (int v = 0; v < 5; ++v)
-                    if (w[v] != u[v]) {
-                        nm |= 1u << v;
-                        u[v] = w[v];
-                    }
+            for (int v = 0; v < 5; ++v) u32[v] = f64_to_f32(u[v]);
+            if (sr_screen32(u32, (float)a.d_atm, (float)a.tau_atm)) {
+                double w[5] = {u[0], u[1], u[2], u[3], u[4]};
+                if (sr_fix(a.d_atm, a.tau_atm, w))
+#pragma unroll
+                    for (int v = 0; v < 5; ++v)
+                        if (w[v] != u[v]) {
+                            nm |= 1u << v;
+                            u[v] = w[v];
+                        }
+            }
         }
 #pragma unroll
         for (int v = 0; v < 5; ++v)
