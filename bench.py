@@ -1,6 +1,9 @@
 #!/usr/bin/env python
 """DG-RK3 throughput (dof-updates/s) of the nodal DG hot path on GB300: the
-mixed-precision path (headline `value`) and the plain FP64 path (`plain_fp64`).
+mixed-precision path with the learned con2prim guess (headline `value`), the
+same path warm-started from the previous pass's pressures (`mixed_warm_start`),
+and the plain FP64 path (`plain_fp64`).  The guess network is trained first
+(untimed) on pairs the method generates.
 
 Workload: 3D special-relativistic blast on a periodic unit cube, 16^3 affine
 elements, 5 LGL nodes per axis (512,000 nodes x 5 conserved variables),
@@ -29,6 +32,8 @@ import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+
+import dg_inputs  # noqa: E402  (seeded input generator, no method arithmetic)
 
 WORKLOAD = dict(system=1, K=(16, 16, 16), n=5, flux=1, limiter=1, gamma=4.0 / 3.0, cfl=0.2, seed=1)
 METRIC = "DG-RK3 dof-updates/s on 1 GB300: plain FP64 vs mixed+learned at equal L2 error"
@@ -117,34 +122,87 @@ TRAFFIC_BYTES_PER_LAUNCH = 37943211.0
 TRAFFIC_SOURCES = ("paper_1609_00098_gb300/csrc/dg_mixed.cuh", "paper_1609_00098_gb300/csrc/dg_physics.cuh",
                    "paper_1609_00098_gb300/csrc/dg_internal.h")
 TRAFFIC_SOURCES_SHA256 = "588ff2c5343eec5384ea413ec5fa2f8b93a7d74c72cf33ca5cd39e51edfb15d9"
+TRAFFIC_VARIANT = "warm_start"
 
 
-def _traffic():
+def _traffic(variant):
     import hashlib
     h = hashlib.sha256()
     for f in TRAFFIC_SOURCES:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
-    return TRAFFIC_BYTES_PER_LAUNCH if h.hexdigest() == TRAFFIC_SOURCES_SHA256 else None
+    ok = h.hexdigest() == TRAFFIC_SOURCES_SHA256 and variant == TRAFFIC_VARIANT
+    return TRAFFIC_BYTES_PER_LAUNCH if ok else None
 
 
-def _algorithmic(nodes, precision):
+def _algorithmic(nodes, precision, learned=False):
     """Compulsory HBM bytes of one fused stage launch, averaged over the 3 stages.
     Both paths keep FP64 stage states: stage 1 reads U^n and writes U^1 (80 B/node);
-    stages 2, 3 read U_s and U^n and write U_{s+1} (120 B/node).  The mixed SR path
-    also reads the previous pass's FP32 pressure (4 B) and writes its own (4 B)."""
-    if precision == 0:
+    stages 2, 3 read U_s and U^n and write U_{s+1} (120 B/node).  The warm-started
+    mixed SR path also reads the previous pass's FP32 pressure (4 B) and writes its
+    own (4 B); with the learned guess computed in the kernel it carries none."""
+    if precision == 0 or learned:
         return nodes * (80 + 120 + 120) / 3.0
     return nodes * (88 + 128 + 128) / 3.0
 
 
-def _measure(pkg, torch, precision, args, dist, U0):
+def _train_guess_net(pkg, torch):
+    """Train the learned con2prim guess (untimed) on pairs the method generates for
+    this problem class: the conserved states and FP64 pressures of the first six
+    FP64 steps of the same blast with another noise seed (2), 2^18 pairs sampled
+    from them, plus 2^16 states of the generic con2prim distribution (rho
+    log-uniform [1e-8, 10], W uniform [1, 10], eps log-uniform [1e-6, 1e2]).
+    Twenty epochs of Adam, batch 2048."""
+    w = WORKLOAD
+    g = w["gamma"]
+    mesh = pkg.Mesh(system=w["system"], K=w["K"], n=w["n"], flux=w["flux"], limiter=w["limiter"], gamma=g)
+    xyz = mesh.coords().cpu().numpy()
+    U = mesh.from_prim(torch.from_numpy(dg_inputs.blast_sr(xyz, seed=2)).cuda())
+    cons, pres = [], []
+    P = torch.empty((mesh.E, 4, mesh.nn), dtype=torch.float64, device="cuda")
+    for _ in range(6):
+        pkg.abi.dg_primitives(mesh.h, U, P)
+        cons.append(U.permute(1, 0, 2).reshape(5, -1).clone())
+        pres.append(P[:, 3, :].reshape(-1).clone())
+        mesh.rk3_step(U, cfl=w["cfl"])
+    mesh.close()
+    cons, pres = torch.cat(cons, 1), torch.cat(pres)
+    gen = torch.Generator().manual_seed(2)
+    pick = torch.randperm(cons.shape[1], generator=gen)[: 1 << 18].cuda()
+    n_gen = 1 << 16
+    prim = torch.from_numpy(np.ascontiguousarray(dg_inputs.c2p_samples(7, n_gen, gamma=g))).cuda()
+    helper = pkg.Mesh(system=1, K=(16, 8, 8), n=4, gamma=g)   # 1024 x 64 = 2^16 nodes
+    Ug = helper.state()
+    pkg.abi.dg_prim2con(helper.h, prim, Ug)
+    helper.close()
+    cons = torch.cat([cons[:, pick], Ug.permute(1, 0, 2).reshape(5, n_gen)], 1).contiguous()
+    pres = torch.cat([pres[pick], prim[4]]).contiguous()
+    n_samp = cons.shape[1]
+    init = dg_inputs.uniform(5, 9, np.arange(pkg.abi.N_NET_PARAMS))
+    params = np.zeros(pkg.abi.N_NET_PARAMS)
+    for o, fan, cnt in ((0, 3, 192), (256, 64, 4096), (4416, 64, 64)):  # W1, W2, W3: U(+-sqrt(3/fan_in))
+        params[o:o + cnt] = np.sqrt(3.0 / fan) * (2.0 * init[o:o + cnt] - 1.0)
+    net = pkg.abi.dg_c2p_net_create(params.astype(np.float32), (-5.0, 4.0, -9.0, 3.0, -4.5, 4.5))
+    epochs = 20
+    losses = torch.zeros(epochs, dtype=torch.float32, device="cuda")
+    t0 = time.time()
+    pkg.abi.dg_c2p_net_train(net, n_samp, cons, pres, epochs, 2048, 2e-3, losses)
+    torch.cuda.synchronize()
+    info = {"pairs": n_samp, "source": "blast seed 2, FP64 steps 0-5 (2^18) + generic con2prim states (2^16)",
+            "epochs": epochs, "batch": 2048, "train_s": round(time.time() - t0, 3),
+            "loss_first_last": [float(losses[0]), float(losses[-1])]}
+    return net, info
+
+
+def _measure(pkg, torch, precision, args, dist, U0, net=None):
     """Warm-up, then K graph-replayed steps timed with per-step CUDA events (L2
     flushed between steps, outside the event pairs), then K profiled steps for
     per-kernel durations."""
     w = WORKLOAD
     mesh = pkg.Mesh(system=w["system"], K=w["K"], n=w["n"], flux=w["flux"], limiter=w["limiter"],
                     gamma=w["gamma"], precision=precision)
+    if net is not None:
+        mesh.set_c2p_net(net)
     U = U0.clone()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     for _ in range(args.warmup):
@@ -203,31 +261,37 @@ def run_ours(args):
                      gamma=w["gamma"])
     nodes = setup.E * setup.nn
     U0 = _init_state(pkg, setup, torch)
+    net, net_info = _train_guess_net(pkg, torch)
 
-    # accuracy at equal time steps (untimed): mixed vs plain FP64 after a few steps
+    # accuracy at equal time steps (untimed): mixed (learned guess, and warm
+    # start) vs plain FP64 after a few steps
     mixed_acc = None
     if not args.no_accuracy:
-        mix = pkg.Mesh(system=w["system"], K=w["K"], n=w["n"], flux=w["flux"], limiter=w["limiter"],
-                       gamma=w["gamma"], precision=1)
-        Uf, Um = U0.clone(), U0.clone()
-        dtv = torch.zeros(1, dtype=torch.float64, device="cuda")
-        for _ in range(args.acc_steps):
-            setup.rk3_step(Uf, cfl=w["cfl"], dt_used=dtv)
-            mix.rk3_step(Um, dt=float(dtv.item()))
-        torch.cuda.synchronize()
-        num = torch.sqrt(((Um - Uf) ** 2).sum(dim=(0, 2)))
-        den = torch.sqrt((Uf ** 2).sum(dim=(0, 2)))
-        rel = (num / torch.clamp(den, min=1e-3 * float(den.max()))).cpu().tolist()
-        mixed_acc = {"steps": args.acc_steps, "rel_l2_vs_fp64_per_var": rel, "max": max(rel)}
-        mix.close()
+        mixed_acc = {}
+        for name, use_net in (("learned", net), ("warm_start", None)):
+            mix = pkg.Mesh(system=w["system"], K=w["K"], n=w["n"], flux=w["flux"], limiter=w["limiter"],
+                           gamma=w["gamma"], precision=1)
+            if use_net is not None:
+                mix.set_c2p_net(use_net)
+            Uf, Um = U0.clone(), U0.clone()
+            dtv = torch.zeros(1, dtype=torch.float64, device="cuda")
+            for _ in range(args.acc_steps):
+                setup.rk3_step(Uf, cfl=w["cfl"], dt_used=dtv)
+                mix.rk3_step(Um, dt=float(dtv.item()))
+            torch.cuda.synchronize()
+            num = torch.sqrt(((Um - Uf) ** 2).sum(dim=(0, 2)))
+            den = torch.sqrt((Uf ** 2).sum(dim=(0, 2)))
+            rel = (num / torch.clamp(den, min=1e-3 * float(den.max()))).cpu().tolist()
+            mixed_acc[name] = {"steps": args.acc_steps, "rel_l2_vs_fp64_per_var": rel, "max": max(rel)}
+            mix.close()
     setup.close()
 
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
     results = {}
-    for precision in (1, 0):
-        results[precision] = _measure(pkg, torch, precision, args, dist, U0)
+    for key, precision, use_net in (("learned", 1, net), ("warm_start", 1, None), ("fp64", 0, None)):
+        results[key] = _measure(pkg, torch, precision, args, dist, U0, use_net)
     clk = clocks.stop()
 
     def agg(ms):
@@ -238,12 +302,14 @@ def run_ours(args):
             total = float(t.item())
         return total
 
-    mesh, graph, step_ms, prof, status, mesh_state = results[1]
+    mesh, graph, step_ms, prof, status, mesh_state = results["learned"]
     total_ms = agg(step_ms)
     ms_per_step = total_ms / args.steps
     value = ws * nodes * 5 * args.steps / (total_ms / 1e3)
-    f_mesh, f_graph, f_ms, f_prof, f_status, _ = results[0]
+    f_mesh, f_graph, f_ms, f_prof, f_status, _ = results["fp64"]
     f_total = agg(f_ms)
+    w_mesh, w_graph, w_ms, w_prof, w_status, _ = results["warm_start"]
+    w_total = agg(w_ms)
 
     # end to end through the C ABI with host buffers (mixed path): every step copies
     # the state from pinned host memory to the device, advances it, and copies it
@@ -282,26 +348,33 @@ def run_ours(args):
 
     st_ms, st_n = prof["stage"]
     stage_avg_s = (st_ms / st_n) / 1e3 if st_n else float("nan")
-    achieved = _algorithmic(nodes, 1) / stage_avg_s / 1e9
+    achieved = _algorithmic(nodes, 1, learned=True) / stage_avg_s / 1e9
     launches = int(sum(c for _, c in prof.values()))
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 arithmetic, f64 state and RK accumulation",
         "data": "synthetic (seeded blast initial data)",
-        "config": _config({"precision": "mixed", "parallelism": "replicas" if ws > 1 else "single GPU",
+        "config": _config({"precision": "mixed", "c2p_guess": "learned (in-kernel MLP)",
+                           "parallelism": "replicas" if ws > 1 else "single GPU",
                            "step_launch": "CUDA graph replay"}),
-        "variant": "mixed (FP32 con2prim/fluxes/contraction/face fluxes, FP64 stage states and RK accumulation)",
+        "variant": "mixed+learned (FP32 con2prim from the in-kernel MLP guess, FP32 fluxes/contraction/face "
+                   "fluxes, FP64 stage states and RK accumulation)",
         "plain_fp64": {"value": ws * nodes * 5 * args.steps / (f_total / 1e3), "unit": UNIT,
                        "ms_per_step": f_total / args.steps, "kernels": kern(f_prof), "device_status": f_status},
         "speedup_vs_plain_fp64": f_total / total_ms,
+        "mixed_warm_start": {"value": ws * nodes * 5 * args.steps / (w_total / 1e3), "unit": UNIT,
+                             "ms_per_step": w_total / args.steps, "kernels": kern(w_prof),
+                             "device_status": w_status,
+                             "note": "con2prim starts from the previous pass's pressure (8 B/node/stage carried)"},
+        "c2p_net": net_info,
         "mixed_accuracy": mixed_acc,
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes},
         "gpu_launches": launches,
         "kernels": kern(prof),
         "roofline": {"kernel": "k_stage_mixed (fused con2prim + RHS + SSP-RK3 stage update + limiter summaries)", "bound": "hbm",
                      "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                     "traffic": _traffic(), "bytes_per_launch": _algorithmic(nodes, 1),
+                     "traffic": _traffic("learned"), "bytes_per_launch": _algorithmic(nodes, 1, learned=True),
                      "avg_launch_ms": stage_avg_s * 1e3,
                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks else "fallback"},
         "clocks": clk,
@@ -311,6 +384,7 @@ def run_ours(args):
         out["cpu_baseline"] = cpu_baseline(seconds=args.cpu_seconds)
     for r in results.values():
         r[0].close()
+    pkg.abi.dg_c2p_net_destroy(net)
     if dist:
         dist.destroy_process_group()
     if rank == 0:

@@ -151,11 +151,15 @@ void dg_c2p_net_destroy(dg_c2p_net *net);
 /* Copy the current FP32 parameters to the host array params[DG_C2P_NET_PARAMS]. */
 dg_status dg_c2p_net_get_params(const dg_c2p_net *net, float *params);
 /* Pressure guesses E 10^(y y_scale + y_shift), clamped into [max(0, s-E), (gamma-1) tau],
- * for `count` conserved states (5 device rows as in dg_con2prim) into p_guess (device). */
+ * for `count` conserved states (5 device rows as in dg_con2prim) into p_guess (device).
+ * States whose features are not finite (D or tau not positive) get -1, which
+ * dg_con2prim reads as "use the standard guess". */
 dg_status dg_c2p_net_guess(dg_c2p_net *net, long long count, double gamma, const double *cons, double *p_guess,
                            void *stream);
 /* Mean squared error of the scaled target over `count` states with true pressures p
- * (device), and its gradient: grad (device, DG_C2P_NET_PARAMS floats), loss (device, 1). */
+ * (device), and its gradient: grad (device, DG_C2P_NET_PARAMS floats), loss (device, 1).
+ * States whose features or target are not finite in FP32 (D or tau not positive,
+ * p below the FP32 range) contribute zero to the loss and to the gradient. */
 dg_status dg_c2p_net_grad(dg_c2p_net *net, long long count, const double *cons, const double *p, float *grad,
                           float *loss, void *stream);
 /* `epochs` passes over the data in order, mini-batches of `batch`, one Adam step
@@ -179,6 +183,19 @@ dg_status dg_c2p_net_train(dg_c2p_net *net, long long count, const double *cons,
  * values in dUdt. */
 #define DG_RHS_STATIC_MAX_NODES 131072
 dg_status dg_rhs_static(const dg_mesh_desc *desc, const double *U, double *dUdt, void *stream);
+
+/* Attach a learned-guess network to a mixed-precision SR mesh (net == NULL
+ * detaches it).  With a network attached, every con2prim inside dg_rhs and
+ * dg_rk3_step's stages starts its FP32 Newton from the network's guess, computed
+ * in the stage kernel for the element's nodes and its neighbours' face nodes;
+ * without one, it starts from the pressure of the previous pass (carried in
+ * library scratch).  Newton stays the judge: the guess changes only the
+ * iteration count and the result within the solver's stopping tolerance.  The
+ * mesh does not own the network: it must stay alive while the mesh uses it, and
+ * training it in place changes the guesses of later calls.  Errors: DG_ERR_ARG
+ * when the mesh is not (mixed, SR) and net != NULL.  Not in the paper (an
+ * addition to Sec. 2.1.2). */
+dg_status dg_mesh_set_c2p_net(dg_mesh *mesh, const dg_c2p_net *net);
 
 /* Synchronise `stream`, then read and clear the mesh's device status word.
  * Returns DG_OK, DG_ERR_C2P or DG_ERR_UNPHYSICAL (first set), or DG_ERR_CUDA. */

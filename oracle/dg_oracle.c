@@ -258,7 +258,9 @@ void or_prim2con(int system, double gamma, long long count, const double *prim, 
  *             = tau - v^2 [ (E + p) - D W/(W+1) ]          (no cancellation at small v)
  * f is increasing with f'(p) = 1 - (g-1) v^2 (1 - D W/(E+p)).  The root lies in
  * [max(0, s-E), (g-1) tau] because tau >= rho eps for W >= 1.  Safeguarded
- * Newton: a step leaving the bracket is replaced by bisection; the bracket is
+ * Newton: a step leaving the bracket is replaced by bisection, except a step
+ * landing exactly on an end that is still its a-priori bound (at v = 0 the root
+ * is the upper bound (g-1) tau itself); the bracket is
  * updated from the sign of f.  Stop once |dp| <= 2^-48 p, then take one more
  * Newton step so the result does not depend on the starting guess.
  * Returns 0 ok, 1 unphysical input, 2 no convergence. */
@@ -295,13 +297,15 @@ static int c2p_node(double g, const double *u, double guess, double *pr, int *it
     if (p < plo) p = plo;
     if (p > phi) p = phi;
     int status = 2;
+    int lo_moved = 0, hi_moved = 0; /* an end still at its a-priori bound may be landed on */
     int it = 0;
     for (; it < 200; ++it) {
         c2p_eval r = c2p_f(g, D, s2, tau, p);
         if (r.f == 0.0) { status = 0; break; }
-        if (r.f > 0.0) phi = p; else plo = p;
+        if (r.f > 0.0) { phi = p; hi_moved = 1; } else { plo = p; lo_moved = 1; }
         double pn = p - r.f / r.df;
-        if (!(pn > plo && pn < phi)) pn = 0.5 * (plo + phi);
+        if (!((pn > plo && pn < phi) || (pn == phi && !hi_moved) || (pn == plo && !lo_moved)))
+            pn = 0.5 * (plo + phi);
         const double dp = fabs(pn - p);
         p = pn;
         if (dp <= 0x1p-48 * p) {

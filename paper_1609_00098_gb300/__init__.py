@@ -93,3 +93,7 @@ class Mesh:
 
     def sync_status(self) -> int:
         return abi.dg_sync_status(self.h)
+
+    def set_c2p_net(self, net):
+        """Attach (or with None detach) a learned con2prim guess network."""
+        abi.dg_mesh_set_c2p_net(self.h, net)

@@ -66,6 +66,7 @@ SIGNATURES = {
     "dg_limiter_summaries": (_i, [_vp, _vp, _vp, _vp]),
     "dg_con2prim": (_i, [_ll, _d, _vp, _vp, _vp, _vp, _vp, _vp]),
     "dg_sync_status": (_i, [_vp, _vp]),
+    "dg_mesh_set_c2p_net": (_i, [_vp, _vp]),
     "dg_c2p_net_create": (_i, [_vp, _vp, ctypes.POINTER(_vp)]),
     "dg_c2p_net_destroy": (None, [_vp]),
     "dg_c2p_net_get_params": (_i, [_vp, _vp]),
@@ -251,6 +252,11 @@ def dg_con2prim(count, gamma, cons, prim, p_guess=None, iters=None, status=None,
 def dg_sync_status(mesh, stream=None) -> int:
     """Returns the status code (does not raise for kernel-side failures)."""
     return load().dg_sync_status(mesh, _stream(stream))
+
+
+def dg_mesh_set_c2p_net(mesh, net):
+    """Attach a learned-guess network to a mixed SR mesh (None detaches)."""
+    _check(load().dg_mesh_set_c2p_net(mesh, net))
 
 
 N_NET_PARAMS = 4481

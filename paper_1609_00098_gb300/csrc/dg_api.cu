@@ -346,6 +346,11 @@ MixedArgs mixed_args(const dg_mesh *m)
     a.d_atm = m->d.d_atm;
     a.tau_atm = m->d.tau_atm;
     a.err = m->err;
+    if (m->net && m->d.system == 1) {
+        const void *w2 = nullptr;
+        net_device_view(m->net, &a.netP, &w2, a.net_sc);
+        a.netW2 = static_cast<const __nv_bfloat16 *>(w2);
+    }
     for (int i = 0; i < MAXN * MAXN; ++i) a.D32[i] = (float)m->T.D[i];
     for (int i = 0; i < MAXN; ++i) {
         a.w64[i] = m->T.w[i];
@@ -572,6 +577,8 @@ static dg_status rk3_step_mixed(dg_mesh *m, double *U, double dt, double cfl, do
     const bool sr = m->d.system == 1;
     const bool lim = m->d.limiter != 0;
     const bool cflmode = cfl > 0.0;
+    // with a learned guess attached, no pressures are carried between passes
+    const bool carry = sr && m->net == nullptr;
     MixedArgs a = mixed_args(m);
     a.Un = U;
     a.dt = dt;
@@ -579,11 +586,11 @@ static dg_status rk3_step_mixed(dg_mesh *m, double *U, double dt, double cfl, do
     a.S = lim ? m->S : nullptr;
     a.flags = (lim && sr) ? m->unphys : nullptr;
     a.mode = 1;
-    float *latest = (sr && m->p_valid) ? m->pbuf[m->pi] : nullptr;
+    float *latest = (carry && m->p_valid) ? m->pbuf[m->pi] : nullptr;
     if (cflmode) {
         DG_CUDA(cudaMemsetAsync(m->lam, 0, sizeof(unsigned long long), s));
-        DG_LAUNCH(m, s, PROF_PRIM, launch_cfl_mixed(m, U, latest, sr ? m->pbuf[1 - m->pi] : nullptr, m->kappa_sw, s));
-        if (sr) {
+        DG_LAUNCH(m, s, PROF_PRIM, launch_cfl_mixed(m, U, latest, carry ? m->pbuf[1 - m->pi] : nullptr, m->kappa_sw, s));
+        if (carry) {
             m->pi = 1 - m->pi;
             latest = m->pbuf[m->pi];
         }
@@ -600,9 +607,9 @@ static dg_status rk3_step_mixed(dg_mesh *m, double *U, double dt, double cfl, do
         a.ca = ca[st];
         a.cb = cb[st];
         a.pin = latest;
-        a.pout = sr ? m->pbuf[1 - m->pi] : nullptr;
+        a.pout = carry ? m->pbuf[1 - m->pi] : nullptr;
         DG_LAUNCH(m, s, PROF_STAGE, launch_stage_mixed(m->d.n, m->d.system, m->d.flux, a, m->E, s));
-        if (sr) {
+        if (carry) {
             m->pi = 1 - m->pi;
             latest = m->pbuf[m->pi];
         }
@@ -611,7 +618,7 @@ static dg_status rk3_step_mixed(dg_mesh *m, double *U, double dt, double cfl, do
             DG_LAUNCH(m, s, PROF_LIMIT, launch_limit_mixed(m->d.n, m->d.system, l, s));
         }
     }
-    m->p_valid = sr ? 1 : 0;
+    m->p_valid = carry ? 1 : 0;
     if (dt_used) {
         if (cflmode) DG_CUDA(cudaMemcpyAsync(dt_used, m->dt, sizeof(double), cudaMemcpyDeviceToDevice, s));
         else DG_CUDA(launch_set(dt_used, dt, s));
@@ -717,6 +724,16 @@ dg_status dg_con2prim(long long count, double gamma, const double *cons, double 
     if (!cons || !prim) return fail(DG_ERR_ARG, "cons and prim must not be NULL");
     if (!(gamma > 1.0)) return fail(DG_ERR_ARG, "gamma must be > 1");
     DG_CUDA(launch_con2prim(count, gamma, cons, prim, p_guess, iters, status, (cudaStream_t)stream));
+    return DG_OK;
+}
+
+dg_status dg_mesh_set_c2p_net(dg_mesh *m, const dg_c2p_net *net)
+{
+    if (dg_status s = check_mesh(m)) return s;
+    if (net && (m->d.system != 1 || m->d.precision != DG_PRECISION_MIXED))
+        return fail(DG_ERR_ARG, "a learned guess can be attached to mixed-precision SR meshes only");
+    m->net = net;
+    m->p_valid = 0;
     return DG_OK;
 }
 

@@ -15,70 +15,16 @@
 #include <cstdint>
 #include <cstring>
 
+#include "dg_c2p_net.cuh"
 #include "dg_mixed.cuh"
 
 namespace dg {
-
-constexpr int NET_PARAMS = 4481;
-constexpr int OFF_W1 = 0, OFF_B1 = 192, OFF_W2 = 256, OFF_B2 = 4352, OFF_W3 = 4416, OFF_B3 = 4480;
-constexpr int NET_TILE = 128;  // samples per CTA, 32 per warp
-constexpr int NET_PARTIAL = NET_PARAMS + 1;  // gradient + loss per CTA
-
-struct NetTileArgs {
-    const float *P;              // FP32 parameters
-    const __nv_bfloat16 *W2b;    // W2 [j][i] in BF16
-    const __nv_bfloat16 *W2tb;   // W2 transposed [i][j] in BF16
-    const double *cons;          // 5 rows of `count`
-    const double *p;             // true pressures (training) or nullptr
-    double *guess;               // output guesses (inference) or nullptr
-    float *partial;              // [gridDim.x][NET_PARTIAL] gradient partials (training)
-    long long count;             // rows of cons
-    long long first;             // first sample of this launch
-    long long nsamp;             // samples in this launch (batch)
-    float inv_batch;             // 1 / batch
-    float gamma;
-    float sc[6];
-};
-
-__device__ __forceinline__ float silu(float z) { return z * __fdividef(1.0f, 1.0f + __expf(-z)); }
-
-__device__ __forceinline__ float dsilu(float z)
-{
-    const float s = __fdividef(1.0f, 1.0f + __expf(-z));
-    return s * (1.0f + z * (1.0f - s));
-}
-
-__device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], const uint32_t b[2])
-{
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-// A fragment (16 x 16) of a row-major BF16 matrix M (leading dimension ld) at (r0, c0).
-__device__ __forceinline__ void load_a(uint32_t a[4], const __nv_bfloat16 *M, int ld, int r0, int c0, int lane)
-{
-    const int g = lane >> 2, tq = lane & 3;
-    a[0] = *reinterpret_cast<const uint32_t *>(M + (r0 + g) * ld + c0 + 2 * tq);
-    a[1] = *reinterpret_cast<const uint32_t *>(M + (r0 + g + 8) * ld + c0 + 2 * tq);
-    a[2] = *reinterpret_cast<const uint32_t *>(M + (r0 + g) * ld + c0 + 2 * tq + 8);
-    a[3] = *reinterpret_cast<const uint32_t *>(M + (r0 + g + 8) * ld + c0 + 2 * tq + 8);
-}
-
-// B fragment (16 x 8, k x n) from the row-major transpose Bt[n][k] at (k0, n0).
-__device__ __forceinline__ void load_b(uint32_t b[2], const __nv_bfloat16 *Bt, int ld, int k0, int n0, int lane)
-{
-    const int g = lane >> 2, tq = lane & 3;
-    b[0] = *reinterpret_cast<const uint32_t *>(Bt + (n0 + g) * ld + k0 + 2 * tq);
-    b[1] = *reinterpret_cast<const uint32_t *>(Bt + (n0 + g) * ld + k0 + 2 * tq + 8);
-}
 
 // Shared memory of one tile.  Inference needs only the first block of members.
 struct NetSmemFwd {
     float x[NET_TILE][3];
     float t[NET_TILE];
+    int ok[NET_TILE];                   // finite features (and target): takes part in the loss
     __nv_bfloat16 h1[NET_TILE][64];     // A of layer 2
     __nv_bfloat16 W2[64][64];           // B^T of layer 2
     float W1[64][3], b1[64], b2[64], W3[64];
@@ -132,10 +78,15 @@ __global__ void __launch_bounds__(NET_TILE) k_net_tile(const NetTileArgs a)
             x2 = 2.0f * (log10f(D) - a.sc[2]) / (a.sc[3] - a.sc[2]) - 1.0f;
             if (TRAIN) t = (log10f(f64_to_f32(a.p[gs]) / E32) - a.sc[4]) / a.sc[5];
         }
+        // states whose features or target are not finite (D or tau not positive,
+        // a pressure below the FP32 range) enter neither the loss nor the gradient
+        const bool fin = valid && isfinite(x0) && isfinite(x1) && isfinite(x2) && isfinite(t);
+        if (!fin) x0 = x1 = x2 = t = 0.0f;
         S.x[tid][0] = x0;
         S.x[tid][1] = x1;
         S.x[tid][2] = x2;
         S.t[tid] = t;
+        S.ok[tid] = fin ? 1 : 0;
     }
     __syncthreads();
 
@@ -213,7 +164,7 @@ __global__ void __launch_bounds__(NET_TILE) k_net_tile(const NetTileArgs a)
                         const float E = tau + D;
                         float pg = E * exp10f(ypart[mt][h] * a.sc[5] + a.sc[4]);
                         pg = fminf(fmaxf(pg, fmaxf(sqrtf(Sx * Sx + Sy * Sy + Sz * Sz) - E, 0.0f)), (a.gamma - 1.0f) * tau);
-                        a.guess[gi] = f32_to_f64(pg);
+                        a.guess[gi] = (S.ok[row] && isfinite(pg)) ? f32_to_f64(pg) : -1.0;
                     }
                 }
         }
@@ -228,7 +179,7 @@ __global__ void __launch_bounds__(NET_TILE) k_net_tile(const NetTileArgs a)
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int row = r0 + mt * 16 + g + 8 * h;
-            const bool ok = (long long)blockIdx.x * NET_TILE + row < a.nsamp;
+            const bool ok = (long long)blockIdx.x * NET_TILE + row < a.nsamp && S.ok[row];
             const float r = ok ? ypart[mt][h] - S.t[row] : 0.0f;
             dy[mt][h] = 2.0f * r * a.inv_batch;
             if (tq == 0) {
@@ -486,6 +437,17 @@ cudaError_t net_launch_tile(dg_c2p_net *n, bool train, const double *cons, const
     if (train) k_net_tile<true><<<grid, NET_TILE, smem, s>>>(a);
     else k_net_tile<false><<<grid, NET_TILE, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+}  // namespace dg
+
+namespace dg {
+
+void net_device_view(const dg_c2p_net *n, const float **P, const void **W2b, float sc[6])
+{
+    *P = n->P;
+    *W2b = n->W2b;
+    for (int i = 0; i < 6; ++i) sc[i] = n->sc[i];
 }
 
 }  // namespace dg

@@ -94,6 +94,7 @@ struct dg_mesh {
     float *pbuf[2];          // SR pressures of the last two passes (con2prim warm starts)
     int pi, p_valid;         // index of the latest pressure buffer, and whether it holds one
     float kappa_sw;          // conditioning above which FP32 con2prim is polished in FP64
+    const dg_c2p_net *net;   // attached learned-guess network (mixed SR path), or nullptr
     // optional per-kernel timing (dg_profile_enable)
     int prof_on;
     void *prof;              // host-side event log, owned by dg_api.cu
@@ -121,6 +122,9 @@ cudaError_t launch_stage_mixed(int n, int system, int flux, const MixedArgs &a, 
 cudaError_t launch_limit_mixed(int n, int system, const LimitMixedArgs &a, cudaStream_t s);
 cudaError_t launch_cfl_mixed(const dg_mesh *m, const double *Un, const float *pin, float *pout, float kappa_sw,
                              cudaStream_t s);
+
+// Device view of a learned-guess network: FP32 parameters, BF16 W2 [j][i], scales.
+void net_device_view(const dg_c2p_net *n, const float **P, const void **W2b, float sc[6]);
 
 // Host LGL tables (long double Newton; closed-form LGL differentiation matrix).
 void lgl_tables(int n, Tables &T);

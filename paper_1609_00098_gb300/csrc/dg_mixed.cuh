@@ -12,6 +12,7 @@
 // operations because the conversion instructions issue at the FP64 rate.
 #pragma once
 
+#include "dg_c2p_net.cuh"
 #include "dg_internal.h"
 #include "dg_physics.cuh"
 
@@ -167,6 +168,7 @@ __device__ __forceinline__ int sr_con2prim32(float g, const float u[5], float gu
     float p = (guess >= 0.0f) ? fminf(fmaxf(guess, plo), phi) : phi;
     float rhoeps = tau;
     int status = 2;
+    bool lo_moved = false, hi_moved = false;
     for (int it = 0; it < 60; ++it) {
         const float Ep = E + p;
         const float v2 = s2 / (Ep * Ep);
@@ -177,9 +179,10 @@ __device__ __forceinline__ int sr_con2prim32(float g, const float u[5], float gu
         const float df = 1.0f - (g - 1.0f) * v2 * (1.0f - DW / Ep);
         const float noise = 6.0e-7f * (p + (g - 1.0f) * (tau + v2 * Ep));
         if (fabsf(f) <= noise) { status = 0; break; }
-        if (f > 0.0f) phi = p; else plo = p;
+        if (f > 0.0f) { phi = p; hi_moved = true; } else { plo = p; lo_moved = true; }
         float pn = p - f / df;
-        if (!(pn > plo && pn < phi)) pn = 0.5f * (plo + phi);
+        if (!((pn > plo && pn < phi) || (pn == phi && !hi_moved) || (pn == plo && !lo_moved)))
+            pn = 0.5f * (plo + phi);
         const float dp = fabsf(pn - p);
         p = pn;
         if (dp <= 4.8e-7f * p || !(phi > plo)) { status = 0; break; }
@@ -213,6 +216,7 @@ __device__ __forceinline__ int sr_polish64(double g, const double u[5], double p
     double plo = fmax(sqrt(s2) - E, 0.0), phi = (g - 1.0) * tau;
     double p = (p0 >= 0.0) ? fmin(fmax(p0, plo), phi) : phi;
     int status = 2;
+    bool lo_moved = false, hi_moved = false;
     for (int it = 0; it < 60; ++it) {
         const double Ep = E + p;
         const double v2 = s2 / (Ep * Ep);
@@ -222,9 +226,10 @@ __device__ __forceinline__ int sr_polish64(double g, const double u[5], double p
         const double f = p - (g - 1.0) * rhoeps;
         const double df = 1.0 - (g - 1.0) * v2 * (1.0 - DW / Ep);
         if (fabs(f) <= 0x1p-50 * (p + (g - 1.0) * (tau + v2 * Ep))) { status = 0; break; }
-        if (f > 0.0) phi = p; else plo = p;
+        if (f > 0.0) { phi = p; hi_moved = true; } else { plo = p; lo_moved = true; }
         double pn = p - f / df;
-        if (!(pn > plo && pn < phi)) pn = 0.5 * (plo + phi);
+        if (!((pn > plo && pn < phi) || (pn == phi && !hi_moved) || (pn == plo && !lo_moved)))
+            pn = 0.5 * (plo + phi);
         const double dp = fabs(pn - p);
         p = pn;
         if (dp <= 0x1p-40 * p || !(phi > plo)) { status = 0; break; }
@@ -259,6 +264,9 @@ struct MixedArgs {
     float g[3], lift0[3], liftN[3];
     float kappa_sw;
     double d_atm, tau_atm;
+    const float *netP;               // learned-guess network (FP32 parameters), or nullptr
+    const __nv_bfloat16 *netW2;      // its W2 in BF16 [j][i]
+    float net_sc[6];                 // its feature scales
     float D32[MAXN * MAXN];
     double w64[MAXN], row1_64[MAXN];
 };
@@ -311,19 +319,33 @@ __device__ __forceinline__ unsigned sr_prims_mixed(float g, double gd, float kap
     return st64 ? ERRBIT_C2P : 0u;
 }
 
-// Primitives of one node of the stage input (element e, node q).
+// Primitives of one node of the stage input (element e, node q), con2prim
+// starting from `guess` (< 0: the standard guess).
 template <int NP, int SYS>
 __device__ __forceinline__ void node_prims_mixed(const MixedArgs &a, long long e, int q, const float u[5],
-                                                 float P[NPRIM], unsigned &errs)
+                                                 float guess, float P[NPRIM], unsigned &errs)
 {
     constexpr int NN = NP * NP * NP;
     if (SYS == 0) {
         ne_primitives32(a.gamma, u, P);
         return;
     }
-    errs |= sr_prims_mixed(a.gamma, a.gamma_d, a.kappa_sw, a.d_atm, a.tau_atm, u, a.Us + e * 5 * NN + q, NN,
-                           a.pin ? a.pin[e * NN + q] : -1.0f, P);
+    errs |= sr_prims_mixed(a.gamma, a.gamma_d, a.kappa_sw, a.d_atm, a.tau_atm, u, a.Us + e * 5 * NN + q, NN, guess,
+                           P);
 }
+
+// Shared memory of k_stage_mixed: the main arrays, then (learned guess only) the
+// network's weights, the features of the element's nodes and their guesses.
+template <int NP>
+struct MixedSmem {
+    static constexpr int NN = NP * NP * NP;
+    static constexpr int ROWS = NN;
+    static constexpr size_t MAIN = sizeof(float) * (25 + NPRIM) * NN;
+    static constexpr size_t NET = (MAIN + 15) / 16 * 16;        // NetWeightsSmem offset
+    static constexpr size_t FEAT = NET + (sizeof(NetWeightsSmem) + 15) / 16 * 16;
+    static constexpr size_t GUESS = FEAT + sizeof(float) * 6 * ROWS;
+    static constexpr size_t TOTAL_LEARNED = GUESS + sizeof(float) * ROWS;
+};
 
 // FP32 screen of the bounds of the conserved fix (Sec. 2.1.4) and of physicality;
 // nodes that fail it are decided in FP64.
@@ -334,11 +356,11 @@ __device__ __forceinline__ bool sr_screen32(const float u[5], float d_atm, float
            !(s2 < 0.999f * u[4] * (u[4] + 2.0f * u[0]));
 }
 
-template <int NP, int SYS, int FLX>
+template <int NP, int SYS, int FLX, int GUESS>
 __global__ void __launch_bounds__(round_up32(NP *NP *NP)) k_stage_mixed(const MixedArgs a)
 {
     constexpr int NN = NP * NP * NP;
-    extern __shared__ float smem_mixed[];
+    extern __shared__ __align__(16) float smem_mixed[];
     float *sF = smem_mixed;     // [3][5][NN] fluxes, later FP32 deviations of the output [5][NN]
     float *sR = sF + 15 * NN;   // [5][NN] right-hand side
     float *sU = sR + 5 * NN;    // [5][NN] stage input state (FP32)
@@ -357,6 +379,29 @@ __global__ void __launch_bounds__(round_up32(NP *NP *NP)) k_stage_mixed(const Mi
     if (t < 6) sNb[t] = elem_neighbour(e, a.K, t >> 1, (t & 1) ? 1 : -1);
     unsigned errs = 0;
 
+    // Learned con2prim guesses for the element's nodes (the network runs on the
+    // tensor cores over the CTA's 16-node tiles).  The neighbours' face nodes in
+    // the face loop start from the pressure of this element's node at the same
+    // point (the other side of the trace), which is already solved by then.
+    using SM = MixedSmem<NP>;
+    float *sGuess = nullptr;
+    if (GUESS) {
+        unsigned char *raw = reinterpret_cast<unsigned char *>(smem_mixed);
+        NetWeightsSmem &W = *reinterpret_cast<NetWeightsSmem *>(raw + SM::NET);
+        float(*sFeat)[6] = reinterpret_cast<float(*)[6]>(raw + SM::FEAT);
+        sGuess = reinterpret_cast<float *>(raw + SM::GUESS);
+        net_stage_weights(W, a.netP, a.netW2);
+        if (t < NN) {
+            float u[5];
+#pragma unroll
+            for (int v = 0; v < 5; ++v) u[v] = f64_to_f32(a.Us[(e * 5 + v) * NN + t]);
+            net_features(u, a.net_sc, sFeat[t]);
+        }
+        __syncthreads();
+        net_guess_rows(W, sFeat, sGuess, NN, a.gamma, a.net_sc);
+        __syncthreads();
+    }
+
     if (t < NN) {
         float u[5];
 #pragma unroll
@@ -365,7 +410,8 @@ __global__ void __launch_bounds__(round_up32(NP *NP *NP)) k_stage_mixed(const Mi
             sU[v * NN + t] = u[v];
         }
         float P[NPRIM];
-        node_prims_mixed<NP, SYS>(a, e, t, u, P, errs);
+        const float guess = GUESS ? sGuess[t] : (a.pin ? a.pin[e * NN + t] : -1.0f);
+        node_prims_mixed<NP, SYS>(a, e, t, u, guess, P, errs);
         if (SYS == 1 && a.pout) a.pout[e * NN + t] = P[3];
 #pragma unroll
         for (int c = 0; c < NPRIM; ++c) sP[c * NN + t] = P[c];
@@ -433,7 +479,8 @@ __global__ void __launch_bounds__(round_up32(NP *NP *NP)) k_stage_mixed(const Mi
             }
 #pragma unroll
             for (int c = 0; c < NPRIM; ++c) Po[c] = sP[c * NN + q];
-            node_prims_mixed<NP, SYS>(a, en, qn, un, Pn, errs);
+            const float gn = GUESS ? Po[3] : (a.pin ? a.pin[en * NN + qn] : -1.0f);
+            node_prims_mixed<NP, SYS>(a, en, qn, un, gn, Pn, errs);
             float dL[5], dR[5];
             if (side) {
                 num_flux_jump32<SYS, FLX>(a.gamma, ax, uo, Po, un, Pn, dL, dR);
@@ -653,12 +700,13 @@ template <int NP>
 cudaError_t launch_stage_mixed_np(int system, int flux, const MixedArgs &a, long long E, cudaStream_t s)
 {
     const dim3 grid((unsigned)E), block(round_up32(NP * NP * NP));
-    const size_t smem = sizeof(float) * (25 + NPRIM) * NP * NP * NP;
+    const bool learned = system == 1 && a.netP != nullptr;
+    const size_t smem = learned ? MixedSmem<NP>::TOTAL_LEARNED : MixedSmem<NP>::MAIN;
     void (*kern)(const MixedArgs);
-    if (system == 0 && flux == 0) kern = k_stage_mixed<NP, 0, 0>;
-    else if (system == 0) kern = k_stage_mixed<NP, 0, 1>;
-    else if (flux == 0) kern = k_stage_mixed<NP, 1, 0>;
-    else kern = k_stage_mixed<NP, 1, 1>;
+    if (system == 0 && flux == 0) kern = k_stage_mixed<NP, 0, 0, 0>;
+    else if (system == 0) kern = k_stage_mixed<NP, 0, 1, 0>;
+    else if (flux == 0) kern = learned ? k_stage_mixed<NP, 1, 0, 1> : k_stage_mixed<NP, 1, 0, 0>;
+    else kern = learned ? k_stage_mixed<NP, 1, 1, 1> : k_stage_mixed<NP, 1, 1, 0>;
     if (smem > 48 * 1024) {
         cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err != cudaSuccess) return err;

@@ -28,7 +28,9 @@ __device__ __forceinline__ void ne_primitives(double g, const double u[5], doubl
 //   rho eps = tau - v^2 [(E+p) - D W/(W+1)]   (from the definitions of D, S, tau),
 //   f'(p) = 1 - (g-1) v^2 (1 - D W/(E+p)),
 // bracketed by [max(0, s-E), (g-1) tau]; Newton steps that leave the bracket
-// become bisections, the bracket follows the sign of f; stop once
+// become bisections, except a step landing exactly on an end that is still its
+// a-priori bound (at v = 0 the root is (g-1) tau itself); the bracket follows
+// the sign of f; stop once
 // |dp| <= 2^-48 p and take one more Newton step.
 struct C2PEval {
     double f, df;
@@ -72,13 +74,15 @@ __device__ __forceinline__ int sr_con2prim(double g, const double u[5], double g
     if (p < plo) p = plo;
     if (p > phi) p = phi;
     int status = 2;
+    bool lo_moved = false, hi_moved = false;  // an end still at its a-priori bound may be landed on
     int it = 0;
     for (; it < 200; ++it) {
         const C2PEval r = sr_c2p_eval(g, D, s2, tau, p);
         if (r.f == 0.0) { status = 0; break; }
-        if (r.f > 0.0) phi = p; else plo = p;
+        if (r.f > 0.0) { phi = p; hi_moved = true; } else { plo = p; lo_moved = true; }
         double pn = p - r.f / r.df;
-        if (!(pn > plo && pn < phi)) pn = 0.5 * (plo + phi);
+        if (!((pn > plo && pn < phi) || (pn == phi && !hi_moved) || (pn == plo && !lo_moved)))
+            pn = 0.5 * (plo + phi);
         const double dp = fabs(pn - p);
         p = pn;
         if (dp <= 0x1p-48 * p) {
