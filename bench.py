@@ -356,6 +356,7 @@ def run_ours(args):
         "dtype": "f32 arithmetic, f64 state and RK accumulation",
         "data": "synthetic (seeded blast initial data)",
         "config": _config({"precision": "mixed", "c2p_guess": "learned (in-kernel MLP)",
+                           "volume_contraction": "tensor cores, split-BF16x3 mma.sync m16n8k8, FP32 accumulate",
                            "parallelism": "replicas" if ws > 1 else "single GPU",
                            "step_launch": "CUDA graph replay"}),
         "variant": "mixed+learned (FP32 con2prim from the in-kernel MLP guess, FP32 fluxes/contraction/face "

@@ -184,6 +184,19 @@ dg_status dg_c2p_net_train(dg_c2p_net *net, long long count, const double *cons,
 #define DG_RHS_STATIC_MAX_NODES 131072
 dg_status dg_rhs_static(const dg_mesh_desc *desc, const double *U, double *dUdt, void *stream);
 
+/* Per-mesh options of the mixed-precision path (no effect on the FP64 path,
+ * which always follows the oracle's arithmetic).
+ *   DG_OPT_TENSOR_CORE_CONTRACTION (default 1): 1 evaluates the volume
+ *     contraction sum_l D_il F_l (Sec. 3.1, eq:405) on the tensor cores as
+ *     split-BF16x3 products accumulated in FP32; 0 uses FP32 FMA on the CUDA
+ *     cores.  Both are FP32-accurate.
+ *   DG_OPT_C2P_KAPPA_SWITCH (default 10): the conditioning estimate tau/(rho eps)
+ *     above which the FP32 con2prim result is finished by FP64 Newton on the FP64
+ *     state (it also bounds W^2 for the FP32 wave speeds); in [1, 1e30].
+ * Errors: DG_ERR_ARG for an unknown option or a value out of range. */
+enum { DG_OPT_TENSOR_CORE_CONTRACTION = 1, DG_OPT_C2P_KAPPA_SWITCH = 2 };
+dg_status dg_mesh_set_option(dg_mesh *mesh, int option, double value);
+
 /* Attach a learned-guess network to a mixed-precision SR mesh (net == NULL
  * detaches it).  With a network attached, every con2prim inside dg_rhs and
  * dg_rk3_step's stages starts its FP32 Newton from the network's guess, computed

@@ -94,6 +94,10 @@ class Mesh:
     def sync_status(self) -> int:
         return abi.dg_sync_status(self.h)
 
+    def set_option(self, option, value):
+        """Mixed-path option: abi.OPT_TENSOR_CORE_CONTRACTION or abi.OPT_C2P_KAPPA_SWITCH."""
+        abi.dg_mesh_set_option(self.h, option, value)
+
     def set_c2p_net(self, net):
         """Attach (or with None detach) a learned con2prim guess network."""
         abi.dg_mesh_set_c2p_net(self.h, net)

@@ -67,6 +67,7 @@ SIGNATURES = {
     "dg_con2prim": (_i, [_ll, _d, _vp, _vp, _vp, _vp, _vp, _vp]),
     "dg_sync_status": (_i, [_vp, _vp]),
     "dg_mesh_set_c2p_net": (_i, [_vp, _vp]),
+    "dg_mesh_set_option": (_i, [_vp, _i, _d]),
     "dg_c2p_net_create": (_i, [_vp, _vp, ctypes.POINTER(_vp)]),
     "dg_c2p_net_destroy": (None, [_vp]),
     "dg_c2p_net_get_params": (_i, [_vp, _vp]),
@@ -252,6 +253,15 @@ def dg_con2prim(count, gamma, cons, prim, p_guess=None, iters=None, status=None,
 def dg_sync_status(mesh, stream=None) -> int:
     """Returns the status code (does not raise for kernel-side failures)."""
     return load().dg_sync_status(mesh, _stream(stream))
+
+
+OPT_TENSOR_CORE_CONTRACTION = 1
+OPT_C2P_KAPPA_SWITCH = 2
+
+
+def dg_mesh_set_option(mesh, option, value):
+    """Set a mixed-path option (OPT_TENSOR_CORE_CONTRACTION, OPT_C2P_KAPPA_SWITCH)."""
+    _check(load().dg_mesh_set_option(mesh, int(option), float(value)))
 
 
 def dg_mesh_set_c2p_net(mesh, net):

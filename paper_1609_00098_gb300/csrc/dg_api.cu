@@ -343,6 +343,7 @@ MixedArgs mixed_args(const dg_mesh *m)
     a.gamma = (float)m->d.gamma;
     a.gamma_d = m->d.gamma;
     a.kappa_sw = m->kappa_sw;
+    a.tc = m->tc_contract;
     a.d_atm = m->d.d_atm;
     a.tau_atm = m->d.tau_atm;
     a.err = m->err;
@@ -455,6 +456,7 @@ dg_status dg_mesh_create(const dg_mesh_desc *d, dg_mesh **out)
     const size_t state = sizeof(double) * (size_t)E * 5 * m->nn;
     const bool mixed = d->precision == DG_PRECISION_MIXED;
     m->kappa_sw = 10.0f;
+    m->tc_contract = 1;
     cudaError_t st = cudaSuccess;
     st = st ? st : cudaMalloc(&m->W1, state);
     st = st ? st : cudaMalloc(&m->W2, state);
@@ -725,6 +727,23 @@ dg_status dg_con2prim(long long count, double gamma, const double *cons, double 
     if (!(gamma > 1.0)) return fail(DG_ERR_ARG, "gamma must be > 1");
     DG_CUDA(launch_con2prim(count, gamma, cons, prim, p_guess, iters, status, (cudaStream_t)stream));
     return DG_OK;
+}
+
+dg_status dg_mesh_set_option(dg_mesh *m, int option, double value)
+{
+    if (dg_status s = check_mesh(m)) return s;
+    switch (option) {
+    case DG_OPT_TENSOR_CORE_CONTRACTION:
+        if (value != 0.0 && value != 1.0) return fail(DG_ERR_ARG, "tensor-core contraction option takes 0 or 1");
+        m->tc_contract = (int)value;
+        return DG_OK;
+    case DG_OPT_C2P_KAPPA_SWITCH:
+        if (!(value >= 1.0 && value <= 1e30)) return fail(DG_ERR_ARG, "kappa switch must be in [1, 1e30]");
+        m->kappa_sw = (float)value;
+        return DG_OK;
+    default:
+        return fail(DG_ERR_ARG, "unknown option %d", option);
+    }
 }
 
 dg_status dg_mesh_set_c2p_net(dg_mesh *m, const dg_c2p_net *net)

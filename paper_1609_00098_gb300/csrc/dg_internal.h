@@ -95,6 +95,7 @@ struct dg_mesh {
     int pi, p_valid;         // index of the latest pressure buffer, and whether it holds one
     float kappa_sw;          // conditioning above which FP32 con2prim is polished in FP64
     const dg_c2p_net *net;   // attached learned-guess network (mixed SR path), or nullptr
+    int tc_contract;         // mixed volume contraction on the tensor cores (split-BF16x3)
     // optional per-kernel timing (dg_profile_enable)
     int prof_on;
     void *prof;              // host-side event log, owned by dg_api.cu

@@ -45,6 +45,37 @@ __device__ __forceinline__ double f32_to_f64(float f)
 }
 
 // ---------------------------------------------------------------------------
+// Split-BF16x3 products on the tensor cores: x = x_hi + x_mid + x_lo with each
+// part the BF16 rounding of what the previous parts leave (24 significant bits in
+// all), and a product kept as the six partial products of order >= 2^-16
+// (lo.hi, hi.lo, mid.mid, mid.hi, hi.mid, hi.hi, smallest first) accumulated in
+// FP32 by mma.sync m16n8k8.
+
+__device__ __forceinline__ void split_bf16x3(float x, float part[3])
+{
+    const float h = __bfloat162float(__float2bfloat16_rn(x));
+    const float r = x - h;
+    const float m = __bfloat162float(__float2bfloat16_rn(r));
+    part[0] = h;
+    part[1] = m;
+    part[2] = r - m;  // rounded to BF16 when packed
+}
+
+__device__ __forceinline__ uint32_t pack2_bf16(float lo, float hi)
+{
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&v);
+}
+
+__device__ __forceinline__ void mma_bf16_k8(float c[4], uint32_t a0, uint32_t a1, uint32_t b)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, {%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a0), "r"(a1), "r"(b));
+}
+
+// ---------------------------------------------------------------------------
 // FP32 physics.  Node primitives are held as P = (vx, vy, vz, p, 1 - v^2); the
 // last entry is 1 for the Newtonian system.  1 - v^2 comes from FP64 wherever the
 // Lorentz factor is large enough for FP32 to lose it (see sr_prims_mixed).
@@ -264,6 +295,7 @@ struct MixedArgs {
     float g[3], lift0[3], liftN[3];
     float kappa_sw;
     double d_atm, tau_atm;
+    int tc;                          // volume contraction: 1 split-BF16x3 tensor cores, 0 FP32 FMA
     const float *netP;               // learned-guess network (FP32 parameters), or nullptr
     const __nv_bfloat16 *netW2;      // its W2 in BF16 [j][i]
     float net_sc[6];                 // its feature scales
@@ -438,25 +470,87 @@ __global__ void __launch_bounds__(round_up32(NP *NP *NP)) k_stage_mixed(const Mi
     }
     __syncthreads();
 
-    // volume term in FP32
-    if (t < NN) {
-        const int i = t % NP, j = (t / NP) % NP, k = t / (NP * NP);
+    // Volume term (eq:405), per axis a and variable v the contraction
+    // sum_l D_il (F_v^a - F_ref)_l along axis a, scaled by -2/dx_a.
+    if (a.tc) {
+        // Tensor cores: for axis a the products R^T = F^T D^T, with rows (v, line)
+        // -- the 5 NP^2 lines of nodes along a -- K = l and N = i padded to 8.
+        const int lane = t & 31, warp = t >> 5, nwarps = blockDim.x >> 5;
+        const int g = lane >> 2, tq = lane & 3;
+        uint32_t bfr[3];  // B = D^T: this lane holds B[2tq][g], B[2tq+1][g] = D[g][2tq], D[g][2tq+1]
+        {
+            float d0[3], d1[3];
+            split_bf16x3((g < NP && 2 * tq < NP) ? sD[g * NP + 2 * tq] : 0.0f, d0);
+            split_bf16x3((g < NP && 2 * tq + 1 < NP) ? sD[g * NP + 2 * tq + 1] : 0.0f, d1);
 #pragma unroll
-        for (int v = 0; v < 5; ++v) {
-            const float *Fx = sF + (0 * 5 + v) * NN;
-            const float *Fy = sF + (1 * 5 + v) * NN;
-            const float *Fz = sF + (2 * 5 + v) * NN;
-            float sx = 0.0f, sy = 0.0f, sz = 0.0f;
-#pragma unroll
-            for (int l = 0; l < NP; ++l) {
-                sx = fmaf(sD[i * NP + l], Fx[l + NP * (j + NP * k)], sx);
-                sy = fmaf(sD[j * NP + l], Fy[i + NP * (l + NP * k)], sy);
-                sz = fmaf(sD[k * NP + l], Fz[i + NP * (j + NP * l)], sz);
-            }
-            sR[v * NN + t] = -(a.g[0] * sx + a.g[1] * sy + a.g[2] * sz);
+            for (int p = 0; p < 3; ++p) bfr[p] = pack2_bf16(d0[p], d1[p]);
         }
+        constexpr int ROWS = 5 * NP * NP, TILES = (ROWS + 15) / 16;
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+            // node of line c at position l along axis ax
+            auto node_of = [=](int c, int l) {
+                return ax == 0 ? l + NP * c : (ax == 1 ? (c % NP) + NP * (l + NP * (c / NP)) : c + NP * NP * l);
+            };
+            const float gax = a.g[ax];
+            for (int tile = warp; tile < TILES; tile += nwarps) {
+                const int ra = tile * 16 + g, rb = ra + 8;
+                float va[2], vb[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int l = 2 * tq + h;
+                    va[h] = (ra < ROWS && l < NP) ? sF[(ax * 5 + ra / (NP * NP)) * NN + node_of(ra % (NP * NP), l)] : 0.0f;
+                    vb[h] = (rb < ROWS && l < NP) ? sF[(ax * 5 + rb / (NP * NP)) * NN + node_of(rb % (NP * NP), l)] : 0.0f;
+                }
+                float pa0[3], pa1[3], pb0[3], pb1[3];
+                split_bf16x3(va[0], pa0);
+                split_bf16x3(va[1], pa1);
+                split_bf16x3(vb[0], pb0);
+                split_bf16x3(vb[1], pb1);
+                uint32_t a0[3], a1[3];
+#pragma unroll
+                for (int p = 0; p < 3; ++p) {
+                    a0[p] = pack2_bf16(pa0[p], pa1[p]);
+                    a1[p] = pack2_bf16(pb0[p], pb1[p]);
+                }
+                float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+                mma_bf16_k8(acc, a0[2], a1[2], bfr[0]);
+                mma_bf16_k8(acc, a0[0], a1[0], bfr[2]);
+                mma_bf16_k8(acc, a0[1], a1[1], bfr[1]);
+                mma_bf16_k8(acc, a0[1], a1[1], bfr[0]);
+                mma_bf16_k8(acc, a0[0], a1[0], bfr[1]);
+                mma_bf16_k8(acc, a0[0], a1[0], bfr[0]);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int r = (c < 2) ? ra : rb, i = 2 * tq + (c & 1);
+                    if (r < ROWS && i < NP) {
+                        float *dst = sR + (r / (NP * NP)) * NN + node_of(r % (NP * NP), i);
+                        *dst = (ax == 0) ? -gax * acc[c] : *dst - gax * acc[c];
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    } else {
+        if (t < NN) {
+            const int i = t % NP, j = (t / NP) % NP, k = t / (NP * NP);
+#pragma unroll
+            for (int v = 0; v < 5; ++v) {
+                const float *Fx = sF + (0 * 5 + v) * NN;
+                const float *Fy = sF + (1 * 5 + v) * NN;
+                const float *Fz = sF + (2 * 5 + v) * NN;
+                float sx = 0.0f, sy = 0.0f, sz = 0.0f;
+#pragma unroll
+                for (int l = 0; l < NP; ++l) {
+                    sx = fmaf(sD[i * NP + l], Fx[l + NP * (j + NP * k)], sx);
+                    sy = fmaf(sD[j * NP + l], Fy[i + NP * (l + NP * k)], sy);
+                    sz = fmaf(sD[k * NP + l], Fz[i + NP * (j + NP * l)], sz);
+                }
+                sR[v * NN + t] = -(a.g[0] * sx + a.g[1] * sy + a.g[2] * sz);
+            }
+        }
+        __syncthreads();
     }
-    __syncthreads();
 
     // surface terms; the neighbour's face node is recovered here from its FP64 state
     for (int ax = 0; ax < 3; ++ax) {

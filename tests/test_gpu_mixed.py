@@ -158,3 +158,33 @@ def test_mixed_ill_conditioned_nodes(pkg):
     assert gm.sync_status() == 0
     err = np.abs(Rg - Ro).max(axis=(0, 2)) / _scale(Ro)
     assert err.max() < 1e-3, err
+
+
+@pytest.mark.parametrize("n", [2, 3, 5, 8])
+def test_tensor_core_and_fma_contractions(pkg, n):
+    """The volume contraction on the tensor cores (split-BF16x3, FP32 accumulate)
+    and on the CUDA cores (FP32 FMA) both give the oracle's RHS to FP32 rounding,
+    and agree with each other to the same level."""
+    om, gm = _pair(pkg, 1, (3, 2, 2), n, 1, 1)
+    U = om.from_prim(di.blast_sr(om.coords(), seed=4))
+    Ro = om.rhs(U)
+    out = {}
+    for tc in (1, 0):
+        gm.set_option(pkg.abi.OPT_TENSOR_CORE_CONTRACTION, tc)
+        out[tc] = gm.rhs(_gpu(U)).cpu().numpy()
+    assert gm.sync_status() == 0
+    sc = _scale(Ro)
+    for tc in (1, 0):
+        err = np.abs(out[tc] - Ro).max(axis=(0, 2)) / sc
+        assert err.max() < 1e-4, (tc, err)
+    diff = np.abs(out[1] - out[0]).max(axis=(0, 2)) / sc
+    assert diff.max() < 1e-4, diff
+
+
+def test_mesh_options_validate(pkg):
+    gm = pkg.Mesh(system=1, K=(2, 2, 2), n=3, flux=1, limiter=0, precision=1, gamma=4.0 / 3.0)
+    for opt, bad in ((pkg.abi.OPT_TENSOR_CORE_CONTRACTION, 2), (pkg.abi.OPT_C2P_KAPPA_SWITCH, 0.5), (99, 1)):
+        with pytest.raises(pkg.abi.DGError):
+            gm.set_option(opt, bad)
+    gm.set_option(pkg.abi.OPT_C2P_KAPPA_SWITCH, 1e3)
+    gm.set_option(pkg.abi.OPT_TENSOR_CORE_CONTRACTION, 0)
