@@ -210,6 +210,41 @@ dg_status dg_mesh_set_option(dg_mesh *mesh, int option, double value);
  * addition to Sec. 2.1.2). */
 dg_status dg_mesh_set_c2p_net(dg_mesh *mesh, const dg_c2p_net *net);
 
+/* ---- Ragged ensemble (batching many independent meshes; the paper has no
+ * counterpart on one device -- its task runtime spreads many small elements over
+ * cores) ----
+ * An ensemble advances `count` mixed-precision meshes together, each with its own
+ * state U[i] (device, dg_state_size(meshes[i]) doubles) and its own CFL step.  The
+ * ensemble keeps the mesh and state pointers: the caller keeps both alive and
+ * must not destroy a mesh before the ensemble.  Meshes sharing n, system, flux,
+ * limiter, gamma, fix bounds, options and learned-guess network form a group; a
+ * step launches one CFL, one stage and one limiter kernel per group (per stage)
+ * over the group's concatenated elements.  Per mesh the arithmetic is that of
+ * dg_rk3_step(mesh, U, 0, cfl, ...), so results are bitwise those of stepping the
+ * meshes one by one with the same per-group options.  Device-side failures set
+ * each mesh's status word (dg_sync_status per mesh).
+ * Errors: DG_ERR_ARG for NULL or repeated meshes/states, FP64 meshes, or meshes on
+ * another device; DG_ERR_CUDA for allocation failures. */
+typedef struct dg_ensemble dg_ensemble;
+dg_status dg_ensemble_create(dg_mesh *const *meshes, double *const *U, int count, dg_ensemble **out);
+void dg_ensemble_destroy(dg_ensemble *ens);
+/* Autotune: per group, time the stage kernel (right-hand side only, written to
+ * library scratch; the states are not changed) for every elements-per-CTA choice
+ * and both volume contractions, and keep the fastest.  Synchronises `stream`. */
+dg_status dg_ensemble_tune(dg_ensemble *ens, void *stream);
+/* One SSP-RK3 step of every mesh (Sec. 3.4) with dt = cfl dx_min / lambda_max of
+ * that mesh.  use_graph != 0: from the second step on, the step's launches are
+ * captured once into a CUDA graph (again when cfl changes) and replayed. */
+dg_status dg_ensemble_step(dg_ensemble *ens, double cfl, int use_graph, void *stream);
+/* Groups and, for group g, info = (n, system, flux, limiter, meshes, elements,
+ * elements per CTA, tensor-core contraction 0/1). */
+int dg_ensemble_num_groups(const dg_ensemble *ens);
+dg_status dg_ensemble_group_info(const dg_ensemble *ens, int g, long long info[8]);
+/* Group of mesh i (-1 for a bad index or ensemble). */
+int dg_ensemble_mesh_group(const dg_ensemble *ens, int i);
+/* The last step's dt of every mesh into dt (device, count doubles). */
+dg_status dg_ensemble_dt(const dg_ensemble *ens, double *dt, void *stream);
+
 /* Synchronise `stream`, then read and clear the mesh's device status word.
  * Returns DG_OK, DG_ERR_C2P or DG_ERR_UNPHYSICAL (first set), or DG_ERR_CUDA. */
 dg_status dg_sync_status(dg_mesh *mesh, void *stream);

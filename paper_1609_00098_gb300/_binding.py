@@ -68,6 +68,14 @@ SIGNATURES = {
     "dg_sync_status": (_i, [_vp, _vp]),
     "dg_mesh_set_c2p_net": (_i, [_vp, _vp]),
     "dg_mesh_set_option": (_i, [_vp, _i, _d]),
+    "dg_ensemble_create": (_i, [_vp, _vp, _i, ctypes.POINTER(_vp)]),
+    "dg_ensemble_destroy": (None, [_vp]),
+    "dg_ensemble_tune": (_i, [_vp, _vp]),
+    "dg_ensemble_step": (_i, [_vp, _d, _i, _vp]),
+    "dg_ensemble_num_groups": (_i, [_vp]),
+    "dg_ensemble_group_info": (_i, [_vp, _i, _vp]),
+    "dg_ensemble_mesh_group": (_i, [_vp, _i]),
+    "dg_ensemble_dt": (_i, [_vp, _vp, _vp]),
     "dg_c2p_net_create": (_i, [_vp, _vp, ctypes.POINTER(_vp)]),
     "dg_c2p_net_destroy": (None, [_vp]),
     "dg_c2p_net_get_params": (_i, [_vp, _vp]),
@@ -253,6 +261,63 @@ def dg_con2prim(count, gamma, cons, prim, p_guess=None, iters=None, status=None,
 def dg_sync_status(mesh, stream=None) -> int:
     """Returns the status code (does not raise for kernel-side failures)."""
     return load().dg_sync_status(mesh, _stream(stream))
+
+
+def dg_ensemble_create(meshes, states):
+    """meshes: Mesh handles (c_void_p); states: matching device float64 tensors."""
+    import torch
+    n = len(meshes)
+    if n != len(states) or n < 1:
+        raise ValueError("need as many states as meshes, at least one")
+    mh = (ctypes.c_void_p * n)(*[m.value if isinstance(m, ctypes.c_void_p) else m for m in meshes])
+    sp = (ctypes.c_void_p * n)(*[_ptr(U, U.numel(), torch.float64, "U") for U in states])
+    h = ctypes.c_void_p()
+    _check(load().dg_ensemble_create(ctypes.addressof(mh), ctypes.addressof(sp), n, ctypes.byref(h)))
+    return h
+
+
+def dg_ensemble_destroy(ens):
+    load().dg_ensemble_destroy(ens)
+
+
+def dg_ensemble_tune(ens, stream=None):
+    _check(load().dg_ensemble_tune(ens, _stream(stream)))
+
+
+def dg_ensemble_step(ens, cfl, use_graph=True, stream=None):
+    _check(load().dg_ensemble_step(ens, float(cfl), 1 if use_graph else 0, _stream(stream)))
+
+
+def dg_ensemble_num_groups(ens) -> int:
+    return int(load().dg_ensemble_num_groups(ens))
+
+
+def dg_ensemble_group_info(ens, g):
+    """(n, system, flux, limiter, meshes, elements, elements per CTA, tensor-core contraction)."""
+    info = (ctypes.c_longlong * 8)()
+    _check(load().dg_ensemble_group_info(ens, int(g), ctypes.addressof(info)))
+    return tuple(info)
+
+
+def dg_ensemble_mesh_group(ens, i) -> int:
+    return int(load().dg_ensemble_mesh_group(ens, int(i)))
+
+
+def dg_ensemble_groups(ens):
+    """List of dicts (n, system, flux, limiter, meshes, elements, epb, tc) per group."""
+    keys = ("n", "system", "flux", "limiter", "meshes", "elements", "epb", "tc")
+    groups = [dict(zip(keys, dg_ensemble_group_info(ens, g))) for g in range(dg_ensemble_num_groups(ens))]
+    count = sum(g["meshes"] for g in groups)
+    for g in groups:
+        g["members"] = []
+    for i in range(count):
+        groups[dg_ensemble_mesh_group(ens, i)]["members"].append(i)
+    return groups
+
+
+def dg_ensemble_dt(ens, dt, stream=None):
+    import torch
+    _check(load().dg_ensemble_dt(ens, _ptr(dt, dt.numel(), torch.float64, "dt"), _stream(stream)))
 
 
 OPT_TENSOR_CORE_CONTRACTION = 1

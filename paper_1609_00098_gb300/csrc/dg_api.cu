@@ -250,7 +250,7 @@ cudaError_t launch_limit(int n, const LimitArgs &a, cudaStream_t s)
 cudaError_t launch_set(double *p, double v, cudaStream_t s);
 
 #define DG_DECL_MIXED(NP)                                                                               \
-    cudaError_t launch_stage_mixed_n##NP(int, int, const MixedArgs &, long long, cudaStream_t);         \
+    cudaError_t launch_stage_mixed_n##NP(int, int, const MixedArgs &, cudaStream_t);                    \
     cudaError_t launch_limit_mixed_n##NP(int, const LimitMixedArgs &, cudaStream_t);
 DG_DECL_MIXED(2)
 DG_DECL_MIXED(3)
@@ -260,18 +260,18 @@ DG_DECL_MIXED(6)
 DG_DECL_MIXED(7)
 DG_DECL_MIXED(8)
 
-cudaError_t launch_stage_mixed(int n, int system, int flux, const MixedArgs &a, long long E, cudaStream_t s)
+cudaError_t launch_stage_mixed(int n, int system, int flux, const MixedArgs &a, cudaStream_t s)
 {
     switch (n) {
-    case 2: return launch_stage_mixed_n2(system, flux, a, E, s);
-    case 3: return launch_stage_mixed_n3(system, flux, a, E, s);
-    case 4: return launch_stage_mixed_n4(system, flux, a, E, s);
-    case 5: return launch_stage_mixed_n5(system, flux, a, E, s);
-    case 6: return launch_stage_mixed_n6(system, flux, a, E, s);
-    case 7: return launch_stage_mixed_n7(system, flux, a, E, s);
-    case 8: return launch_stage_mixed_n8(system, flux, a, E, s);
+    case 2: return launch_stage_mixed_n2(system, flux, a, s);
+    case 3: return launch_stage_mixed_n3(system, flux, a, s);
+    case 4: return launch_stage_mixed_n4(system, flux, a, s);
+    case 5: return launch_stage_mixed_n5(system, flux, a, s);
+    case 6: return launch_stage_mixed_n6(system, flux, a, s);
+    case 7: return launch_stage_mixed_n7(system, flux, a, s);
+    case 8: return launch_stage_mixed_n8(system, flux, a, s);
+    default: return cudaErrorInvalidValue;
     }
-    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_limit_mixed(int n, int system, const LimitMixedArgs &a, cudaStream_t s)
@@ -286,6 +286,84 @@ cudaError_t launch_limit_mixed(int n, int system, const LimitMixedArgs &a, cudaS
     case 8: return launch_limit_mixed_n8(system, a, s);
     }
     return cudaErrorInvalidValue;
+}
+
+// Per-mesh slot of a mixed stage launch (pointers filled in by the caller).
+MeshSlot mixed_slot(const dg_mesh *m)
+{
+    MeshSlot sl;
+    std::memset(&sl, 0, sizeof(sl));
+    for (int ax = 0; ax < 3; ++ax) {
+        sl.K[ax] = m->d.K[ax];
+        const double g = 2.0 / m->dx[ax];
+        sl.g[ax] = (float)g;
+        sl.lift0[ax] = (float)(g / m->T.w[0]);
+        sl.liftN[ax] = (float)(g / m->T.w[m->d.n - 1]);
+    }
+    sl.err = m->err;
+    return sl;
+}
+
+// Group-level arguments of a mixed stage launch for meshes like m (n, system,
+// gamma, fix bounds, options, network); one element per CTA, no slot table.
+MixedArgs mixed_args(const dg_mesh *m)
+{
+    MixedArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.one = mixed_slot(m);
+    a.nslots = 1;
+    a.nelem = m->E;
+    a.epb = 1;
+    a.lim = m->d.limiter != 0;
+    a.gamma = (float)m->d.gamma;
+    a.gamma_d = m->d.gamma;
+    a.kappa_sw = m->kappa_sw;
+    a.tc = m->tc_contract;
+    a.d_atm = m->d.d_atm;
+    a.tau_atm = m->d.tau_atm;
+    if (m->net && m->d.system == 1) {
+        const void *w2 = nullptr;
+        net_device_view(m->net, &a.netP, &w2, a.net_sc);
+        a.netW2 = static_cast<const __nv_bfloat16 *>(w2);
+    }
+    for (int i = 0; i < MAXN * MAXN; ++i) a.D32[i] = (float)m->T.D[i];
+    for (int i = 0; i < MAXN; ++i) {
+        a.w64[i] = m->T.w[i];
+        a.row1_64[i] = m->T.row1[i];
+    }
+    return a;
+}
+
+LimitSlot limit_slot(const dg_mesh *m, double *U, unsigned char *troubled)
+{
+    LimitSlot l;
+    std::memset(&l, 0, sizeof(l));
+    l.U = U;
+    l.S = m->S;
+    l.flags = (m->d.system == 1) ? m->unphys : nullptr;
+    l.troubled = troubled;
+    for (int ax = 0; ax < 3; ++ax) {
+        l.K[ax] = m->d.K[ax];
+        l.tvb[ax] = m->d.tvb_M * m->dx[ax] * m->dx[ax];
+        l.inv_dx[ax] = 1.0 / m->dx[ax];
+        l.beta_dx[ax] = m->d.beta / m->dx[ax];
+        l.hdx[ax] = 0.5 * m->dx[ax];
+    }
+    return l;
+}
+
+LimitMixedArgs limit_mixed_args(const dg_mesh *m, double *U, unsigned char *troubled)
+{
+    LimitMixedArgs l;
+    std::memset(&l, 0, sizeof(l));
+    l.one = limit_slot(m, U, troubled);
+    l.nslots = 1;
+    l.E = m->E;
+    l.limiter = m->d.limiter;
+    l.d_atm = m->d.d_atm;
+    l.tau_atm = m->d.tau_atm;
+    for (int i = 0; i < MAXN; ++i) l.x[i] = m->T.x[i];
+    return l;
 }
 
 }  // namespace dg
@@ -326,59 +404,6 @@ LimitArgs limit_args(const dg_mesh *m, double *U, unsigned char *troubled)
     l.tvb_M = m->d.tvb_M;
     l.beta = m->d.beta;
     l.T = m->T;
-    return l;
-}
-
-MixedArgs mixed_args(const dg_mesh *m)
-{
-    MixedArgs a;
-    std::memset(&a, 0, sizeof(a));
-    for (int ax = 0; ax < 3; ++ax) {
-        a.K[ax] = m->d.K[ax];
-        const double g = 2.0 / m->dx[ax];
-        a.g[ax] = (float)g;
-        a.lift0[ax] = (float)(g / m->T.w[0]);
-        a.liftN[ax] = (float)(g / m->T.w[m->d.n - 1]);
-    }
-    a.gamma = (float)m->d.gamma;
-    a.gamma_d = m->d.gamma;
-    a.kappa_sw = m->kappa_sw;
-    a.tc = m->tc_contract;
-    a.d_atm = m->d.d_atm;
-    a.tau_atm = m->d.tau_atm;
-    a.err = m->err;
-    if (m->net && m->d.system == 1) {
-        const void *w2 = nullptr;
-        net_device_view(m->net, &a.netP, &w2, a.net_sc);
-        a.netW2 = static_cast<const __nv_bfloat16 *>(w2);
-    }
-    for (int i = 0; i < MAXN * MAXN; ++i) a.D32[i] = (float)m->T.D[i];
-    for (int i = 0; i < MAXN; ++i) {
-        a.w64[i] = m->T.w[i];
-        a.row1_64[i] = m->T.row1[i];
-    }
-    return a;
-}
-
-LimitMixedArgs limit_mixed_args(const dg_mesh *m, double *U, unsigned char *troubled)
-{
-    LimitMixedArgs l;
-    std::memset(&l, 0, sizeof(l));
-    l.U = U;
-    l.S = m->S;
-    l.flags = (m->d.system == 1) ? m->unphys : nullptr;
-    l.troubled = troubled;
-    l.E = m->E;
-    for (int ax = 0; ax < 3; ++ax) {
-        l.K[ax] = m->d.K[ax];
-        l.tvb[ax] = m->d.tvb_M * m->dx[ax] * m->dx[ax];
-        l.inv_dx[ax] = 1.0 / m->dx[ax];
-        l.beta_dx[ax] = m->d.beta / m->dx[ax];
-        for (int i = 0; i < MAXN; ++i) l.hx[ax][i] = 0.5 * m->dx[ax] * m->T.x[i];
-    }
-    l.limiter = m->d.limiter;
-    l.d_atm = m->d.d_atm;
-    l.tau_atm = m->d.tau_atm;
     return l;
 }
 
@@ -457,6 +482,7 @@ dg_status dg_mesh_create(const dg_mesh_desc *d, dg_mesh **out)
     const bool mixed = d->precision == DG_PRECISION_MIXED;
     m->kappa_sw = 10.0f;
     m->tc_contract = 1;
+    m->epb = 1;
     cudaError_t st = cudaSuccess;
     st = st ? st : cudaMalloc(&m->W1, state);
     st = st ? st : cudaMalloc(&m->W2, state);
@@ -540,11 +566,12 @@ dg_status dg_rhs(dg_mesh *m, const double *U, double *dUdt, void *stream)
     cudaStream_t s = (cudaStream_t)stream;
     if (m->d.precision == DG_PRECISION_MIXED) {
         MixedArgs a = mixed_args(m);
-        a.Us = U;
-        a.Un = U;
-        a.out = dUdt;
+        a.one.Us = U;
+        a.one.Un = U;
+        a.one.out = dUdt;
         a.mode = 0;
-        DG_LAUNCH(m, s, PROF_STAGE, launch_stage_mixed(m->d.n, m->d.system, m->d.flux, a, m->E, s));
+        a.lim = 0;
+        DG_LAUNCH(m, s, PROF_STAGE, launch_stage_mixed(m->d.n, m->d.system, m->d.flux, a, s));
         return DG_OK;
     }
     DG_LAUNCH(m, s, PROF_PRIM, launch_primitives(m, U, m->P, 0, nullptr, nullptr, s));
@@ -582,11 +609,11 @@ static dg_status rk3_step_mixed(dg_mesh *m, double *U, double dt, double cfl, do
     // with a learned guess attached, no pressures are carried between passes
     const bool carry = sr && m->net == nullptr;
     MixedArgs a = mixed_args(m);
-    a.Un = U;
-    a.dt = dt;
-    a.dt_ptr = cflmode ? m->dt : nullptr;
-    a.S = lim ? m->S : nullptr;
-    a.flags = (lim && sr) ? m->unphys : nullptr;
+    a.one.Un = U;
+    a.one.dt = dt;
+    a.one.dt_ptr = cflmode ? m->dt : nullptr;
+    a.one.S = lim ? m->S : nullptr;
+    a.one.flags = (lim && sr) ? m->unphys : nullptr;
     a.mode = 1;
     float *latest = (carry && m->p_valid) ? m->pbuf[m->pi] : nullptr;
     if (cflmode) {
@@ -603,14 +630,15 @@ static dg_status rk3_step_mixed(dg_mesh *m, double *U, double dt, double cfl, do
     const float ca[3] = {0.0f, 0.75f, (float)(1.0 / 3.0)};
     const float cb[3] = {1.0f, 0.25f, (float)(2.0 / 3.0)};
     for (int st = 0; st < 3; ++st) {
-        a.Us = ins[st];
-        a.out = outs[st];
+        a.one.Us = ins[st];
+        a.one.out = outs[st];
         a.first = st == 0;
         a.ca = ca[st];
         a.cb = cb[st];
-        a.pin = latest;
-        a.pout = carry ? m->pbuf[1 - m->pi] : nullptr;
-        DG_LAUNCH(m, s, PROF_STAGE, launch_stage_mixed(m->d.n, m->d.system, m->d.flux, a, m->E, s));
+        a.one.pin = latest;
+        a.one.pout = carry ? m->pbuf[1 - m->pi] : nullptr;
+        a.epb = m->epb > 0 ? m->epb : 1;
+        DG_LAUNCH(m, s, PROF_STAGE, launch_stage_mixed(m->d.n, m->d.system, m->d.flux, a, s));
         if (carry) {
             m->pi = 1 - m->pi;
             latest = m->pbuf[m->pi];

@@ -96,6 +96,7 @@ struct dg_mesh {
     float kappa_sw;          // conditioning above which FP32 con2prim is polished in FP64
     const dg_c2p_net *net;   // attached learned-guess network (mixed SR path), or nullptr
     int tc_contract;         // mixed volume contraction on the tensor cores (split-BF16x3)
+    int epb;                 // mixed stage kernel: elements per CTA
     // optional per-kernel timing (dg_profile_enable)
     int prof_on;
     void *prof;              // host-side event log, owned by dg_api.cu
@@ -119,10 +120,19 @@ cudaError_t launch_con2prim(long long count, double gamma, const double *cons, d
 
 struct MixedArgs;
 struct LimitMixedArgs;
-cudaError_t launch_stage_mixed(int n, int system, int flux, const MixedArgs &a, long long E, cudaStream_t s);
+cudaError_t launch_stage_mixed(int n, int system, int flux, const MixedArgs &a, cudaStream_t s);
 cudaError_t launch_limit_mixed(int n, int system, const LimitMixedArgs &a, cudaStream_t s);
 cudaError_t launch_cfl_mixed(const dg_mesh *m, const double *Un, const float *pin, float *pout, float kappa_sw,
                              cudaStream_t s);
+struct CflArgs;
+struct MeshSlot;
+struct LimitSlot;
+CflArgs cfl_args(const dg_mesh *m, float kappa_sw);
+cudaError_t launch_cfl_batch(int system, const CflArgs &a, long long nchunks, cudaStream_t s);
+MixedArgs mixed_args(const dg_mesh *m);
+MeshSlot mixed_slot(const dg_mesh *m);
+LimitMixedArgs limit_mixed_args(const dg_mesh *m, double *U, unsigned char *troubled);
+LimitSlot limit_slot(const dg_mesh *m, double *U, unsigned char *troubled);
 
 // Device view of a learned-guess network: FP32 parameters, BF16 W2 [j][i], scales.
 void net_device_view(const dg_c2p_net *n, const float **P, const void **W2b, float sc[6]);

@@ -274,8 +274,11 @@ __device__ __forceinline__ int sr_polish64(double g, const double u[5], double p
 }
 
 // ---------------------------------------------------------------------------
-
-struct MixedArgs {
+// Per-mesh part of a stage launch.  A launch advances one mesh (its slot passed
+// inline) or a ragged batch of meshes that share n, the system, the flux, the
+// limiter setting and the guess mode (slot table and element offsets in device
+// memory; each CTA finds its mesh by binary search over the offsets).
+struct MeshSlot {
     const double *Us;       // stage input (state layout, FP64)
     const double *Un;       // U^n (stages 2, 3)
     double *out;            // stage output U_{s+1} (mode 1) or dU/dt (mode 0)
@@ -286,13 +289,23 @@ struct MixedArgs {
     unsigned int *err;
     const double *dt_ptr;
     double dt;
+    int K[3];
+    float g[3], lift0[3], liftN[3];
+};
+
+struct MixedArgs {
+    MeshSlot one;                    // the mesh of a single-mesh launch
+    const MeshSlot *slots;           // batch: per-mesh slots, or nullptr
+    const long long *elem0;          // batch: first element of each mesh in the launch (nslots entries)
+    int nslots;
+    long long nelem;                 // elements in the launch
+    int epb;                         // elements per CTA
+    int lim;                         // limiter on: write summaries and flags, leave the SR fix to it
     float ca, cb;           // U_{s+1} = ca U^n + cb (U_s + dt R) = U_s + ca (U^n - U_s) + cb dt R
     int first;              // first stage: U_{s+1} = U_s + dt R
     int mode;               // 0: dU/dt, 1: stage update
-    int K[3];
     float gamma;
     double gamma_d;
-    float g[3], lift0[3], liftN[3];
     float kappa_sw;
     double d_atm, tau_atm;
     int tc;                          // volume contraction: 1 split-BF16x3 tensor cores, 0 FP32 FMA
@@ -302,6 +315,46 @@ struct MixedArgs {
     float D32[MAXN * MAXN];
     double w64[MAXN], row1_64[MAXN];
 };
+
+constexpr int CFL_CHUNK = 256;  // nodes per CTA of the CFL pass
+
+// Per-mesh part of a CFL launch; a launch covers one mesh or a ragged batch of
+// meshes with the same n and system, in chunks of CFL_CHUNK nodes (a chunk never
+// spans two meshes, so the block maximum goes to one mesh's slot).
+struct CflSlot {
+    const double *Un;
+    const float *pin;              // previous pass's pressures (guesses), or nullptr
+    float *pout;                   // this pass's pressures, or nullptr
+    unsigned long long *lam;
+    unsigned int *err;
+    long long nodes;
+};
+
+struct CflArgs {
+    CflSlot one;
+    const CflSlot *slots;          // batch: per-mesh slots, or nullptr
+    const long long *chunk0;       // batch: first chunk of each mesh
+    int nslots;
+    int nn;
+    float gamma;
+    double gamma_d;
+    float kappa_sw;
+    double d_atm, tau_atm;
+    const float *netP;             // learned-guess network, or nullptr
+    const __nv_bfloat16 *netW2;
+    float net_sc[6];
+};
+
+__device__ __forceinline__ int find_slot(const long long *elem0, int nslots, long long ge)
+{
+    int lo = 0, hi = nslots - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (elem0[mid] <= ge) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
 
 // SR primitives of one node, u the FP32 copy of the FP64 state Ub[v * stride]:
 // FP32 con2prim from `guess`; where the conditioning estimate tau/(rho eps)
@@ -350,33 +403,32 @@ __device__ __forceinline__ unsigned sr_prims_mixed(float g, double gd, float kap
     P[4] = f64_to_f32(1.0 - (Pd[0] * Pd[0] + Pd[1] * Pd[1] + Pd[2] * Pd[2]));
     return st64 ? ERRBIT_C2P : 0u;
 }
+// Threads per element and the largest CTA of k_stage_mixed<NP>.
+template <int NP>
+struct StageShape {
+    static constexpr int NN = NP * NP * NP;
+    static constexpr int TPE = round_up32(NN);
+    static constexpr int MAXT = TPE > 256 ? TPE : 256;
+    static constexpr int MAX_EPB = MAXT / TPE;
+};
 
-// Primitives of one node of the stage input (element e, node q), con2prim
-// starting from `guess` (< 0: the standard guess).
-template <int NP, int SYS>
-__device__ __forceinline__ void node_prims_mixed(const MixedArgs &a, long long e, int q, const float u[5],
-                                                 float guess, float P[NPRIM], unsigned &errs)
-{
-    constexpr int NN = NP * NP * NP;
-    if (SYS == 0) {
-        ne_primitives32(a.gamma, u, P);
-        return;
-    }
-    errs |= sr_prims_mixed(a.gamma, a.gamma_d, a.kappa_sw, a.d_atm, a.tau_atm, u, a.Us + e * 5 * NN + q, NN, guess,
-                           P);
-}
-
-// Shared memory of k_stage_mixed: the main arrays, then (learned guess only) the
-// network's weights, the features of the element's nodes and their guesses.
+// Shared memory of k_stage_mixed: per element (stride ELEM) the main arrays,
+// the plane sums, the neighbour indices, two flags, the element index and the
+// mesh slot; then (learned guess only) the network's weights, and the features
+// and guesses of all the CTA's nodes.
 template <int NP>
 struct MixedSmem {
     static constexpr int NN = NP * NP * NP;
-    static constexpr int ROWS = NN;
     static constexpr size_t MAIN = sizeof(float) * (25 + NPRIM) * NN;
-    static constexpr size_t NET = (MAIN + 15) / 16 * 16;        // NetWeightsSmem offset
-    static constexpr size_t FEAT = NET + (sizeof(NetWeightsSmem) + 15) / 16 * 16;
-    static constexpr size_t GUESS = FEAT + sizeof(float) * 6 * ROWS;
-    static constexpr size_t TOTAL_LEARNED = GUESS + sizeof(float) * ROWS;
+    static constexpr size_t Q = (MAIN + 15) / 16 * 16;
+    static constexpr size_t NB = Q + sizeof(double) * 3 * NP * 5;
+    static constexpr size_t FLAG = NB + sizeof(long long) * 7;      // 6 neighbours + element index
+    static constexpr size_t SLOT = (FLAG + 2 * sizeof(int) + 15) / 16 * 16;
+    static constexpr size_t ELEM = (SLOT + sizeof(MeshSlot) + 15) / 16 * 16;
+    __host__ __device__ static size_t net(int epb) { return ELEM * epb; }
+    __host__ __device__ static size_t feat(int epb) { return net(epb) + (sizeof(NetWeightsSmem) + 15) / 16 * 16; }
+    __host__ __device__ static size_t guess(int epb) { return feat(epb) + sizeof(float) * 6 * NN * epb; }
+    __host__ __device__ static size_t total(int epb, bool learned) { return learned ? guess(epb) + sizeof(float) * NN * epb : ELEM * epb; }
 };
 
 // FP32 screen of the bounds of the conserved fix (Sec. 2.1.4) and of physicality;
@@ -387,64 +439,83 @@ __device__ __forceinline__ bool sr_screen32(const float u[5], float d_atm, float
     return !(u[0] > 2.0f * d_atm) || !(u[4] > 2.0f * tau_atm * u[0]) ||
            !(s2 < 0.999f * u[4] * (u[4] + 2.0f * u[0]));
 }
-
 template <int NP, int SYS, int FLX, int GUESS>
-__global__ void __launch_bounds__(round_up32(NP *NP *NP)) k_stage_mixed(const MixedArgs a)
+__global__ void __launch_bounds__(StageShape<NP>::MAXT) k_stage_mixed(const MixedArgs a)
 {
     constexpr int NN = NP * NP * NP;
-    extern __shared__ __align__(16) float smem_mixed[];
-    float *sF = smem_mixed;     // [3][5][NN] fluxes, later FP32 deviations of the output [5][NN]
-    float *sR = sF + 15 * NN;   // [5][NN] right-hand side
-    float *sU = sR + 5 * NN;    // [5][NN] stage input state (FP32)
-    float *sP = sU + 5 * NN;    // [NPRIM][NN] primitives of the input
+    constexpr int TPE = StageShape<NP>::TPE;
+    using SM = MixedSmem<NP>;
+    extern __shared__ __align__(16) unsigned char smem_mixed[];
+    const int sub = threadIdx.x / TPE, t = threadIdx.x % TPE;
+    unsigned char *base = smem_mixed + SM::ELEM * sub;
+    float *sF = reinterpret_cast<float *>(base);  // [3][5][NN] fluxes (later the FP64 output)
+    float *sR = sF + 15 * NN;                      // [5][NN] right-hand side
+    float *sU = sR + 5 * NN;                       // [5][NN] stage input state (FP32)
+    float *sP = sU + 5 * NN;                       // [NPRIM][NN] primitives of the input
+    double *sQ = reinterpret_cast<double *>(base + SM::Q);
+    long long *sNb = reinterpret_cast<long long *>(base + SM::NB);
+    int *sFlag = reinterpret_cast<int *>(base + SM::FLAG);
+    MeshSlot &sl = *reinterpret_cast<MeshSlot *>(base + SM::SLOT);
     __shared__ float sD[NP * NP];
-    __shared__ double sW64[NP], sRow164[NP], sQ[3 * NP * 5];
-    __shared__ long long sNb[6];
+    __shared__ double sW64[NP], sRow164[NP];
 
-    const int t = threadIdx.x;
-    const long long e = blockIdx.x;
-    for (int i = t; i < NP * NP; i += blockDim.x) sD[i] = a.D32[i];
-    if (t < NP) {
-        sW64[t] = a.w64[t];
-        sRow164[t] = a.row1_64[t];
+    const long long ge = (long long)blockIdx.x * a.epb + sub;
+    const bool live = sub < a.epb && ge < a.nelem;  // uniform within the element's warps
+    if (t == 0) {
+        sFlag[0] = sFlag[1] = 0;
+        if (live) {
+            const int m = a.slots ? find_slot(a.elem0, a.nslots, ge) : 0;
+            sl = a.slots ? a.slots[m] : a.one;
+            sNb[6] = a.slots ? ge - a.elem0[m] : ge;
+        }
     }
-    if (t < 6) sNb[t] = elem_neighbour(e, a.K, t >> 1, (t & 1) ? 1 : -1);
+    for (int i = threadIdx.x; i < NP * NP; i += blockDim.x) sD[i] = a.D32[i];
+    if (threadIdx.x < NP) {
+        sW64[threadIdx.x] = a.w64[threadIdx.x];
+        sRow164[threadIdx.x] = a.row1_64[threadIdx.x];
+    }
+    __syncthreads();
+    const long long e = live ? sNb[6] : 0;
+    if (live && t < 6) sNb[t] = elem_neighbour(e, sl.K, t >> 1, (t & 1) ? 1 : -1);
+    const bool own = live && t < NN;  // this thread holds node t of a live element
     unsigned errs = 0;
 
-    // Learned con2prim guesses for the element's nodes (the network runs on the
-    // tensor cores over the CTA's 16-node tiles).  The neighbours' face nodes in
-    // the face loop start from the pressure of this element's node at the same
-    // point (the other side of the trace), which is already solved by then.
-    using SM = MixedSmem<NP>;
+    // Learned con2prim guesses for the CTA's nodes (rows sub * NN + t; the
+    // network runs on the tensor cores over 16-row tiles).  The neighbours' face
+    // nodes in the face loop start from the pressure of this element's node at
+    // the same point (the other side of the trace), solved by then.
     float *sGuess = nullptr;
     if (GUESS) {
-        unsigned char *raw = reinterpret_cast<unsigned char *>(smem_mixed);
-        NetWeightsSmem &W = *reinterpret_cast<NetWeightsSmem *>(raw + SM::NET);
-        float(*sFeat)[6] = reinterpret_cast<float(*)[6]>(raw + SM::FEAT);
-        sGuess = reinterpret_cast<float *>(raw + SM::GUESS);
+        NetWeightsSmem &W = *reinterpret_cast<NetWeightsSmem *>(smem_mixed + SM::net(a.epb));
+        float(*sFeat)[6] = reinterpret_cast<float(*)[6]>(smem_mixed + SM::feat(a.epb));
+        sGuess = reinterpret_cast<float *>(smem_mixed + SM::guess(a.epb));
         net_stage_weights(W, a.netP, a.netW2);
         if (t < NN) {
-            float u[5];
+            float u[5] = {1.0f, 0.0f, 0.0f, 0.0f, 1.0f};
+            if (own)
 #pragma unroll
-            for (int v = 0; v < 5; ++v) u[v] = f64_to_f32(a.Us[(e * 5 + v) * NN + t]);
-            net_features(u, a.net_sc, sFeat[t]);
+                for (int v = 0; v < 5; ++v) u[v] = f64_to_f32(sl.Us[(e * 5 + v) * NN + t]);
+            net_features(u, a.net_sc, sFeat[sub * NN + t]);
         }
         __syncthreads();
-        net_guess_rows(W, sFeat, sGuess, NN, a.gamma, a.net_sc);
+        net_guess_rows(W, sFeat, sGuess, NN * a.epb, a.gamma, a.net_sc);
         __syncthreads();
+        sGuess += sub * NN;
     }
 
-    if (t < NN) {
+    if (own) {
         float u[5];
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
-            u[v] = f64_to_f32(a.Us[(e * 5 + v) * NN + t]);
+            u[v] = f64_to_f32(sl.Us[(e * 5 + v) * NN + t]);
             sU[v * NN + t] = u[v];
         }
         float P[NPRIM];
-        const float guess = GUESS ? sGuess[t] : (a.pin ? a.pin[e * NN + t] : -1.0f);
-        node_prims_mixed<NP, SYS>(a, e, t, u, guess, P, errs);
-        if (SYS == 1 && a.pout) a.pout[e * NN + t] = P[3];
+        const float guess = GUESS ? sGuess[t] : (sl.pin ? sl.pin[e * NN + t] : -1.0f);
+        if (SYS == 0) ne_primitives32(a.gamma, u, P);
+        else errs |= sr_prims_mixed(a.gamma, a.gamma_d, a.kappa_sw, a.d_atm, a.tau_atm, u,
+                                    sl.Us + e * 5 * NN + t, NN, guess, P);
+        if (SYS == 1 && sl.pout) sl.pout[e * NN + t] = P[3];
 #pragma unroll
         for (int c = 0; c < NPRIM; ++c) sP[c * NN + t] = P[c];
 #pragma unroll
@@ -464,7 +535,7 @@ __global__ void __launch_bounds__(round_up32(NP *NP *NP)) k_stage_mixed(const Mi
 #pragma unroll
         for (int c = 0; c < 15; ++c) ref[c] = sF[c * NN];
         __syncthreads();
-        if (t < NN)
+        if (own)
 #pragma unroll
             for (int c = 0; c < 15; ++c) sF[c * NN + t] -= ref[c];
     }
@@ -475,7 +546,7 @@ __global__ void __launch_bounds__(round_up32(NP *NP *NP)) k_stage_mixed(const Mi
     if (a.tc) {
         // Tensor cores: for axis a the products R^T = F^T D^T, with rows (v, line)
         // -- the 5 NP^2 lines of nodes along a -- K = l and N = i padded to 8.
-        const int lane = t & 31, warp = t >> 5, nwarps = blockDim.x >> 5;
+        const int lane = t & 31, warp = t >> 5, nwarps = TPE >> 5;
         const int g = lane >> 2, tq = lane & 3;
         uint32_t bfr[3];  // B = D^T: this lane holds B[2tq][g], B[2tq+1][g] = D[g][2tq], D[g][2tq+1]
         {
@@ -492,8 +563,8 @@ __global__ void __launch_bounds__(round_up32(NP *NP *NP)) k_stage_mixed(const Mi
             auto node_of = [=](int c, int l) {
                 return ax == 0 ? l + NP * c : (ax == 1 ? (c % NP) + NP * (l + NP * (c / NP)) : c + NP * NP * l);
             };
-            const float gax = a.g[ax];
-            for (int tile = warp; tile < TILES; tile += nwarps) {
+            const float gax = live ? sl.g[ax] : 0.0f;
+            for (int tile = warp; live && tile < TILES; tile += nwarps) {
                 const int ra = tile * 16 + g, rb = ra + 8;
                 float va[2], vb[2];
 #pragma unroll
@@ -532,7 +603,7 @@ __global__ void __launch_bounds__(round_up32(NP *NP *NP)) k_stage_mixed(const Mi
             __syncthreads();
         }
     } else {
-        if (t < NN) {
+        if (own) {
             const int i = t % NP, j = (t / NP) % NP, k = t / (NP * NP);
 #pragma unroll
             for (int v = 0; v < 5; ++v) {
@@ -546,7 +617,7 @@ __global__ void __launch_bounds__(round_up32(NP *NP *NP)) k_stage_mixed(const Mi
                     sy = fmaf(sD[j * NP + l], Fy[i + NP * (l + NP * k)], sy);
                     sz = fmaf(sD[k * NP + l], Fz[i + NP * (j + NP * l)], sz);
                 }
-                sR[v * NN + t] = -(a.g[0] * sx + a.g[1] * sy + a.g[2] * sz);
+                sR[v * NN + t] = -(sl.g[0] * sx + sl.g[1] * sy + sl.g[2] * sz);
             }
         }
         __syncthreads();
@@ -554,7 +625,7 @@ __global__ void __launch_bounds__(round_up32(NP *NP *NP)) k_stage_mixed(const Mi
 
     // surface terms; the neighbour's face node is recovered here from its FP64 state
     for (int ax = 0; ax < 3; ++ax) {
-        for (int fp = t; fp < 2 * NP * NP; fp += blockDim.x) {
+        for (int fp = t; live && fp < 2 * NP * NP; fp += TPE) {
             const int side = fp / (NP * NP);
             const int rem = fp % (NP * NP);
             int id[3];
@@ -569,26 +640,28 @@ __global__ void __launch_bounds__(round_up32(NP *NP *NP)) k_stage_mixed(const Mi
 #pragma unroll
             for (int v = 0; v < 5; ++v) {
                 uo[v] = sU[v * NN + q];
-                un[v] = f64_to_f32(a.Us[(en * 5 + v) * NN + qn]);
+                un[v] = f64_to_f32(sl.Us[(en * 5 + v) * NN + qn]);
             }
 #pragma unroll
             for (int c = 0; c < NPRIM; ++c) Po[c] = sP[c * NN + q];
-            const float gn = GUESS ? Po[3] : (a.pin ? a.pin[en * NN + qn] : -1.0f);
-            node_prims_mixed<NP, SYS>(a, en, qn, un, gn, Pn, errs);
+            const float gn = GUESS ? Po[3] : (sl.pin ? sl.pin[en * NN + qn] : -1.0f);
+            if (SYS == 0) ne_primitives32(a.gamma, un, Pn);
+            else errs |= sr_prims_mixed(a.gamma, a.gamma_d, a.kappa_sw, a.d_atm, a.tau_atm, un,
+                                        sl.Us + en * 5 * NN + qn, NN, gn, Pn);
             float dL[5], dR[5];
             if (side) {
                 num_flux_jump32<SYS, FLX>(a.gamma, ax, uo, Po, un, Pn, dL, dR);
 #pragma unroll
-                for (int v = 0; v < 5; ++v) sR[v * NN + q] -= a.liftN[ax] * dL[v];
+                for (int v = 0; v < 5; ++v) sR[v * NN + q] -= sl.liftN[ax] * dL[v];
             } else {
                 num_flux_jump32<SYS, FLX>(a.gamma, ax, un, Pn, uo, Po, dL, dR);
 #pragma unroll
-                for (int v = 0; v < 5; ++v) sR[v * NN + q] += a.lift0[ax] * dR[v];
+                for (int v = 0; v < 5; ++v) sR[v * NN + q] += sl.lift0[ax] * dR[v];
             }
         }
         __syncthreads();
     }
-    if (errs) atomicOr(a.err, errs);
+    if (errs) atomicOr(sl.err, errs);
 
     // Stage update in FP64: U_{s+1} = U_s + [ca (U^n - U_s) + cb dt R], the bracket
     // in FP32 (it carries the FP32 RHS), the accumulation in FP64.  The limiter
@@ -597,29 +670,29 @@ __global__ void __launch_bounds__(round_up32(NP *NP *NP)) k_stage_mixed(const Mi
     // which visits the flagged elements.
     double val[5];
     bool bad = false, needfix = false;
-    if (t < NN) {
-        const float dt = (float)(a.dt_ptr ? *a.dt_ptr : a.dt);
+    if (own) {
+        const float dt = (float)(sl.dt_ptr ? *sl.dt_ptr : sl.dt);
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
             const long long ix = (e * 5 + v) * NN + t;
             const float R = sR[v * NN + t];
             if (a.mode == 0) {
-                a.out[ix] = f32_to_f64(R);
+                sl.out[ix] = f32_to_f64(R);
                 continue;
             }
-            const double us = a.Us[ix];
+            const double us = sl.Us[ix];
             float inc;
             if (a.first) {
                 inc = dt * R;
             } else {
-                const float dn = f64_to_f32(a.Un[ix] - us);
+                const float dn = f64_to_f32(sl.Un[ix] - us);
                 inc = a.ca * dn + a.cb * (dt * R);
             }
             val[v] = us + f32_to_f64(inc);
         }
     }
     if (a.mode == 0) return;
-    if (t < NN && SYS == 1) {
+    if (own && SYS == 1) {
         float u32[5];
 #pragma unroll
         for (int v = 0; v < 5; ++v) u32[v] = f64_to_f32(val[v]);
@@ -628,16 +701,16 @@ __global__ void __launch_bounds__(round_up32(NP *NP *NP)) k_stage_mixed(const Mi
             double w[5] = {val[0], val[1], val[2], val[3], val[4]};
             if (sr_fix(a.d_atm, a.tau_atm, w)) {
                 needfix = true;
-                if (a.S == nullptr)
+                if (!a.lim)
 #pragma unroll
                     for (int v = 0; v < 5; ++v) val[v] = w[v];
             }
         }
     }
-    if (t < NN)
+    if (own)
 #pragma unroll
-        for (int v = 0; v < 5; ++v) a.out[(e * 5 + v) * NN + t] = val[v];
-    if (a.S == nullptr) return;
+        for (int v = 0; v < 5; ++v) sl.out[(e * 5 + v) * NN + t] = val[v];
+    if (!a.lim) return;
 
     // Limiter summaries of the output in FP64 (the limiter's decisions and its
     // replacement, and through them the conserved fix at the replaced nodes, are
@@ -646,13 +719,14 @@ __global__ void __launch_bounds__(round_up32(NP *NP *NP)) k_stage_mixed(const Mi
     // give the cell mean sum_i w_i Q_0[i] / 8, the face means Q_a[0] / 4 and
     // Q_a[NP-1] / 4, and the P1 coefficients sum_i row1_i Q_a[i] / 4.  The FP64 copy
     // of the output overlays the flux array, which is no longer read.
-    double *sV = reinterpret_cast<double *>(smem_mixed);
-    if (t < NN)
+    double *sV = reinterpret_cast<double *>(base);
+    if (own)
 #pragma unroll
         for (int v = 0; v < 5; ++v) sV[v * NN + t] = val[v];
-    const int anybad = __syncthreads_or(bad);
-    const int anyfix = __syncthreads_or(needfix);
-    for (int id = t; id < 15 * NP; id += blockDim.x) {
+    if (bad) atomicOr(&sFlag[0], 1);
+    if (needfix) atomicOr(&sFlag[1], 1);
+    __syncthreads();
+    for (int id = t; live && id < 15 * NP; id += TPE) {
         const int ax = id / (5 * NP), ia = (id / 5) % NP, v = id % 5;
         const int b = (ax + 1) % 3, c = (ax + 2) % 3;
         const double *Vv = sV + v * NN;
@@ -671,7 +745,7 @@ __global__ void __launch_bounds__(round_up32(NP *NP *NP)) k_stage_mixed(const Mi
         sQ[(ax * NP + ia) * 5 + v] = q;
     }
     __syncthreads();
-    for (int id = t; id < 50; id += blockDim.x) {
+    for (int id = t; live && id < 50; id += TPE) {
         const int v = id / 10, kind = id % 10;
         double r;
         if (kind == 0) {
@@ -687,9 +761,9 @@ __global__ void __launch_bounds__(round_up32(NP *NP *NP)) k_stage_mixed(const Mi
             for (int i = 0; i < NP; ++i) s = fma(sRow164[i], sQ[(ax * NP + i) * 5 + v], s);
             r = s * 0.25;
         }
-        a.S[e * 50 + id] = r;
+        sl.S[e * 50 + id] = r;
     }
-    if (SYS == 1 && t == 0 && a.flags) a.flags[e] = (anybad ? 1 : 0) | (anyfix ? 2 : 0);
+    if (SYS == 1 && live && t == 0 && sl.flags) sl.flags[e] = (sFlag[0] ? 1 : 0) | (sFlag[1] ? 2 : 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -701,19 +775,28 @@ __global__ void __launch_bounds__(round_up32(NP *NP *NP)) k_stage_mixed(const Mi
 // FP64; then (SR) the conserved fix of Sec. 2.1.4 runs in FP64 on every node that
 // an FP32 screen of its bounds does not clear.  Elements that are neither
 // troubled nor flagged by the stage kernel as needing the fix are left alone.
-struct LimitMixedArgs {
+// Like the stage kernel, a launch covers one mesh or a ragged batch of meshes.
+struct LimitSlot {
     double *U;
     const double *S;
     const unsigned char *flags;
     unsigned char *troubled;
-    long long E;
     int K[3];
-    int limiter;
     double tvb[3];          // M dx_a^2
     double inv_dx[3];       // 1 / dx_a
     double beta_dx[3];      // beta / dx_a
+    double hdx[3];          // dx_a / 2
+};
+
+struct LimitMixedArgs {
+    LimitSlot one;
+    const LimitSlot *slots;
+    const long long *elem0;
+    int nslots;
+    long long E;            // elements in the launch
+    int limiter;
     double d_atm, tau_atm;
-    double hx[3][MAXN];     // 0.5 dx_a xbar_i
+    double x[MAXN];         // LGL nodes
 };
 
 template <int NP, int SYS>
@@ -723,15 +806,22 @@ __global__ void __launch_bounds__(256) k_limit_mixed(const LimitMixedArgs a)
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (warp >= a.E) return;
-    const long long e = warp;
+    long long e = warp;
+    const LimitSlot *slp = &a.one;
+    if (a.slots) {
+        const int m = find_slot(a.elem0, a.nslots, warp);
+        slp = a.slots + m;
+        e = warp - a.elem0[m];
+    }
+    const LimitSlot &sl = *slp;
     int flag = 0;
-    double sl = 0.0, U0 = 0.0;
+    double slope = 0.0, U0 = 0.0;
     if (lane < 15) {
         const int v = lane / 3, ax = lane % 3;
-        const double *Se = a.S + (e * 5 + v) * 10;
+        const double *Se = sl.S + (e * 5 + v) * 10;
         U0 = Se[0];
-        const double U0m = a.S[(elem_neighbour(e, a.K, ax, -1) * 5 + v) * 10];
-        const double U0p = a.S[(elem_neighbour(e, a.K, ax, +1) * 5 + v) * 10];
+        const double U0m = sl.S[(elem_neighbour(e, sl.K, ax, -1) * 5 + v) * 10];
+        const double U0p = sl.S[(elem_neighbour(e, sl.K, ax, +1) * 5 + v) * 10];
         flag = (a.limiter == 2);
         if (a.limiter == 1) {
             const double ulo = Se[1 + 2 * ax], uhi = Se[2 + 2 * ax];
@@ -739,34 +829,35 @@ __global__ void __launch_bounds__(256) k_limit_mixed(const LimitMixedArgs a)
             const double vr = U0 + minmod3(uhi - U0, U0 - U0m, U0p - U0);
             if (fabs(vl - ulo) > 1e-8 || fabs(vr - uhi) > 1e-8) flag = 1;
         }
-        const double s1 = 2.0 * Se[7 + ax] * a.inv_dx[ax];
-        sl = (fabs(s1) <= a.tvb[ax]) ? s1 : minmod3(s1, (U0p - U0) * a.beta_dx[ax], (U0 - U0m) * a.beta_dx[ax]);
+        const double s1 = 2.0 * Se[7 + ax] * sl.inv_dx[ax];
+        slope = (fabs(s1) <= sl.tvb[ax]) ? s1
+                                         : minmod3(s1, (U0p - U0) * sl.beta_dx[ax], (U0 - U0m) * sl.beta_dx[ax]);
     }
     const unsigned fb = __ballot_sync(0xffffffffu, flag);
     unsigned mask = 0;
 #pragma unroll
     for (int v = 0; v < 5; ++v)
         if ((fb >> (3 * v)) & 7u) mask |= 1u << v;
-    const unsigned char fl = a.flags ? a.flags[e] : 0;
+    const unsigned char fl = sl.flags ? sl.flags[e] : 0;
     if (fl & 1) mask = 0x1fu;
-    if (lane == 0 && a.troubled) a.troubled[e] = (unsigned char)mask;
+    if (lane == 0 && sl.troubled) sl.troubled[e] = (unsigned char)mask;
     if (!mask && !(fl & 2)) return;
     double m0[5], s0[5], s1[5], s2[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
         m0[v] = __shfl_sync(0xffffffffu, U0, 3 * v);
-        s0[v] = __shfl_sync(0xffffffffu, sl, 3 * v);
-        s1[v] = __shfl_sync(0xffffffffu, sl, 3 * v + 1);
-        s2[v] = __shfl_sync(0xffffffffu, sl, 3 * v + 2);
+        s0[v] = __shfl_sync(0xffffffffu, slope, 3 * v);
+        s1[v] = __shfl_sync(0xffffffffu, slope, 3 * v + 1);
+        s2[v] = __shfl_sync(0xffffffffu, slope, 3 * v + 2);
     }
     for (int q = lane; q < NN; q += 32) {
         const int i = q % NP, j = (q / NP) % NP, k = q / (NP * NP);
+        const double h0 = sl.hdx[0] * a.x[i], h1 = sl.hdx[1] * a.x[j], h2 = sl.hdx[2] * a.x[k];
         double u[5];
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
             const long long ix = (e * 5 + v) * NN + q;
-            u[v] = (mask & (1u << v)) ? m0[v] + s0[v] * a.hx[0][i] + s1[v] * a.hx[1][j] + s2[v] * a.hx[2][k]
-                                      : a.U[ix];
+            u[v] = (mask & (1u << v)) ? m0[v] + s0[v] * h0 + s1[v] * h1 + s2[v] * h2 : sl.U[ix];
         }
         unsigned nm = mask;
         if (SYS == 1) {
@@ -786,16 +877,20 @@ __global__ void __launch_bounds__(256) k_limit_mixed(const LimitMixedArgs a)
         }
 #pragma unroll
         for (int v = 0; v < 5; ++v)
-            if (nm & (1u << v)) a.U[(e * 5 + v) * NN + q] = u[v];
+            if (nm & (1u << v)) sl.U[(e * 5 + v) * NN + q] = u[v];
     }
 }
 
 template <int NP>
-cudaError_t launch_stage_mixed_np(int system, int flux, const MixedArgs &a, long long E, cudaStream_t s)
+cudaError_t launch_stage_mixed_np(int system, int flux, const MixedArgs &a, cudaStream_t s)
 {
-    const dim3 grid((unsigned)E), block(round_up32(NP * NP * NP));
+    using SS = StageShape<NP>;
+    if (a.epb < 1 || a.epb > SS::MAX_EPB) return cudaErrorInvalidValue;
+    if (a.nelem <= 0) return cudaSuccess;
+    const long long blocks = (a.nelem + a.epb - 1) / a.epb;
+    const dim3 grid((unsigned)blocks), block(SS::TPE * a.epb);
     const bool learned = system == 1 && a.netP != nullptr;
-    const size_t smem = learned ? MixedSmem<NP>::TOTAL_LEARNED : MixedSmem<NP>::MAIN;
+    const size_t smem = MixedSmem<NP>::total(a.epb, learned);
     void (*kern)(const MixedArgs);
     if (system == 0 && flux == 0) kern = k_stage_mixed<NP, 0, 0, 0>;
     else if (system == 0) kern = k_stage_mixed<NP, 0, 1, 0>;
@@ -812,6 +907,7 @@ cudaError_t launch_stage_mixed_np(int system, int flux, const MixedArgs &a, long
 template <int NP>
 cudaError_t launch_limit_mixed_np(int system, const LimitMixedArgs &a, cudaStream_t s)
 {
+    if (a.E <= 0) return cudaSuccess;
     const long long threads = a.E * 32;
     const unsigned grid = (unsigned)((threads + 255) / 256);
     if (system == 0) k_limit_mixed<NP, 0><<<grid, 256, 0, s>>>(a);
@@ -819,14 +915,21 @@ cudaError_t launch_limit_mixed_np(int system, const LimitMixedArgs &a, cudaStrea
     return cudaGetLastError();
 }
 
+// Largest elements-per-CTA of the stage kernel for n nodes per axis.
+inline int stage_max_epb(int n)
+{
+    const int nn = n * n * n, tpe = round_up32(nn);
+    const int maxt = tpe > 256 ? tpe : 256;
+    return maxt / tpe;
+}
+
 }  // namespace dg
 
 #define DG_INSTANTIATE_MIXED(NP)                                                                       \
     namespace dg {                                                                                     \
-    cudaError_t launch_stage_mixed_n##NP(int system, int flux, const MixedArgs &a, long long E,         \
-                                         cudaStream_t s)                                               \
+    cudaError_t launch_stage_mixed_n##NP(int system, int flux, const MixedArgs &a, cudaStream_t s)      \
     {                                                                                                  \
-        return launch_stage_mixed_np<NP>(system, flux, a, E, s);                                       \
+        return launch_stage_mixed_np<NP>(system, flux, a, s);                                          \
     }                                                                                                  \
     cudaError_t launch_limit_mixed_n##NP(int system, const LimitMixedArgs &a, cudaStream_t s)           \
     {                                                                                                  \
