@@ -114,15 +114,15 @@ def _init_state(pkg, mesh, torch):
     return mesh.from_prim(torch.from_numpy(prim).cuda())
 
 
-# DRAM bytes per k_stage_mixed launch on this workload (mean over the three stages
-# of a step), from the ncu capture summarised in
+# DRAM bytes per k_stage_mixed launch (learned guess) on this workload (mean over
+# the three stages of a step), from the ncu capture summarised in
 # profiles/k_stage_mixed_sr_blast_16x16x16_n5.md.  Reported only while the
 # kernel's sources still hash to the value they had when it was taken.
-TRAFFIC_BYTES_PER_LAUNCH = 37943211.0
+TRAFFIC_BYTES_PER_LAUNCH = 34925824.0
 TRAFFIC_SOURCES = ("paper_1609_00098_gb300/csrc/dg_mixed.cuh", "paper_1609_00098_gb300/csrc/dg_physics.cuh",
-                   "paper_1609_00098_gb300/csrc/dg_internal.h")
-TRAFFIC_SOURCES_SHA256 = "588ff2c5343eec5384ea413ec5fa2f8b93a7d74c72cf33ca5cd39e51edfb15d9"
-TRAFFIC_VARIANT = "warm_start"
+                   "paper_1609_00098_gb300/csrc/dg_internal.h", "paper_1609_00098_gb300/csrc/dg_c2p_net.cuh")
+TRAFFIC_SOURCES_SHA256 = "1eb12feaba94f43c303542b83bcbfb5af53b431139f5b6c4efac68f674c529f4"
+TRAFFIC_VARIANT = "learned"
 
 
 def _traffic(variant):
@@ -192,6 +192,73 @@ def _train_guess_net(pkg, torch):
             "epochs": epochs, "batch": 2048, "train_s": round(time.time() - t0, 3),
             "loss_first_last": [float(losses[0]), float(losses[-1])]}
     return net, info
+
+
+def _ensemble(pkg, torch, net, args):
+    """Ragged ensemble (untimed setup): 256 meshes from the seeded recipe -- system
+    NE or SR with probability 1/2, K uniform in [2, 16] per axis, n uniform in
+    [3, 8].  NE meshes carry the smooth density wave (LLF, no limiter), SR meshes
+    the blast (HLL, MinModN, learned con2prim guess); mixed precision, CFL 0.2.
+    Times `ens_steps` steps of (a) the batched per-group launches replayed as one
+    CUDA graph per step, after the launch-shape autotuner, and (b) the same meshes
+    stepped one by one with dg_rk3_step.  The states (2.7 GB each) exceed L2."""
+    recipe = dg_inputs.ensemble_recipe(5)
+    meshes, states = [], []
+    for system, K, n in recipe:
+        g = 4.0 / 3.0 if system else 1.4
+        m = pkg.Mesh(system=system, K=(K, K, K), n=n, flux=1 if system else 0, limiter=1 if system else 0,
+                     gamma=g, precision=1)
+        if system:
+            m.set_c2p_net(net)
+        xyz = m.coords().cpu().numpy()
+        prim = dg_inputs.blast_sr(xyz, seed=1) if system else dg_inputs.smooth_wave_ne(
+            xyz, k=dg_inputs.wave_numbers(1))
+        states.append(m.from_prim(torch.from_numpy(prim).cuda()))
+        meshes.append(m)
+    nodes = sum(m.E * m.nn for m in meshes)
+    ens = pkg.abi.dg_ensemble_create([m.h for m in meshes], states)
+    t0 = time.time()
+    pkg.abi.dg_ensemble_tune(ens)
+    tune_s = time.time() - t0
+    stream = torch.cuda.current_stream()
+
+    def timed(step_all):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.ens_steps)]
+        torch.cuda.synchronize()
+        for a, b in ev:
+            a.record(stream)
+            step_all()
+            b.record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ev)
+
+    for _ in range(3):
+        pkg.abi.dg_ensemble_step(ens, 0.2, use_graph=True)
+    batched_ms = timed(lambda: pkg.abi.dg_ensemble_step(ens, 0.2, use_graph=True))
+
+    def one_by_one():
+        for m, U in zip(meshes, states):
+            m.rk3_step(U, cfl=0.2)
+    one_by_one()
+    permesh_ms = timed(one_by_one)
+    status = max(m.sync_status() for m in meshes)
+    groups = pkg.abi.dg_ensemble_groups(ens)
+    for g in groups:
+        g.pop("members", None)
+    pkg.abi.dg_ensemble_destroy(ens)
+    for m in meshes:
+        m.close()
+    dof = nodes * 5 * args.ens_steps
+    return {"workload": "256 meshes: NE smooth wave (LLF) or SR blast (HLL, MinModN, learned guess), "
+                        "K in [2,16], n in [3,8], seed 5, mixed precision, CFL 0.2",
+            "meshes": len(recipe), "nodes": nodes, "steps": args.ens_steps,
+            "batched_graph": {"value": dof / (batched_ms / 1e3), "unit": UNIT,
+                              "ms_per_step": batched_ms / args.ens_steps},
+            "per_mesh_launches": {"value": dof / (permesh_ms / 1e3), "unit": UNIT,
+                                  "ms_per_step": permesh_ms / args.ens_steps},
+            "speedup": permesh_ms / batched_ms, "tune_s": round(tune_s, 3), "groups": groups,
+            "device_status": status}
 
 
 def _measure(pkg, torch, precision, args, dist, U0, net=None):
@@ -381,6 +448,8 @@ def run_ours(args):
         "clocks": clk,
         "device_status": status,
     }
+    if not args.no_ensemble:
+        out["ensemble"] = _ensemble(pkg, torch, net, args)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(seconds=args.cpu_seconds)
     for r in results.values():
@@ -459,6 +528,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--acc-steps", type=int, default=10)
+    ap.add_argument("--ens-steps", type=int, default=20)
+    ap.add_argument("--no-ensemble", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

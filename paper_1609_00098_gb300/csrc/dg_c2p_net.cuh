@@ -91,9 +91,12 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
     return *reinterpret_cast<const uint32_t *>(&v);
 }
 
-// Network weights staged in shared memory for in-kernel inference.
+// Network weights staged in shared memory for in-kernel inference.  W2's rows
+// are padded to 72 BF16 (144 bytes): the eight rows a B-fragment load touches then
+// fall in different banks.
+constexpr int NET_W2_LD = 72;
 struct NetWeightsSmem {
-    __nv_bfloat16 W2[64][64];  // [j][i]: the B^T operand of layer 2
+    __nv_bfloat16 W2[64][NET_W2_LD];  // [j][i]: the B^T operand of layer 2
     float W1[64][3], b1[64], b2[64], W3[64], b3;
 };
 
@@ -102,9 +105,8 @@ struct NetWeightsSmem {
 // waits about one L2 round trip rather than one per element.
 __device__ __forceinline__ void net_stage_weights(NetWeightsSmem &W, const float *P, const __nv_bfloat16 *W2b)
 {
-    constexpr int NV = 64 * 64 * 2 / 16;  // uint4 vectors of W2
+    constexpr int NV = 64 * 64 * 2 / 16;  // uint4 vectors of W2, 8 per row
     const uint4 *src = reinterpret_cast<const uint4 *>(W2b);
-    uint4 *dst = reinterpret_cast<uint4 *>(&W.W2[0][0]);
     for (int k0 = 0; k0 < NV; k0 += 4 * (int)blockDim.x) {
         uint4 r[4];
 #pragma unroll
@@ -115,7 +117,7 @@ __device__ __forceinline__ void net_stage_weights(NetWeightsSmem &W, const float
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int k = k0 + j * blockDim.x + threadIdx.x;
-            if (k < NV) dst[k] = r[j];
+            if (k < NV) *reinterpret_cast<uint4 *>(&W.W2[k >> 3][(k & 7) * 8]) = r[j];
         }
     }
     for (int k = threadIdx.x; k < 192 + 64; k += blockDim.x) {
@@ -182,7 +184,7 @@ __device__ __forceinline__ void net_guess_rows(const NetWeightsSmem &W, const fl
 #pragma unroll
             for (int nt = 0; nt < 8; ++nt) {
                 uint32_t bf[2];
-                load_b(bf, &W.W2[0][0], 64, kk * 16, nt * 8, lane);
+                load_b(bf, &W.W2[0][0], NET_W2_LD, kk * 16, nt * 8, lane);
                 mma_bf16(acc[nt], af, bf);
             }
         }
