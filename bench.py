@@ -58,6 +58,24 @@ def _dist():
     return ws, rank, local
 
 
+def max_over_ranks(total_ms: float, dist=None) -> float:
+    """The slowest rank's time: the whole job is done when the last replica is.
+    NCCL reduces on the GPU, gloo (CPU tests) on the host."""
+    if not dist:
+        return float(total_ms)
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(nodes_per_rank: int, world_size: int, steps: int, total_ms: float) -> float:
+    """dof-updates/s of all replicas together: every rank advances its own copy
+    of the workload (weak scaling), and the job takes the slowest rank's time."""
+    return world_size * nodes_per_rank * 5 * steps / (total_ms / 1e3)
+
+
 class ClockSampler:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
 
@@ -362,17 +380,12 @@ def run_ours(args):
     clk = clocks.stop()
 
     def agg(ms):
-        total = float(sum(ms))
-        if dist:
-            t = torch.tensor([total], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total = float(t.item())
-        return total
+        return max_over_ranks(float(sum(ms)), dist)
 
     mesh, graph, step_ms, prof, status, mesh_state = results["learned"]
     total_ms = agg(step_ms)
     ms_per_step = total_ms / args.steps
-    value = ws * nodes * 5 * args.steps / (total_ms / 1e3)
+    value = whole_job_rate(nodes, ws, args.steps, total_ms)
     f_mesh, f_graph, f_ms, f_prof, f_status, _ = results["fp64"]
     f_total = agg(f_ms)
     w_mesh, w_graph, w_ms, w_prof, w_status, _ = results["warm_start"]

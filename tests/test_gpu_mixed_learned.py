@@ -126,3 +126,34 @@ def test_set_c2p_net_rejects_other_meshes(pkg, trained):
         with pytest.raises(pkg.abi.DGError):
             m.set_c2p_net(trained)
         m.set_c2p_net(None)
+
+
+def test_full_size_blast_learned_graph_replay(pkg, trained):
+    """The bench workload at full size in the bench's launch configuration: the
+    mixed path with the learned guess, one CFL step captured into a CUDA graph and
+    replayed.  After 10 steps (the oracle takes the GPU's dt sequence) the state
+    is within the 1e-6 bar of the FP64 oracle."""
+    import torch
+    om = oracle.Mesh(oracle.MeshSpec(system=1, K=(16, 16, 16), n=5, flux=1, limiter=1, gamma=G))
+    gm = pkg.Mesh(system=1, K=(16, 16, 16), n=5, flux=1, limiter=1, gamma=G, precision=1)
+    gm.set_c2p_net(trained)
+    U = om.from_prim(di.blast_sr(om.coords(), seed=1))
+    Ug = _gpu(U)
+    dt = torch.zeros(1, dtype=torch.float64, device="cuda")
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        gm.rk3_step(Ug, cfl=0.2, dt_used=dt)   # first step (warm-up, outside the graph)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    U = om.rk3_step(U, float(dt.item()))
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        gm.rk3_step(Ug, cfl=0.2, dt_used=dt)
+    for _ in range(9):
+        graph.replay()
+        torch.cuda.synchronize()
+        U = om.rk3_step(U, float(dt.item()))
+    assert gm.sync_status() == 0
+    d = _rel_l2(om, Ug.cpu().numpy(), U)
+    assert np.all(d <= 1e-6), d

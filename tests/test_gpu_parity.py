@@ -262,3 +262,52 @@ def test_full_size_blast_one_step(pkg):
     assert abs(dt.item() - h) <= 4e-16 * h
     assert np.array_equal(tg.cpu().numpy(), to)
     assert _rel(Ug.cpu().numpy(), Uo).max() <= TOL
+
+
+def test_full_size_con2prim_2p24(pkg):
+    """The standalone con2prim workload at full size (2^24 seeded states): the
+    GPU's primitives and iteration counts are bitwise the oracle's on every node."""
+    import torch
+    g = 4.0 / 3.0
+    N = 1 << 24
+    prim = di.c2p_samples(3, N, gamma=g)
+    cons = oracle.prim2con(1, g, prim)
+    del prim
+    po, ito, sto = oracle.con2prim(g, cons)
+    pg = torch.empty((5, N), dtype=torch.float64, device="cuda")
+    it = torch.empty(N, dtype=torch.int32, device="cuda")
+    st = torch.empty(N, dtype=torch.int32, device="cuda")
+    pkg.abi.dg_con2prim(N, g, _gpu(cons), pg, None, it, st)
+    assert np.array_equal(st.cpu().numpy(), sto) and np.all(sto == 0)
+    assert np.array_equal(pg.cpu().numpy(), po)
+    assert np.array_equal(it.cpu().numpy(), ito)
+
+
+def test_full_size_kh_one_step(pkg):
+    """The Kelvin-Helmholtz workload at full size (64^3 elements, n = 6, HLL,
+    MinModN; 56.6 M nodes): one CFL step, FP64 path bitwise equal to the oracle
+    (state, troubled flags, dt); the mixed path within FP32 rounding of it."""
+    import torch
+    kw = dict(system=0, K=(64, 64, 64), n=6, flux=1, limiter=1, gamma=5.0 / 3.0, lo=(-0.5,) * 3, hi=(0.5,) * 3)
+    om, gm = _pair(pkg, **kw)
+    U = _init(om, "kh", seed=1)
+    h = om.cfl_dt(U, 0.2)
+    to = np.zeros(om.E, dtype=np.uint8)
+    Uo = om.rk3_step(U, h, to)
+    Ug = _gpu(U)
+    dt = torch.zeros(1, dtype=torch.float64, device="cuda")
+    tg = torch.zeros(om.E, dtype=torch.uint8, device="cuda")
+    gm.rk3_step(Ug, cfl=0.2, dt_used=dt, troubled=tg)
+    assert gm.sync_status() == 0
+    assert dt.item() == h
+    assert np.array_equal(tg.cpu().numpy(), to)
+    assert np.array_equal(Ug.cpu().numpy(), Uo)
+    del gm, Ug, tg
+    mm = pkg.Mesh(precision=1, **kw)
+    Um = _gpu(U)
+    mm.rk3_step(Um, dt=h)
+    assert mm.sync_status() == 0
+    # S_z of the shear layer is zero up to rounding: scales floored at 1 % of the largest
+    sc = np.abs(Uo).max(axis=(0, 2))
+    d = np.abs(Um.cpu().numpy() - Uo).max(axis=(0, 2)) / np.maximum(sc, 1e-2 * sc.max())
+    assert d.max() < 1e-5, d
