@@ -322,6 +322,7 @@ def dg_ensemble_dt(ens, dt, stream=None):
 
 OPT_TENSOR_CORE_CONTRACTION = 1
 OPT_C2P_KAPPA_SWITCH = 2
+OPT_ELEMENTS_PER_CTA = 3
 
 
 def dg_mesh_set_option(mesh, option, value):

@@ -313,7 +313,7 @@ MixedArgs mixed_args(const dg_mesh *m)
     a.one = mixed_slot(m);
     a.nslots = 1;
     a.nelem = m->E;
-    a.epb = 1;
+    a.epb = m->epb > 0 ? m->epb : 1;
     a.lim = m->d.limiter != 0;
     a.gamma = (float)m->d.gamma;
     a.gamma_d = m->d.gamma;
@@ -769,6 +769,14 @@ dg_status dg_mesh_set_option(dg_mesh *m, int option, double value)
         if (!(value >= 1.0 && value <= 1e30)) return fail(DG_ERR_ARG, "kappa switch must be in [1, 1e30]");
         m->kappa_sw = (float)value;
         return DG_OK;
+    case DG_OPT_ELEMENTS_PER_CTA: {
+        const int epb = (int)value;
+        if ((double)epb != value || epb < 1 || epb > stage_max_epb(m->d.n) || (epb & (epb - 1)))
+            return fail(DG_ERR_ARG, "elements per CTA must be a power of two in [1, %d] for n = %d",
+                        stage_max_epb(m->d.n), m->d.n);
+        m->epb = epb;
+        return DG_OK;
+    }
     default:
         return fail(DG_ERR_ARG, "unknown option %d", option);
     }

@@ -410,17 +410,26 @@ struct StageShape {
     static constexpr int TPE = round_up32(NN);
     static constexpr int MAXT = TPE > 256 ? TPE : 256;
     static constexpr int MAX_EPB = MAXT / TPE;
+    // CTAs of MAXT threads that must fit on an SM: for n <= 5 this caps the
+    // registers at 64 per thread (occupancy 50 % instead of ~37 %, a few spills)
+    static constexpr int MIN_CTAS = NN <= 128 ? 4 : 1;
 };
 
 // Shared memory of k_stage_mixed: per element (stride ELEM) the main arrays,
-// the plane sums, the neighbour indices, two flags, the element index and the
-// mesh slot; then (learned guess only) the network's weights, and the features
+// the neighbour face nodes (later the summaries' partial sums), the plane sums,
+// the neighbour indices, two flags, the element index and the mesh slot; then (learned guess only) the network's weights, and the features
 // and guesses of all the CTA's nodes.
 template <int NP>
 struct MixedSmem {
     static constexpr int NN = NP * NP * NP;
+    static constexpr int NF = 6 * NP * NP;                           // face points (both sides, 3 axes)
     static constexpr size_t MAIN = sizeof(float) * (25 + NPRIM) * NN;
-    static constexpr size_t Q = (MAIN + 15) / 16 * 16;
+    // neighbour face-node states [5][NF] and guesses [NF] (face phase), later the
+    // summaries' partial sums [3][NP][NP][5] (FP64)
+    static constexpr size_t FACE = (MAIN + 15) / 16 * 16;
+    static constexpr size_t FACE_BYTES = sizeof(float) * 6 * NF > sizeof(double) * 15 * NP * NP
+                                             ? sizeof(float) * 6 * NF : sizeof(double) * 15 * NP * NP;
+    static constexpr size_t Q = (FACE + FACE_BYTES + 15) / 16 * 16;
     static constexpr size_t NB = Q + sizeof(double) * 3 * NP * 5;
     static constexpr size_t FLAG = NB + sizeof(long long) * 7;      // 6 neighbours + element index
     static constexpr size_t SLOT = (FLAG + 2 * sizeof(int) + 15) / 16 * 16;
@@ -440,7 +449,7 @@ __device__ __forceinline__ bool sr_screen32(const float u[5], float d_atm, float
            !(s2 < 0.999f * u[4] * (u[4] + 2.0f * u[0]));
 }
 template <int NP, int SYS, int FLX, int GUESS>
-__global__ void __launch_bounds__(StageShape<NP>::MAXT) k_stage_mixed(const MixedArgs a)
+__global__ void __launch_bounds__(StageShape<NP>::MAXT, StageShape<NP>::MIN_CTAS) k_stage_mixed(const MixedArgs a)
 {
     constexpr int NN = NP * NP * NP;
     constexpr int TPE = StageShape<NP>::TPE;
@@ -453,6 +462,10 @@ __global__ void __launch_bounds__(StageShape<NP>::MAXT) k_stage_mixed(const Mixe
     float *sU = sR + 5 * NN;                       // [5][NN] stage input state (FP32)
     float *sP = sU + 5 * NN;                       // [NPRIM][NN] primitives of the input
     double *sQ = reinterpret_cast<double *>(base + SM::Q);
+    constexpr int NF = SM::NF;
+    float *sFU = reinterpret_cast<float *>(base + SM::FACE);  // [5][NF] neighbour face-node states
+    float *sFG = sFU + 5 * NF;                                // [NF] their con2prim guesses (warm start)
+    double *sPart = reinterpret_cast<double *>(base + SM::FACE);
     long long *sNb = reinterpret_cast<long long *>(base + SM::NB);
     int *sFlag = reinterpret_cast<int *>(base + SM::FLAG);
     MeshSlot &sl = *reinterpret_cast<MeshSlot *>(base + SM::SLOT);
@@ -501,6 +514,22 @@ __global__ void __launch_bounds__(StageShape<NP>::MAXT) k_stage_mixed(const Mixe
         net_guess_rows(W, sFeat, sGuess, NN * a.epb, a.gamma, a.net_sc);
         __syncthreads();
         sGuess += sub * NN;
+    }
+
+    // Neighbour face nodes of all three axes (point f = 2 NP^2 ax + NP^2 side + rem):
+    // their FP32 states and guesses, staged while the element's own nodes load.
+    for (int f = t; live && f < NF; f += TPE) {
+        const int ax = f / (2 * NP * NP), fpa = f % (2 * NP * NP);
+        const int side = fpa / (NP * NP), rem = fpa % (NP * NP);
+        int id[3];
+        id[ax] = side ? 0 : NP - 1;
+        id[(ax + 1) % 3] = rem % NP;
+        id[(ax + 2) % 3] = rem / NP;
+        const int qn = id[0] + NP * (id[1] + NP * id[2]);
+        const long long en = elem_neighbour(e, sl.K, ax, side ? 1 : -1);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) sFU[v * NF + f] = f64_to_f32(sl.Us[(en * 5 + v) * NN + qn]);
+        if (!GUESS) sFG[f] = sl.pin ? sl.pin[en * NN + qn] : -1.0f;
     }
 
     if (own) {
@@ -623,44 +652,61 @@ __global__ void __launch_bounds__(StageShape<NP>::MAXT) k_stage_mixed(const Mixe
         __syncthreads();
     }
 
-    // surface terms; the neighbour's face node is recovered here from its FP64 state
-    for (int ax = 0; ax < 3; ++ax) {
-        for (int fp = t; live && fp < 2 * NP * NP; fp += TPE) {
-            const int side = fp / (NP * NP);
-            const int rem = fp % (NP * NP);
-            int id[3];
-            id[ax] = side ? NP - 1 : 0;
-            id[(ax + 1) % 3] = rem % NP;
-            id[(ax + 2) % 3] = rem / NP;
-            const int q = id[0] + NP * (id[1] + NP * id[2]);
-            id[ax] = side ? 0 : NP - 1;
-            const int qn = id[0] + NP * (id[1] + NP * id[2]);
-            const long long en = sNb[2 * ax + side];
-            float uo[5], Po[NPRIM], un[5], Pn[NPRIM];
+    // Surface terms (eq:411, lift of reading R1) for the face points of all three
+    // axes at once; the neighbour's face node is recovered here from its staged
+    // state.  Each axis's lift goes to its own array (over the flux arrays, no
+    // longer read): within an axis a node lies on at most one face, so there are no
+    // write conflicts, and the three are summed in a fixed order afterwards.
+    float *sA = sF;  // [3][5][NN]
+    if (own)
 #pragma unroll
-            for (int v = 0; v < 5; ++v) {
-                uo[v] = sU[v * NN + q];
-                un[v] = f64_to_f32(sl.Us[(en * 5 + v) * NN + qn]);
-            }
+        for (int c = 0; c < 15; ++c) sA[c * NN + t] = 0.0f;
+    __syncthreads();
+    for (int f = t; live && f < NF; f += TPE) {
+        const int ax = f / (2 * NP * NP), fpa = f % (2 * NP * NP);
+        const int side = fpa / (NP * NP), rem = fpa % (NP * NP);
+        int id[3];
+        id[ax] = side ? NP - 1 : 0;
+        id[(ax + 1) % 3] = rem % NP;
+        id[(ax + 2) % 3] = rem / NP;
+        const int q = id[0] + NP * (id[1] + NP * id[2]);
+        id[ax] = side ? 0 : NP - 1;
+        const int qn = id[0] + NP * (id[1] + NP * id[2]);
+        float uo[5], Po[NPRIM], un[5], Pn[NPRIM];
 #pragma unroll
-            for (int c = 0; c < NPRIM; ++c) Po[c] = sP[c * NN + q];
-            const float gn = GUESS ? Po[3] : (sl.pin ? sl.pin[en * NN + qn] : -1.0f);
-            if (SYS == 0) ne_primitives32(a.gamma, un, Pn);
-            else errs |= sr_prims_mixed(a.gamma, a.gamma_d, a.kappa_sw, a.d_atm, a.tau_atm, un,
-                                        sl.Us + en * 5 * NN + qn, NN, gn, Pn);
-            float dL[5], dR[5];
-            if (side) {
-                num_flux_jump32<SYS, FLX>(a.gamma, ax, uo, Po, un, Pn, dL, dR);
-#pragma unroll
-                for (int v = 0; v < 5; ++v) sR[v * NN + q] -= sl.liftN[ax] * dL[v];
-            } else {
-                num_flux_jump32<SYS, FLX>(a.gamma, ax, un, Pn, uo, Po, dL, dR);
-#pragma unroll
-                for (int v = 0; v < 5; ++v) sR[v * NN + q] += sl.lift0[ax] * dR[v];
-            }
+        for (int v = 0; v < 5; ++v) {
+            uo[v] = sU[v * NN + q];
+            un[v] = sFU[v * NF + f];
         }
-        __syncthreads();
+#pragma unroll
+        for (int c = 0; c < NPRIM; ++c) Po[c] = sP[c * NN + q];
+        const float gn = GUESS ? Po[3] : sFG[f];
+        if (SYS == 0) {
+            ne_primitives32(a.gamma, un, Pn);
+        } else {
+            const long long en = sNb[2 * ax + side];
+            errs |= sr_prims_mixed(a.gamma, a.gamma_d, a.kappa_sw, a.d_atm, a.tau_atm, un,
+                                   sl.Us + en * 5 * NN + qn, NN, gn, Pn);
+        }
+        float dL[5], dR[5];
+        float *acc = sA + ax * 5 * NN + q;
+        if (side) {
+            num_flux_jump32<SYS, FLX>(a.gamma, ax, uo, Po, un, Pn, dL, dR);
+            const float lN = sl.liftN[ax];
+#pragma unroll
+            for (int v = 0; v < 5; ++v) acc[v * NN] = -lN * dL[v];
+        } else {
+            num_flux_jump32<SYS, FLX>(a.gamma, ax, un, Pn, uo, Po, dL, dR);
+            const float l0 = sl.lift0[ax];
+#pragma unroll
+            for (int v = 0; v < 5; ++v) acc[v * NN] = l0 * dR[v];
+        }
     }
+    __syncthreads();
+    if (own)
+#pragma unroll
+        for (int v = 0; v < 5; ++v)
+            sR[v * NN + t] += (sA[v * NN + t] + sA[(5 + v) * NN + t]) + sA[(10 + v) * NN + t];
     if (errs) atomicOr(sl.err, errs);
 
     // Stage update in FP64: U_{s+1} = U_s + [ca (U^n - U_s) + cb dt R], the bracket
@@ -726,22 +772,26 @@ __global__ void __launch_bounds__(StageShape<NP>::MAXT) k_stage_mixed(const Mixe
     if (bad) atomicOr(&sFlag[0], 1);
     if (needfix) atomicOr(&sFlag[1], 1);
     __syncthreads();
-    for (int id = t; live && id < 15 * NP; id += TPE) {
-        const int ax = id / (5 * NP), ia = (id / 5) % NP, v = id % 5;
+    // partial sums over t0 for every (axis, plane, t1, variable), then over t1
+    for (int id = t; live && id < 15 * NP * NP; id += TPE) {
+        const int v = id % 5, t1 = (id / 5) % NP, ia = (id / (5 * NP)) % NP, ax = id / (5 * NP * NP);
         const int b = (ax + 1) % 3, c = (ax + 2) % 3;
         const double *Vv = sV + v * NN;
-        double q = 0.0;
-        for (int t1 = 0; t1 < NP; ++t1) {
-            double r = 0.0;
-            for (int t0 = 0; t0 < NP; ++t0) {
-                int id3[3];
-                id3[ax] = ia;
-                id3[b] = t0;
-                id3[c] = t1;
-                r = fma(sW64[t0], Vv[id3[0] + NP * (id3[1] + NP * id3[2])], r);
-            }
-            q = fma(sW64[t1], r, q);
+        double r = 0.0;
+        for (int t0 = 0; t0 < NP; ++t0) {
+            int id3[3];
+            id3[ax] = ia;
+            id3[b] = t0;
+            id3[c] = t1;
+            r = fma(sW64[t0], Vv[id3[0] + NP * (id3[1] + NP * id3[2])], r);
         }
+        sPart[id] = r;
+    }
+    __syncthreads();
+    for (int id = t; live && id < 15 * NP; id += TPE) {
+        const int ax = id / (5 * NP), ia = (id / 5) % NP, v = id % 5;
+        double q = 0.0;
+        for (int t1 = 0; t1 < NP; ++t1) q = fma(sW64[t1], sPart[((ax * NP + ia) * NP + t1) * 5 + v], q);
         sQ[(ax * NP + ia) * 5 + v] = q;
     }
     __syncthreads();

@@ -188,3 +188,30 @@ def test_mesh_options_validate(pkg):
             gm.set_option(opt, bad)
     gm.set_option(pkg.abi.OPT_C2P_KAPPA_SWITCH, 1e3)
     gm.set_option(pkg.abi.OPT_TENSOR_CORE_CONTRACTION, 0)
+    for bad in (0, 3, 16):
+        with pytest.raises(pkg.abi.DGError):
+            gm.set_option(pkg.abi.OPT_ELEMENTS_PER_CTA, bad)
+    gm.set_option(pkg.abi.OPT_ELEMENTS_PER_CTA, 8)
+
+
+@pytest.mark.parametrize("n,epb", [(3, 4), (4, 2), (5, 2)])
+def test_elements_per_cta_do_not_change_results(pkg, n, epb):
+    """Several elements per CTA (the learned guess batched over all of them)
+    give the same bits as one element per CTA."""
+    from oracle import mlp
+    net = pkg.abi.dg_c2p_net_create(mlp.init_params(di.uniform(5, 9, np.arange(mlp.N_PARAMS))).astype(np.float32),
+                                    mlp.DEFAULT_SCALES)
+    try:
+        out = []
+        for e in (1, epb):
+            om, gm = _pair(pkg, 1, (3, 3, 2), n, 1, 1)
+            gm.set_c2p_net(net)
+            gm.set_option(pkg.abi.OPT_ELEMENTS_PER_CTA, e)
+            U = _gpu(om.from_prim(di.blast_sr(om.coords(), seed=2)))
+            for _ in range(3):
+                gm.rk3_step(U, cfl=0.2)
+            assert gm.sync_status() == 0
+            out.append(U.cpu().numpy())
+        assert np.array_equal(out[0], out[1])
+    finally:
+        pkg.abi.dg_c2p_net_destroy(net)

@@ -307,7 +307,8 @@ def test_full_size_kh_one_step(pkg):
     Um = _gpu(U)
     mm.rk3_step(Um, dt=h)
     assert mm.sync_status() == 0
-    # S_z of the shear layer is zero up to rounding: scales floored at 1 % of the largest
-    sc = np.abs(Uo).max(axis=(0, 2))
-    d = np.abs(Um.cpu().numpy() - Uo).max(axis=(0, 2)) / np.maximum(sc, 1e-2 * sc.max())
-    assert d.max() < 1e-5, d
+    # max-norm error against the largest variable's scale (S_z of the shear layer
+    # is zero up to rounding and has no scale of its own): FP32 rounding level
+    sc = np.abs(Uo).max()
+    d = np.abs(Um.cpu().numpy() - Uo).max(axis=(0, 2)) / sc
+    assert d.max() < 2e-6, d
