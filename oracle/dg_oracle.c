@@ -138,6 +138,7 @@ int or_legendre_vinv(int n, const double *x, double *Vinv)
 or_mesh *or_mesh_create(const or_desc *d)
 {
     if (d->dim < 1 || d->dim > 3 || d->n < 2 || d->n > OR_MAXN) return NULL;
+    if (d->flux < 0 || d->flux > 2 || (d->flux == 2 && d->system != 0)) return NULL;  /* Roe: Newtonian only */
     or_mesh *m = (or_mesh *)calloc(1, sizeof(or_mesh));
     m->d = *d;
     m->nn = 1;
@@ -423,6 +424,46 @@ static void speeds_axis(int system, double g, const double *u, const double *P, 
 
 /* Numerical flux along +e_a between lower state L and upper state R (Sec. 3.2):
  * LLF (eq:LLF) or HLL with Davis speeds (eq:HLL). */
+/* Roe flux for the Newtonian ideal gas (Sec. 3.2.3, eq:Roe): half the sum of the
+ * physical fluxes minus half of sum_i alpha_i |lambda_i| e_i, with the flux
+ * Jacobian along e_a evaluated at the Roe averages (eq:RoeAverages) of the
+ * velocity and of the specific enthalpy h = (E + p)/rho.  Its eigenvalues are
+ * u_n - c, u_n (three times), u_n + c with c^2 = (g-1)(h - |v|^2/2); the wave
+ * strengths alpha_i are the jump U_R - U_L on the left eigenvectors, written in
+ * the frame (normal, t1, t2) = (a, a+1, a+2). */
+static void roe_flux(double g, int a, const double *uL, const double *PL, const double *uR, const double *PR,
+                     const double *FL, const double *FR, double *Fs)
+{
+    const double sl = sqrt(uL[0]), sr = sqrt(uR[0]);
+    const double wsum = sl + sr;
+    double vh[3];
+    for (int i = 0; i < 3; ++i) vh[i] = (sl * PL[i] + sr * PR[i]) / wsum;
+    const double hL = (uL[4] + PL[3]) / uL[0], hR = (uR[4] + PR[3]) / uR[0];
+    const double hh = (sl * hL + sr * hR) / wsum;
+    const double q2 = vh[0] * vh[0] + vh[1] * vh[1] + vh[2] * vh[2];
+    const double c2 = (g - 1.0) * (hh - 0.5 * q2);
+    const double c = sqrt(c2);
+    const int b = (a + 1) % 3, d = (a + 2) % 3;
+    const double un = vh[a], ut1 = vh[b], ut2 = vh[d];
+    const double j1 = uR[0] - uL[0], jn = uR[1 + a] - uL[1 + a];
+    const double jt1 = uR[1 + b] - uL[1 + b], jt2 = uR[1 + d] - uL[1 + d], j5 = uR[4] - uL[4];
+    const double al3 = jt1 - ut1 * j1;
+    const double al4 = jt2 - ut2 * j1;
+    const double j5b = j5 - al3 * ut1 - al4 * ut2;
+    const double al2 = (g - 1.0) / c2 * (j1 * (hh - un * un) + un * jn - j5b);
+    const double al1 = (j1 * (un + c) - jn - c * al2) / (2.0 * c);
+    const double al5 = j1 - (al1 + al2);
+    const double w1 = fabs(un - c) * al1, w2 = fabs(un) * al2, w5 = fabs(un + c) * al5;
+    const double w3 = fabs(un) * al3, w4 = fabs(un) * al4;
+    double D[5];
+    D[0] = w1 + w2 + w5;
+    D[1 + a] = w1 * (un - c) + w2 * un + w5 * (un + c);
+    D[1 + b] = (w1 + w2 + w5) * ut1 + w3;
+    D[1 + d] = (w1 + w2 + w5) * ut2 + w4;
+    D[4] = w1 * (hh - un * c) + w2 * (0.5 * q2) + w3 * ut1 + w4 * ut2 + w5 * (hh + un * c);
+    for (int v = 0; v < 5; ++v) Fs[v] = 0.5 * (FL[v] + FR[v]) - 0.5 * D[v];
+}
+
 static void num_flux(const or_mesh *m, int a, const double *uL, const double *PL,
                      const double *uR, const double *PR, double *Fs, double *FL, double *FR)
 {
@@ -433,7 +474,9 @@ static void num_flux(const or_mesh *m, int a, const double *uL, const double *PL
     flux_axis(uR, PR, a, FR);
     speeds_axis(sys, g, uL, PL, a, &lminL, &lmaxL);
     speeds_axis(sys, g, uR, PR, a, &lminR, &lmaxR);
-    if (m->d.flux == 0) {
+    if (m->d.flux == 2) {
+        roe_flux(g, a, uL, PL, uR, PR, FL, FR, Fs);
+    } else if (m->d.flux == 0) {
         /* alpha = largest |lambda| on either side */
         double al = fmax(fmax(fabs(lminL), fabs(lmaxL)), fmax(fabs(lminR), fabs(lmaxR)));
         for (int v = 0; v < 5; ++v)

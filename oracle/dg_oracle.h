@@ -30,7 +30,8 @@ typedef struct {
     int dim;         /* number of active axes, 1..3 */
     int K[3];        /* elements per axis (inactive axes: 1) */
     int n;           /* LGL nodes per active axis, 2..OR_MAXN */
-    int flux;        /* 0 local Lax-Friedrichs (eq:LLF), 1 HLL with Davis speeds (eq:HLL) */
+    int flux;        /* 0 local Lax-Friedrichs (eq:LLF), 1 HLL with Davis speeds (eq:HLL),
+                        2 Roe (eq:Roe, Newtonian only) */
     int limiter;     /* 0 none, 1 generalized minmodB troubled-cell limiter ("MinModN"), 2 plain minmod ("MinMod") */
     double gamma;    /* ideal-gas adiabatic index */
     double lo[3];    /* periodic box */
@@ -68,7 +69,7 @@ long long or_con2prim(long long count, double gamma, const double *cons, double 
 /* Mesh-layout primitive recovery: P[e][0..3][node] = (vx, vy, vz, p).  Returns failures. */
 long long or_primitives(const or_mesh *m, const double *U, double *P);
 
-/* Point-wise numerical flux along +e_axis (LLF or HLL) for tests. */
+/* Point-wise numerical flux along +e_axis (LLF, HLL or Roe) for tests. */
 int or_num_flux(int system, double gamma, int flux, int axis, const double *uL, const double *uR,
                 double *Fs, double *FL, double *FR, double *speeds);
 /* Semi-discrete right-hand side, eq:411.  Returns number of con2prim failures. */

@@ -83,8 +83,8 @@ def test_c2p_rejects_unphysical():
     assert list(st) == [1, 1, 1]  # D <= 0; tau <= 0; S^2 >= tau (tau + 2 D)
 
 
-@pytest.mark.parametrize("system,gamma", [(0, 1.4), (1, 4.0 / 3.0)])
-@pytest.mark.parametrize("flux", [0, 1])
+@pytest.mark.parametrize("system,gamma,flux", [(0, 1.4, 0), (0, 1.4, 1), (0, 1.4, 2), (1, 4.0 / 3.0, 0),
+                                               (1, 4.0 / 3.0, 1)])
 @pytest.mark.parametrize("axis", [0, 1, 2])
 def test_flux_consistency(system, gamma, flux, axis):
     # F*(U, U) = F(U) (Sec. 3.2)
@@ -149,3 +149,70 @@ def test_sr_speeds_limits():
     u = oracle.prim2con(1, g, np.array([[rho], [v], [0.0], [0.0], [p]]))[:, 0]
     _, _, _, sp = oracle.num_flux(1, g, 1, 0, u, u)
     assert np.allclose(sp[:2], [(v - cs) / (1 - v * cs), (v + cs) / (1 + v * cs)], rtol=1e-13)
+
+
+def _euler_jacobian(g, vel, H, axis):
+    """Analytic flux Jacobian dF^axis/dU of the 3D Euler equations (ideal gas) at
+    velocity vel and specific enthalpy H (textbook form, written out here)."""
+    q2 = vel @ vel
+    un = vel[axis]
+    A = np.zeros((5, 5))
+    A[0, 1 + axis] = 1.0
+    for i in range(3):
+        A[1 + i, 0] = -vel[i] * un
+        A[1 + i, 1 + i] += un
+        A[1 + i, 1 + axis] += vel[i]
+    A[1 + axis, 0] += 0.5 * (g - 1.0) * q2
+    for j in range(3):
+        A[1 + axis, 1 + j] -= (g - 1.0) * vel[j]
+    A[1 + axis, 4] = g - 1.0
+    A[4, 0] = un * (0.5 * (g - 1.0) * q2 - H)
+    for j in range(3):
+        A[4, 1 + j] = -(g - 1.0) * un * vel[j]
+    A[4, 1 + axis] += H
+    A[4, 4] = g * un
+    return A
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_roe_flux_matches_eigendecomposition(axis):
+    """eq:Roe for the ideal gas equals 1/2 (F_L + F_R) - 1/2 |A| (U_R - U_L) with A
+    the analytic Jacobian at the Roe averages (eq:RoeAverages) and |A| formed
+    from a numerical eigendecomposition; and A (U_R - U_L) = F_R - F_L (Roe's
+    conservation condition)."""
+    g = 1.4
+    pl = np.array([[1.0], [0.75], [0.1], [-0.2], [1.0]])
+    pr = np.array([[0.125], [0.05], [0.3], [0.05], [0.1]])
+    uL = oracle.prim2con(0, g, pl)[:, 0]
+    uR = oracle.prim2con(0, g, pr)[:, 0]
+    Fs, FL, FR, _ = oracle.num_flux(0, g, 2, axis, uL, uR)
+    sl, sr = math.sqrt(pl[0, 0]), math.sqrt(pr[0, 0])
+    vel = (sl * pl[1:4, 0] + sr * pr[1:4, 0]) / (sl + sr)
+    hL = (uL[4] + pl[4, 0]) / pl[0, 0]
+    hR = (uR[4] + pr[4, 0]) / pr[0, 0]
+    H = (sl * hL + sr * hR) / (sl + sr)
+    A = _euler_jacobian(g, vel, H, axis)
+    assert np.allclose(A @ (uR - uL), FR - FL, rtol=1e-13, atol=1e-13)
+    lam, R = np.linalg.eig(A)
+    absA = (R * np.abs(lam.real)) @ np.linalg.inv(R)
+    ref = 0.5 * (FL + FR) - 0.5 * absA.real @ (uR - uL)
+    assert np.allclose(Fs, ref, rtol=1e-12, atol=1e-13), (Fs, ref)
+
+
+def test_roe_upwinds_supersonic_flow():
+    """All Roe eigenvalues of one sign: eq:Roe is the upwind flux."""
+    g = 1.4
+    pl = np.array([[1.0], [3.0], [0.2], [0.0], [0.1]])
+    pr = np.array([[0.5], [2.8], [-0.1], [0.1], [0.05]])
+    uL = oracle.prim2con(0, g, pl)[:, 0]
+    uR = oracle.prim2con(0, g, pr)[:, 0]
+    Fs, FL, FR, _ = oracle.num_flux(0, g, 2, 0, uL, uR)
+    assert np.allclose(Fs, FL, rtol=1e-13, atol=1e-14)
+    flip = np.array([1, -1, 1, 1, 1])
+    Fs2, FL2, FR2, _ = oracle.num_flux(0, g, 2, 0, uR * flip, uL * flip)
+    assert np.allclose(Fs2, FR2, rtol=1e-13, atol=1e-14)
+
+
+def test_roe_is_newtonian_only():
+    with pytest.raises(Exception):
+        oracle.Mesh(oracle.MeshSpec(system=1, K=(2, 2, 2), n=3, flux=2, gamma=4.0 / 3.0))

@@ -170,6 +170,20 @@ def test_ne_sod_table_loose():
         assert 0.75 < o < 1.25, (errs, o)
 
 
+def test_ne_sod_table_roe_loose():
+    """tab:NE_sod, Roe-MinMod-2 and Roe-MinModN-3 (Sec. 3.2.3 flux): first-order
+    convergence and errors within the band of the HLL pin."""
+    rows = read_golden("ne_sod_roe.txt")
+    for n, limiter in ((2, 2), (3, 1)):
+        sel = [(int(nx), ref) for nn, lim, nx, ref in rows if (nn, lim) == (n, limiter)]
+        errs = [_sod_error(nx, n=n, flux=2, limiter=limiter) for nx, _ in sel]
+        for (nx, ref), e in zip(sel, errs):
+            assert 0.6 * ref < e < 1.2 * ref, (n, limiter, nx, e, ref)
+        for i in range(len(errs) - 1):
+            o = math.log2(errs[i] / errs[i + 1])
+            assert 0.75 < o < 1.25, (n, limiter, errs, o)
+
+
 def test_blast_amplifies_rounding():
     """Characterises the SR blast with the MinModN limiter: a 1-ulp random
     perturbation of the initial state grows to ~1e-12 relative in 10 steps, so
