@@ -44,7 +44,7 @@ typedef enum {
 } dg_status;
 
 enum { DG_SYSTEM_NEWTONIAN = 0, DG_SYSTEM_SR = 1 };
-enum { DG_FLUX_LLF = 0, DG_FLUX_HLL = 1 };
+enum { DG_FLUX_LLF = 0, DG_FLUX_HLL = 1, DG_FLUX_ROE = 2 };
 enum { DG_LIMITER_NONE = 0, DG_LIMITER_MINMODN = 1, DG_LIMITER_MINMOD = 2 };
 enum { DG_PRECISION_FP64 = 0, DG_PRECISION_MIXED = 1 };
 
@@ -52,7 +52,7 @@ typedef struct {
     int system;      /* DG_SYSTEM_*: Newtonian Euler (Sec. 2.1.1) or flat-space SR hydro (Sec. 2.1.2) */
     int K[3];        /* elements per axis, >= 1 */
     int n;           /* LGL nodes per axis, 2..8 (degree N = n-1) */
-    int flux;        /* DG_FLUX_*: eq:LLF or eq:HLL with Davis speeds */
+    int flux;        /* DG_FLUX_*: eq:LLF, eq:HLL with Davis speeds, or eq:Roe (Newtonian only) */
     int limiter;     /* DG_LIMITER_*: none, generalized minmodB detector + limiter (Sec. 3.3.2), plain minmod (Sec. 3.3.1) */
     int precision;   /* DG_PRECISION_* */
     double gamma;    /* ideal-gas adiabatic index, > 1 */

@@ -452,7 +452,8 @@ dg_status dg_mesh_create(const dg_mesh_desc *d, dg_mesh **out)
     *out = nullptr;
     if (d->system != 0 && d->system != 1) return fail(DG_ERR_ARG, "system must be 0 or 1");
     if (d->n < 2 || d->n > MAXN) return fail(DG_ERR_ARG, "n must be in 2..%d", MAXN);
-    if (d->flux != 0 && d->flux != 1) return fail(DG_ERR_ARG, "flux must be 0 (LLF) or 1 (HLL)");
+    if (d->flux != 0 && d->flux != 1 && !(d->flux == 2 && d->system == 0))
+        return fail(DG_ERR_ARG, "flux must be 0 (LLF), 1 (HLL) or, for the Newtonian system, 2 (Roe)");
     if (d->limiter < 0 || d->limiter > 2) return fail(DG_ERR_ARG, "limiter must be 0, 1 or 2");
     if (d->precision != 0 && d->precision != 1) return fail(DG_ERR_ARG, "precision must be 0 (FP64) or 1 (mixed)");
     if (!(d->gamma > 1.0)) return fail(DG_ERR_ARG, "gamma must be > 1");

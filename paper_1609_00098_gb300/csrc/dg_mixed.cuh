@@ -140,6 +140,46 @@ __device__ __forceinline__ void num_flux_jump32(float g, int a, const float uL[5
     float FL[5], FR[5], lminL, lmaxL, lminR, lmaxR;
     flux_axis32(uL, PL, a, FL);
     flux_axis32(uR, PR, a, FR);
+    if (FLX == 2) {
+        // Roe (eq:Roe, Newtonian): F* - F_L = dF/2 - D/2, F* - F_R = -dF/2 - D/2,
+        // with the dissipation D = sum_i alpha_i |lambda_i| e_i at the Roe averages;
+        // the wave strengths come from the jump, so equal states give D = 0.
+        const float sl = sqrtf(uL[0]), sr = sqrtf(uR[0]);
+        const float inv = 1.0f / (sl + sr);
+        float vh[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) vh[i] = (sl * PL[i] + sr * PR[i]) * inv;
+        const float hL = (uL[4] + PL[3]) / uL[0], hR = (uR[4] + PR[3]) / uR[0];
+        const float hh = (sl * hL + sr * hR) * inv;
+        const float q2 = vh[0] * vh[0] + vh[1] * vh[1] + vh[2] * vh[2];
+        const float c2 = (g - 1.0f) * (hh - 0.5f * q2);
+        const float c = sqrtf(c2);
+        const int b = a == 0 ? 1 : (a == 1 ? 2 : 0), d = a == 0 ? 2 : (a == 1 ? 0 : 1);
+        const float un = vh[a], ut1 = vh[b], ut2 = vh[d];
+        const float j1 = uR[0] - uL[0], jn = uR[1 + a] - uL[1 + a];
+        const float jt1 = uR[1 + b] - uL[1 + b], jt2 = uR[1 + d] - uL[1 + d], j5 = uR[4] - uL[4];
+        const float al3 = jt1 - ut1 * j1;
+        const float al4 = jt2 - ut2 * j1;
+        const float j5b = j5 - al3 * ut1 - al4 * ut2;
+        const float al2 = (g - 1.0f) / c2 * (j1 * (hh - un * un) + un * jn - j5b);
+        const float al1 = (j1 * (un + c) - jn - c * al2) / (2.0f * c);
+        const float al5 = j1 - (al1 + al2);
+        const float w1 = fabsf(un - c) * al1, w2 = fabsf(un) * al2, w5 = fabsf(un + c) * al5;
+        const float w3 = fabsf(un) * al3, w4 = fabsf(un) * al4;
+        float D[5];
+        D[0] = w1 + w2 + w5;
+        D[1 + a] = w1 * (un - c) + w2 * un + w5 * (un + c);
+        D[1 + b] = (w1 + w2 + w5) * ut1 + w3;
+        D[1 + d] = (w1 + w2 + w5) * ut2 + w4;
+        D[4] = w1 * (hh - un * c) + w2 * (0.5f * q2) + w3 * ut1 + w4 * ut2 + w5 * (hh + un * c);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+            const float dF = FR[v] - FL[v];
+            dL[v] = 0.5f * dF - 0.5f * D[v];
+            dR[v] = -0.5f * dF - 0.5f * D[v];
+        }
+        return;
+    }
     speeds_axis32<SYS>(g, uL, PL, a, lminL, lmaxL);
     speeds_axis32<SYS>(g, uR, PR, a, lminR, lmaxR);
     if (FLX == 0) {
@@ -942,7 +982,8 @@ cudaError_t launch_stage_mixed_np(int system, int flux, const MixedArgs &a, cuda
     const bool learned = system == 1 && a.netP != nullptr;
     const size_t smem = MixedSmem<NP>::total(a.epb, learned);
     void (*kern)(const MixedArgs);
-    if (system == 0 && flux == 0) kern = k_stage_mixed<NP, 0, 0, 0>;
+    if (system == 0 && flux == 2) kern = k_stage_mixed<NP, 0, 2, 0>;
+    else if (system == 0 && flux == 0) kern = k_stage_mixed<NP, 0, 0, 0>;
     else if (system == 0) kern = k_stage_mixed<NP, 0, 1, 0>;
     else if (flux == 0) kern = learned ? k_stage_mixed<NP, 1, 0, 1> : k_stage_mixed<NP, 1, 0, 0>;
     else kern = learned ? k_stage_mixed<NP, 1, 1, 1> : k_stage_mixed<NP, 1, 1, 0>;

@@ -162,6 +162,43 @@ __device__ __forceinline__ void speeds_axis(double g, const double u[5], const d
 
 // Numerical flux along +e_a between the lower state L and the upper state R:
 // FLX = 0 local Lax-Friedrichs (eq:LLF), 1 HLL with Davis speeds (eq:HLL).
+// Roe dissipation D = sum_i alpha_i |lambda_i| e_i of eq:Roe for the Newtonian
+// ideal gas (Sec. 3.2.3): the flux Jacobian along e_a at the Roe averages
+// (eq:RoeAverages) of the velocity and of h = (E + p)/rho, eigenvalues u_n - c,
+// u_n (x3), u_n + c with c^2 = (g-1)(h - |v|^2/2), wave strengths from the jump on
+// the left eigenvectors in the frame (normal, t1, t2) = (a, a+1, a+2).
+__device__ __forceinline__ void roe_dissipation(double g, int a, const double uL[5], const double PL[4],
+                                                const double uR[5], const double PR[4], double D[5])
+{
+    const double sl = sqrt(uL[0]), sr = sqrt(uR[0]);
+    const double wsum = sl + sr;
+    double vh[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) vh[i] = (sl * PL[i] + sr * PR[i]) / wsum;
+    const double hL = (uL[4] + PL[3]) / uL[0], hR = (uR[4] + PR[3]) / uR[0];
+    const double hh = (sl * hL + sr * hR) / wsum;
+    const double q2 = vh[0] * vh[0] + vh[1] * vh[1] + vh[2] * vh[2];
+    const double c2 = (g - 1.0) * (hh - 0.5 * q2);
+    const double c = sqrt(c2);
+    const int b = (a + 1) % 3, d = (a + 2) % 3;
+    const double un = vh[a], ut1 = vh[b], ut2 = vh[d];
+    const double j1 = uR[0] - uL[0], jn = uR[1 + a] - uL[1 + a];
+    const double jt1 = uR[1 + b] - uL[1 + b], jt2 = uR[1 + d] - uL[1 + d], j5 = uR[4] - uL[4];
+    const double al3 = jt1 - ut1 * j1;
+    const double al4 = jt2 - ut2 * j1;
+    const double j5b = j5 - al3 * ut1 - al4 * ut2;
+    const double al2 = (g - 1.0) / c2 * (j1 * (hh - un * un) + un * jn - j5b);
+    const double al1 = (j1 * (un + c) - jn - c * al2) / (2.0 * c);
+    const double al5 = j1 - (al1 + al2);
+    const double w1 = fabs(un - c) * al1, w2 = fabs(un) * al2, w5 = fabs(un + c) * al5;
+    const double w3 = fabs(un) * al3, w4 = fabs(un) * al4;
+    D[0] = w1 + w2 + w5;
+    D[1 + a] = w1 * (un - c) + w2 * un + w5 * (un + c);
+    D[1 + b] = (w1 + w2 + w5) * ut1 + w3;
+    D[1 + d] = (w1 + w2 + w5) * ut2 + w4;
+    D[4] = w1 * (hh - un * c) + w2 * (0.5 * q2) + w3 * ut1 + w4 * ut2 + w5 * (hh + un * c);
+}
+
 template <int SYS, int FLX>
 __device__ __forceinline__ void num_flux(double g, int a, const double uL[5], const double PL[4],
                                          const double uR[5], const double PR[4], double Fs[5],
@@ -170,6 +207,13 @@ __device__ __forceinline__ void num_flux(double g, int a, const double uL[5], co
     double lminL, lmaxL, lminR, lmaxR;
     flux_axis(uL, PL, a, FL);
     flux_axis(uR, PR, a, FR);
+    if (FLX == 2) {  // Roe (Newtonian only)
+        double D[5];
+        roe_dissipation(g, a, uL, PL, uR, PR, D);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) Fs[v] = 0.5 * (FL[v] + FR[v]) - 0.5 * D[v];
+        return;
+    }
     speeds_axis<SYS>(g, uL, PL, a, lminL, lmaxL);
     speeds_axis<SYS>(g, uR, PR, a, lminR, lmaxR);
     if (FLX == 0) {

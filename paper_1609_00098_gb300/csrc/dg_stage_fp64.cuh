@@ -279,7 +279,8 @@ cudaError_t launch_stage_np(int system, int flux, const StageArgs &a, long long 
     const dim3 grid((unsigned)E), block(round_up32(NP * NP * NP));
     const size_t smem = sizeof(double) * 20 * NP * NP * NP;
     void (*kern)(const StageArgs);
-    if (system == 0 && flux == 0) kern = k_stage_fp64<NP, 0, 0>;
+    if (system == 0 && flux == 2) kern = k_stage_fp64<NP, 0, 2>;
+    else if (system == 0 && flux == 0) kern = k_stage_fp64<NP, 0, 0>;
     else if (system == 0) kern = k_stage_fp64<NP, 0, 1>;
     else if (flux == 0) kern = k_stage_fp64<NP, 1, 0>;
     else kern = k_stage_fp64<NP, 1, 1>;

@@ -215,3 +215,21 @@ def test_elements_per_cta_do_not_change_results(pkg, n, epb):
         assert np.array_equal(out[0], out[1])
     finally:
         pkg.abi.dg_c2p_net_destroy(net)
+
+
+def test_mixed_roe(pkg):
+    """Roe flux on the mixed path: RHS to FP32 rounding of the oracle's, and ten
+    shear-layer steps within the 1e-6 bar."""
+    om, gm = _pair(pkg, 0, (4, 4, 4), 5, 2, 1, lo=(-0.5,) * 3, hi=(0.5,) * 3, gamma=5 / 3)
+    U = om.from_prim(di.kh_ne(om.coords(), seed=3))
+    Ro = om.rhs(U)
+    err = np.abs(gm.rhs(_gpu(U)).cpu().numpy() - Ro).max(axis=(0, 2)) / _scale(Ro)
+    assert err.max() < 5e-4, err  # the FP32 level of test_mixed_rhs_close_to_oracle
+    Ug = _gpu(U)
+    for _ in range(10):
+        h = om.cfl_dt(U, 0.2)
+        U = om.rk3_step(U, h)
+        gm.rk3_step(Ug, dt=h)
+    assert gm.sync_status() == 0
+    d = _rel_l2(om, Ug.cpu().numpy(), U)
+    assert np.all(d <= 1e-6), d

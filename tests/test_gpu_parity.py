@@ -312,3 +312,28 @@ def test_full_size_kh_one_step(pkg):
     sc = np.abs(Uo).max()
     d = np.abs(Um.cpu().numpy() - Uo).max(axis=(0, 2)) / sc
     assert d.max() < 2e-6, d
+
+
+@pytest.mark.parametrize("n,limiter", [(2, 2), (4, 1), (6, 0)])
+def test_roe_fp64_bitwise(pkg, n, limiter):
+    """Roe flux (Sec. 3.2.3) on the FP64 path: RHS and three CFL steps of the
+    shear layer bitwise equal to the oracle."""
+    import torch
+    kw = dict(system=0, K=(3, 2, 2), n=n, flux=2, limiter=limiter, gamma=5.0 / 3.0, lo=(-0.5,) * 3, hi=(0.5,) * 3)
+    om, gm = _pair(pkg, **kw)
+    U = _init(om, "kh", seed=2)
+    assert np.array_equal(gm.rhs(_gpu(U)).cpu().numpy(), om.rhs(U))
+    Ug = _gpu(U)
+    dt = torch.zeros(1, dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        h = om.cfl_dt(U, 0.2)
+        U = om.rk3_step(U, h)
+        gm.rk3_step(Ug, cfl=0.2, dt_used=dt)
+        assert dt.item() == h
+    assert gm.sync_status() == 0
+    assert np.array_equal(Ug.cpu().numpy(), U)
+
+
+def test_roe_rejected_for_sr(pkg):
+    with pytest.raises(pkg.abi.DGError):
+        pkg.Mesh(system=1, K=(2, 2, 2), n=3, flux=2, gamma=4.0 / 3.0)
