@@ -310,6 +310,28 @@ class Mesh:
             t += h
         return U, t
 
+    def ab3_run(self, U, steps: int, dt: float):
+        """Third-order Adams-Bashforth with a fixed dt (Sec. 3.4, the paper's other
+        third-order integrator):
+            U^{n+1} = U^n + dt (23/12 L^n - 16/12 L^{n-1} + 5/12 L^{n-2}),
+        followed by the limiter and (SR) the conserved fix, as after an SSP-RK3
+        stage.  The two right-hand sides missing at the start come from two
+        SSP-RK3 steps, each recording L(U) of the state it starts from."""
+        U = _f64(U).copy()
+        hist = []
+        for _ in range(steps):
+            L = self.rhs(U)
+            if len(hist) < 2:
+                hist.append(L)
+                U = self.rk3_step(U, dt)
+                continue
+            U = U + dt * ((23.0 / 12.0 * L - 16.0 / 12.0 * hist[-1]) + 5.0 / 12.0 * hist[-2])
+            hist = [hist[-1], L]
+            U, _ = self.limit(U)
+            if self.spec.system == 1:
+                U, _ = self.fix(U)
+        return U
+
     def norms(self, U, V):
         l1 = np.zeros(5)
         l2 = np.zeros(5)

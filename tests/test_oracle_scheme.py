@@ -199,3 +199,32 @@ def test_blast_amplifies_rounding():
         V = m.rk3_step(V, h)
     rel = np.abs(U - V).max(axis=(0, 2)) / np.abs(U).max(axis=(0, 2))
     assert 3e-13 < rel.max() < 1e-10, rel
+
+
+def test_ab3_temporal_order():
+    """The Adams-Bashforth stepper (Sec. 3.4) is third order in time: halving the
+    fixed dt at a spatially converged mesh divides the error by ~8."""
+    spec = oracle.MeshSpec(system=0, dim=1, K=(2, 1, 1), n=6, flux=0, gamma=1.4)
+    m = oracle.Mesh(spec)
+    U0 = m.from_prim(di.smooth_wave_ne(m.coords(), 0.0, k=(1, 1, 1), vel=(1.0, 0.0, 0.0)))
+    T = 0.4
+    ref, _ = m.run(U0, 1600, dt=T / 1600)
+    e = []
+    for nsteps in (100, 200, 400):
+        U = m.ab3_run(U0, nsteps, T / nsteps)
+        e.append(np.abs(U - ref).max())
+    o1, o2 = math.log2(e[0] / e[1]), math.log2(e[1] / e[2])
+    assert 2.7 < o1 < 3.4 and 2.7 < o2 < 3.4, (e, o1, o2)
+
+
+def test_ab3_conserves_and_matches_rk3_start():
+    """AB3's first two steps are SSP-RK3 steps; later steps keep the totals."""
+    spec = oracle.MeshSpec(system=1, K=(3, 3, 3), n=4, flux=1, limiter=1, gamma=4 / 3)
+    m = oracle.Mesh(spec)
+    U = m.from_prim(di.blast_sr(m.coords(), seed=1))
+    dt = 0.5 * m.cfl_dt(U, 0.2)
+    assert np.array_equal(m.ab3_run(U, 2, dt), m.run(U, 2, dt=dt)[0])
+    t0 = m.totals(U)
+    U5 = m.ab3_run(U, 5, dt)
+    drift = np.abs(m.totals(U5) - t0) / np.abs(t0).max()
+    assert np.all(drift < 1e-13), drift
