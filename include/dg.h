@@ -120,6 +120,21 @@ dg_status dg_rk3_step(dg_mesh *mesh, double *U, double dt, double cfl, double *d
 dg_status dg_limit(dg_mesh *mesh, double *U, unsigned char *troubled, void *stream);
 /* SR conserved-variable fix alone, in place (Sec. 2.1.4); no-op for Newtonian meshes. */
 dg_status dg_fix(dg_mesh *mesh, double *U, void *stream);
+/* Third-order Adams-Bashforth step (Sec. 3.4, the paper's other third-order
+ * integrator) with a fixed dt:
+ *   U^{n+1} = U^n + dt (23/12 L^n - 16/12 L^{n-1} + 5/12 L^{n-2}),
+ * then the limiter and (SR) the conserved fix, as after an SSP-RK3 stage.  The
+ * mesh keeps the last three right-hand sides (library scratch, allocated on the
+ * first call); the first two steps after mesh creation or dg_ab3_reset are
+ * SSP-RK3 steps that record L(U) of the state they start from.  FP64 meshes
+ * give the oracle's bits; mixed meshes evaluate L in mixed precision and
+ * combine in FP64.  troubled (device, one byte per element, may be NULL) gets the
+ * limiter's mask.  Errors: DG_ERR_ARG for dt <= 0 or a dt different from the
+ * previous step's without a reset; DG_ERR_NOMEM/CUDA if the history cannot be
+ * allocated. */
+dg_status dg_ab3_step(dg_mesh *mesh, double *U, double dt, unsigned char *troubled, void *stream);
+dg_status dg_ab3_reset(dg_mesh *mesh);
+
 /* Limiter summaries S[e][v][10] = (cell mean, face means lo/hi for x, y, z,
  * Legendre P1 coefficients along x, y, z) of U. */
 dg_status dg_limiter_summaries(dg_mesh *mesh, const double *U, double *S, void *stream);

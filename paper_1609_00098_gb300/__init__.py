@@ -94,6 +94,14 @@ class Mesh:
     def sync_status(self) -> int:
         return abi.dg_sync_status(self.h)
 
+    def ab3_step(self, U, dt, troubled=None):
+        """Third-order Adams-Bashforth step with a fixed dt (two SSP-RK3 start-up steps)."""
+        abi.dg_ab3_step(self.h, U, dt, troubled)
+        return U
+
+    def ab3_reset(self):
+        abi.dg_ab3_reset(self.h)
+
     def set_option(self, option, value):
         """Mixed-path option: abi.OPT_TENSOR_CORE_CONTRACTION or abi.OPT_C2P_KAPPA_SWITCH."""
         abi.dg_mesh_set_option(self.h, option, value)

@@ -68,6 +68,8 @@ SIGNATURES = {
     "dg_sync_status": (_i, [_vp, _vp]),
     "dg_mesh_set_c2p_net": (_i, [_vp, _vp]),
     "dg_mesh_set_option": (_i, [_vp, _i, _d]),
+    "dg_ab3_step": (_i, [_vp, _vp, _d, _vp, _vp]),
+    "dg_ab3_reset": (_i, [_vp]),
     "dg_ensemble_create": (_i, [_vp, _vp, _i, ctypes.POINTER(_vp)]),
     "dg_ensemble_destroy": (None, [_vp]),
     "dg_ensemble_tune": (_i, [_vp, _vp]),
@@ -328,6 +330,16 @@ OPT_ELEMENTS_PER_CTA = 3
 def dg_mesh_set_option(mesh, option, value):
     """Set a mixed-path option (OPT_TENSOR_CORE_CONTRACTION, OPT_C2P_KAPPA_SWITCH)."""
     _check(load().dg_mesh_set_option(mesh, int(option), float(value)))
+
+
+def dg_ab3_step(mesh, U, dt, troubled=None, stream=None):
+    import torch
+    _check(load().dg_ab3_step(mesh, _ptr(U, None, torch.float64, "U"), float(dt),
+                              _ptr(troubled, None, torch.uint8, "troubled"), _stream(stream)))
+
+
+def dg_ab3_reset(mesh):
+    _check(load().dg_ab3_reset(mesh))
 
 
 def dg_mesh_set_c2p_net(mesh, net):

@@ -432,6 +432,7 @@ void free_scratch(dg_mesh *m)
     cudaFree(m->W2);
     cudaFree(m->pbuf[0]);
     cudaFree(m->pbuf[1]);
+    for (int i = 0; i < 3; ++i) cudaFree(m->abL[i]);
     cudaFree(m->P);
     cudaFree(m->S);
     cudaFree(m->unphys);
@@ -703,6 +704,41 @@ dg_status dg_rk3_step(dg_mesh *m, double *U, double dt, double cfl, double *dt_u
         if (cflmode) DG_CUDA(cudaMemcpyAsync(dt_used, m->dt, sizeof(double), cudaMemcpyDeviceToDevice, s));
         else DG_CUDA(launch_set(dt_used, dt, s));
     }
+    return DG_OK;
+}
+
+dg_status dg_ab3_reset(dg_mesh *m)
+{
+    if (dg_status s = check_mesh(m)) return s;
+    m->ab_n = 0;
+    return DG_OK;
+}
+
+dg_status dg_ab3_step(dg_mesh *m, double *U, double dt, unsigned char *troubled, void *stream)
+{
+    if (dg_status s = check_mesh(m)) return s;
+    if (!U) return fail(DG_ERR_ARG, "U is NULL");
+    if (!(dt > 0.0)) return fail(DG_ERR_ARG, "need dt > 0");
+    if (m->ab_n > 0 && dt != m->ab_dt)
+        return fail(DG_ERR_ARG, "Adams-Bashforth needs a fixed dt: call dg_ab3_reset before changing it");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t state = sizeof(double) * (size_t)m->E * 5 * m->nn;
+    for (int i = 0; i < 3; ++i)
+        if (!m->abL[i]) DG_CUDA(cudaMalloc(&m->abL[i], state));
+    double *Ln = m->abL[m->ab_n % 3];
+    if (dg_status st = dg_rhs(m, U, Ln, stream)) return st;
+    if (m->ab_n < 2) {
+        // start-up: SSP-RK3 steps record the right-hand sides AB3 needs
+        if (dg_status st = dg_rk3_step(m, U, dt, 0.0, nullptr, troubled, stream)) return st;
+    } else {
+        const double *L1 = m->abL[(m->ab_n - 1) % 3], *L2 = m->abL[(m->ab_n - 2) % 3];
+        DG_LAUNCH(m, s, PROF_OTHER, launch_ab3_combine(U, Ln, L1, L2, dt, m->E * 5 * m->nn, s));
+        if (dg_status st = dg_limit(m, U, troubled, stream)) return st;
+        if (m->d.system == 1)
+            if (dg_status st = dg_fix(m, U, stream)) return st;
+    }
+    m->ab_n += 1;
+    m->ab_dt = dt;
     return DG_OK;
 }
 

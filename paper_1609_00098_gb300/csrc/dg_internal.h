@@ -97,6 +97,11 @@ struct dg_mesh {
     const dg_c2p_net *net;   // attached learned-guess network (mixed SR path), or nullptr
     int tc_contract;         // mixed volume contraction on the tensor cores (split-BF16x3)
     int epb;                 // mixed stage kernel: elements per CTA
+    // Adams-Bashforth state (dg_ab3_step): the last three right-hand sides (ring),
+    // the steps taken since the last reset, and the fixed dt
+    double *abL[3];
+    long long ab_n;
+    double ab_dt;
     // optional per-kernel timing (dg_profile_enable)
     int prof_on;
     void *prof;              // host-side event log, owned by dg_api.cu
@@ -112,6 +117,8 @@ cudaError_t launch_limit(int n, const LimitArgs &a, cudaStream_t s);
 cudaError_t launch_primitives(const dg_mesh *m, const double *U, double *P, int fix, double *Ufix,
                               unsigned long long *lam, cudaStream_t s);
 cudaError_t launch_fix(const dg_mesh *m, double *U, cudaStream_t s);
+cudaError_t launch_ab3_combine(double *U, const double *L0, const double *L1, const double *L2, double dt,
+                               long long count, cudaStream_t s);
 cudaError_t launch_dt(const dg_mesh *m, double cfl, double *dt, cudaStream_t s);
 cudaError_t launch_coords(const dg_mesh *m, double *xyz, cudaStream_t s);
 cudaError_t launch_prim2con(const dg_mesh *m, const double *prim, double *U, cudaStream_t s);

@@ -91,6 +91,16 @@ __global__ void __launch_bounds__(kThreads) k_fix(double *U, long long total, in
     }
 }
 
+// U <- U + dt ((c0 L0 - c1 L1) + c2 L2), the third-order Adams-Bashforth
+// combination (Sec. 3.4) with c = (23, 16, 5)/12, in the oracle's operation order.
+__global__ void __launch_bounds__(kThreads) k_ab3(double *U, const double *L0, const double *L1, const double *L2,
+                                                  double dt, double c0, double c1, double c2, long long count)
+{
+    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < count;
+         g += (long long)gridDim.x * blockDim.x)
+        U[g] = U[g] + dt * ((c0 * L0[g] - c1 * L1[g]) + c2 * L2[g]);
+}
+
 __global__ void k_dt(const unsigned long long *lam, double cfl, double dxmin, double *dt)
 {
     const double l = __longlong_as_double((long long)*lam);
@@ -204,6 +214,14 @@ cudaError_t launch_fix(const dg_mesh *m, double *U, cudaStream_t s)
 {
     const long long total = m->E * m->nn;
     k_fix<<<grid_for(total, kThreads), kThreads, 0, s>>>(U, total, m->nn, m->d.d_atm, m->d.tau_atm);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ab3_combine(double *U, const double *L0, const double *L1, const double *L2, double dt,
+                               long long count, cudaStream_t s)
+{
+    k_ab3<<<grid_for(count, kThreads), kThreads, 0, s>>>(U, L0, L1, L2, dt, 23.0 / 12.0, 16.0 / 12.0, 5.0 / 12.0,
+                                                         count);
     return cudaGetLastError();
 }
 

@@ -233,3 +233,18 @@ def test_mixed_roe(pkg):
     assert gm.sync_status() == 0
     d = _rel_l2(om, Ug.cpu().numpy(), U)
     assert np.all(d <= 1e-6), d
+
+
+def test_mixed_ab3(pkg):
+    """Adams-Bashforth on a mixed mesh (mixed right-hand side, FP64 combination):
+    ten blast steps within the 1e-6 bar of the oracle's AB3."""
+    om, gm = _pair(pkg, 1, (4, 3, 3), 5, 1, 1)
+    U = om.from_prim(di.blast_sr(om.coords(), seed=1))
+    dt = 0.5 * om.cfl_dt(U, 0.2)
+    Uo = om.ab3_run(U, 10, dt)
+    Ug = _gpu(U)
+    for _ in range(10):
+        gm.ab3_step(Ug, dt)
+    assert gm.sync_status() == 0
+    d = _rel_l2(om, Ug.cpu().numpy(), Uo)
+    assert np.all(d <= 1e-6), d

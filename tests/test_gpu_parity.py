@@ -337,3 +337,26 @@ def test_roe_fp64_bitwise(pkg, n, limiter):
 def test_roe_rejected_for_sr(pkg):
     with pytest.raises(pkg.abi.DGError):
         pkg.Mesh(system=1, K=(2, 2, 2), n=3, flux=2, gamma=4.0 / 3.0)
+
+
+@pytest.mark.parametrize("system,flux,limiter,n,kind", [(1, 1, 1, 4, "blast"), (0, 1, 0, 5, "kh"), (0, 2, 2, 3, "kh")])
+def test_ab3_fp64_bitwise(pkg, system, flux, limiter, n, kind):
+    """Adams-Bashforth (Sec. 3.4) on the FP64 path: six fixed-dt steps (two SSP-RK3
+    start-up steps, then AB3 with the limiter and the fix) give the oracle's bits."""
+    import torch
+    kw = dict(system=system, K=(3, 3, 2), n=n, flux=flux, limiter=limiter)
+    if kind == "kh":
+        kw.update(gamma=5.0 / 3.0, lo=(-0.5,) * 3, hi=(0.5,) * 3)
+    om, gm = _pair(pkg, **kw)
+    U = _init(om, kind, seed=2)
+    dt = 0.5 * om.cfl_dt(U, 0.2)
+    Uo = om.ab3_run(U, 6, dt)
+    Ug = _gpu(U)
+    for _ in range(6):
+        gm.ab3_step(Ug, dt)
+    assert gm.sync_status() == 0
+    assert np.array_equal(Ug.cpu().numpy(), Uo)
+    with pytest.raises(pkg.abi.DGError):
+        gm.ab3_step(Ug, 0.5 * dt)
+    gm.ab3_reset()
+    gm.ab3_step(Ug, 0.5 * dt)
