@@ -57,6 +57,7 @@ class Desc(ctypes.Structure):
         ("beta", ctypes.c_double),
         ("d_atm", ctypes.c_double),
         ("tau_atm", ctypes.c_double),
+        ("mrs_alpha", ctypes.c_double),
     ]
 
 
@@ -199,6 +200,7 @@ class MeshSpec:
     beta: float = 2.0
     d_atm: float = 1e-12
     tau_atm: float = 1e-14
+    mrs_alpha: float = 0.0
     extra: dict = field(default_factory=dict)
 
 
@@ -224,6 +226,7 @@ class Mesh:
         d.beta = spec.beta
         d.d_atm = spec.d_atm
         d.tau_atm = spec.tau_atm
+        d.mrs_alpha = spec.mrs_alpha
         self._d = d
         self.h = lib.or_mesh_create(ctypes.byref(d))
         if not self.h:

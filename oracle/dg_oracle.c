@@ -139,6 +139,8 @@ or_mesh *or_mesh_create(const or_desc *d)
 {
     if (d->dim < 1 || d->dim > 3 || d->n < 2 || d->n > OR_MAXN) return NULL;
     if (d->flux < 0 || d->flux > 2 || (d->flux == 2 && d->system != 0)) return NULL;  /* Roe: Newtonian only */
+    if (d->limiter < 0 || d->limiter > 3 || (d->limiter == 3 && (d->system != 0 || !(d->mrs_alpha >= 0.0))))
+        return NULL;  /* MRS: Newtonian only, alpha~ >= 0 */
     or_mesh *m = (or_mesh *)calloc(1, sizeof(or_mesh));
     m->d = *d;
     m->nn = 1;
@@ -728,12 +730,97 @@ static int unphysical_node(const double *u)
  *    (eq:MinModSol, eq:MinModB), U_a = 2 c1_a / dx_a;
  *  - MinMod: every variable of every element is replaced that way;
  *  - SR: an element with an unphysical node is limited in every variable. */
+/* Moment limiter of Moe, Rossmanith and Seal (Sec. 3.3.3, eq:MRSSol), Newtonian
+ * system, in the reading used here:
+ *   U -> U0 + Theta (U - U0) on the conserved variables, one Theta in [0, 1] per
+ *   element, found from the primitives w = (rho, vx, vy, vz, p):
+ *   w0      primitives of the LGL cell average U0 of the element;
+ *   we_max, we_min  max and min of w over the element's nodes;
+ *   M, m    max and min of the face neighbours' w0 (along the active axes),
+ *           widened to w0 + alpha~ h^{3/2} and w0 - alpha~ h^{3/2}, h the largest
+ *           element width;
+ *   Theta = min over the components of min(1, |(M - w0)/(we_max - w0)|,
+ *           |(m - w0)/(we_min - w0)|), a ratio counting 1 when its denominator is
+ *           at the rounding level of w0 (|d| <= 1e-12 |w0|: a component that is
+ *           constant over the element up to rounding says nothing).
+ * The element's cell average is kept exactly. */
+static long long limit_mrs(const or_mesh *m, double *U, unsigned char *troubled)
+{
+    const int nn = m->nn, dim = m->d.dim;
+    const long long E = m->E;
+    const double g = m->d.gamma;
+    double h = 0.0;
+    for (int a = 0; a < dim; ++a) h = fmax(h, m->dx[a]);
+    const double wid = m->d.mrs_alpha * h * sqrt(h);
+    /* per element: U0[5], w0[5], we_max[5], we_min[5] */
+    double *T = (double *)malloc(sizeof(double) * 20 * E);
+    double *S = (double *)malloc(sizeof(double) * 10 * 5 * E);
+    or_limiter_summaries(m, U, S);
+#pragma omp parallel for schedule(static)
+    for (long long e = 0; e < E; ++e) {
+        double *Te = T + 20 * e;
+        for (int v = 0; v < 5; ++v) Te[v] = S[(e * 5 + v) * 10];
+        double P0[4];
+        node_prim(0, g, Te, P0);
+        Te[5] = Te[0];
+        for (int c = 0; c < 4; ++c) Te[6 + c] = P0[c];
+        for (int c = 0; c < 5; ++c) {
+            Te[10 + c] = -INFINITY;
+            Te[15 + c] = INFINITY;
+        }
+        for (int q = 0; q < nn; ++q) {
+            double u[5], P[4];
+            for (int v = 0; v < 5; ++v) u[v] = U[(e * 5 + v) * nn + q];
+            node_prim(0, g, u, P);
+            const double w[5] = {u[0], P[0], P[1], P[2], P[3]};
+            for (int c = 0; c < 5; ++c) {
+                Te[10 + c] = fmax(Te[10 + c], w[c]);
+                Te[15 + c] = fmin(Te[15 + c], w[c]);
+            }
+        }
+    }
+    long long count = 0;
+#pragma omp parallel for reduction(+ : count) schedule(static)
+    for (long long e = 0; e < E; ++e) {
+        const double *Te = T + 20 * e;
+        double theta = 1.0;
+        for (int c = 0; c < 5; ++c) {
+            const double w0 = Te[5 + c];
+            double M = w0 + wid, mm = w0 - wid;
+            for (int a = 0; a < dim; ++a)
+                for (int sd = -1; sd <= 1; sd += 2) {
+                    const double *Tn = T + 20 * neighbour(m, e, a, sd);
+                    M = fmax(M, Tn[5 + c]);
+                    mm = fmin(mm, Tn[5 + c]);
+                }
+            const double dmax = Te[10 + c] - w0, dmin = Te[15 + c] - w0;
+            const double tiny = 1e-12 * fabs(w0);
+            if (fabs(dmax) > tiny) theta = fmin(theta, fabs((M - w0) / dmax));
+            if (fabs(dmin) > tiny) theta = fmin(theta, fabs((mm - w0) / dmin));
+        }
+        if (troubled) troubled[e] = theta < 1.0 ? 0x1f : 0;
+        if (!(theta < 1.0)) continue;
+        ++count;
+        for (int v = 0; v < 5; ++v) {
+            const double U0 = Te[v];
+            for (int q = 0; q < nn; ++q) {
+                double *x = U + (e * 5 + v) * nn + q;
+                *x = U0 + theta * (*x - U0);
+            }
+        }
+    }
+    free(S);
+    free(T);
+    return count;
+}
+
 long long or_limit(const or_mesh *m, double *U, unsigned char *troubled)
 {
     if (m->d.limiter == 0) {
         if (troubled) memset(troubled, 0, (size_t)m->E);
         return 0;
     }
+    if (m->d.limiter == 3) return limit_mrs(m, U, troubled);
     const int nn = m->nn, dim = m->d.dim;
     const long long E = m->E;
     double *S = (double *)malloc(sizeof(double) * 10 * 5 * E);

@@ -32,7 +32,8 @@ typedef struct {
     int n;           /* LGL nodes per active axis, 2..OR_MAXN */
     int flux;        /* 0 local Lax-Friedrichs (eq:LLF), 1 HLL with Davis speeds (eq:HLL),
                         2 Roe (eq:Roe, Newtonian only) */
-    int limiter;     /* 0 none, 1 generalized minmodB troubled-cell limiter ("MinModN"), 2 plain minmod ("MinMod") */
+    int limiter;     /* 0 none, 1 generalized minmodB troubled-cell limiter ("MinModN"), 2 plain minmod ("MinMod"),
+                        3 moment limiter of Moe, Rossmanith and Seal ("MRS", Sec. 3.3.3, Newtonian only) */
     double gamma;    /* ideal-gas adiabatic index */
     double lo[3];    /* periodic box */
     double hi[3];
@@ -40,6 +41,7 @@ typedef struct {
     double beta;     /* slope limiter beta: 2 minmod, 1 MUSCL (Sec. 3.3.1) */
     double d_atm;    /* SR conserved fix: floor on D */
     double tau_atm;  /* SR conserved fix: floor on tau, as a fraction of D */
+    double mrs_alpha; /* MRS: alpha~ of the bound widening alpha~ h^{3/2} */
 } or_desc;
 
 typedef struct or_mesh or_mesh;

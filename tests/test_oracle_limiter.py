@@ -131,3 +131,66 @@ def test_fix_bounds():
     assert np.all(s2 <= (1 - 1e-12) * tau * (tau + 2 * D) * (1 + 1e-15))
     _, _, st = oracle.con2prim(4 / 3, F[0])
     assert np.all(st == 0)
+
+
+def _mrs_mesh(K, n, alpha, dim=1):
+    Ks = (K, 1, 1) if dim == 1 else (K, K, K)
+    return oracle.Mesh(oracle.MeshSpec(system=0, dim=dim, K=Ks, n=n, flux=2, limiter=3, gamma=1.4,
+                                       mrs_alpha=alpha))
+
+
+def test_mrs_rescales_with_one_theta_and_keeps_means():
+    """eq:MRSSol: every element becomes U0 + Theta (U - U0) with a single Theta in
+    [0, 1] for all conserved variables and nodes; the cell means are kept."""
+    m = _mrs_mesh(3, 4, 0.5, dim=3)
+    U = m.from_prim(di.kh_ne(m.coords(), seed=4, amp=0.3))
+    V, t = m.limit(U)
+    S0 = m.summaries(U)[:, :, 0]
+    S1 = m.summaries(V)[:, :, 0]
+    assert np.allclose(S0, S1, rtol=0, atol=1e-14 * np.abs(S0).max())
+    assert (t != 0).any()
+    for e in range(m.E):
+        d0 = U[e] - S0[e][:, None]
+        d1 = V[e] - S0[e][:, None]
+        big = np.abs(d0) > 1e-12 * np.abs(U[e]).max()
+        th = d1[big] / d0[big]
+        assert np.all((th >= -1e-12) & (th <= 1 + 1e-12))
+        assert np.ptp(th) < 1e-9, (e, np.ptp(th))
+        assert (t[e] != 0) == (th.min() < 1 - 1e-12)
+
+
+def test_mrs_leaves_linear_data_alone():
+    """Data linear along one axis (the others constant, velocity constant up to
+    rounding) stay within the neighbours' means: Theta = 1, even with alpha~ = 0."""
+    m = _mrs_mesh(8, 4, 0.0, dim=3)
+    x, y, z = m.coords()
+    prim = np.stack([1.5 + 0.2 * x, 0.3 + 0 * x, -0.2 + 0 * x, 0.1 + 0 * x, 1.0 + 0.1 * x])
+    # periodic wrap breaks linearity at the box edge: judge interior elements only
+    U = m.from_prim(prim)
+    V, t = m.limit(U)
+    xc = x.reshape(m.E, -1).mean(axis=1)
+    yc = y.reshape(m.E, -1).mean(axis=1)
+    zc = z.reshape(m.E, -1).mean(axis=1)
+    inner = (np.minimum(xc, 1 - xc) > 0.13) & (np.minimum(yc, 1 - yc) > 0.13) & (np.minimum(zc, 1 - zc) > 0.13)
+    assert inner.any() and np.all(t[inner] == 0)
+    assert np.array_equal(V[inner], U[inner])
+
+
+def test_mrs_keeps_smooth_extrema_only_with_alpha():
+    """alpha~ > 0 widens the bounds by alpha~ h^{3/2}: on a fine mesh a smooth
+    extremum is left alone; with alpha~ = 0 the elements at the extrema are
+    clipped (Sec. 3.3.3)."""
+    counts = []
+    for alpha in (0.0, 50.0):
+        m = _mrs_mesh(64, 3, alpha)
+        x = m.coords()[0]
+        U = m.from_prim(di.smooth_wave_ne(m.coords(), 0.0, k=(1, 1, 1), vel=(0.5, 0.0, 0.0)))
+        _, t = m.limit(U)
+        counts.append(int((t != 0).sum()))
+    assert counts[0] > 0 and counts[1] == 0, counts
+
+
+def test_mrs_needs_newtonian_and_nonnegative_alpha():
+    for kw in (dict(system=1, gamma=4.0 / 3.0, mrs_alpha=1.0), dict(system=0, gamma=1.4, mrs_alpha=-1.0)):
+        with pytest.raises(Exception):
+            oracle.Mesh(oracle.MeshSpec(K=(2, 2, 2), n=3, limiter=3, **kw))
