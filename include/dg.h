@@ -45,7 +45,7 @@ typedef enum {
 
 enum { DG_SYSTEM_NEWTONIAN = 0, DG_SYSTEM_SR = 1 };
 enum { DG_FLUX_LLF = 0, DG_FLUX_HLL = 1, DG_FLUX_ROE = 2 };
-enum { DG_LIMITER_NONE = 0, DG_LIMITER_MINMODN = 1, DG_LIMITER_MINMOD = 2 };
+enum { DG_LIMITER_NONE = 0, DG_LIMITER_MINMODN = 1, DG_LIMITER_MINMOD = 2, DG_LIMITER_MRS = 3 };
 enum { DG_PRECISION_FP64 = 0, DG_PRECISION_MIXED = 1 };
 
 typedef struct {
@@ -53,7 +53,8 @@ typedef struct {
     int K[3];        /* elements per axis, >= 1 */
     int n;           /* LGL nodes per axis, 2..8 (degree N = n-1) */
     int flux;        /* DG_FLUX_*: eq:LLF, eq:HLL with Davis speeds, or eq:Roe (Newtonian only) */
-    int limiter;     /* DG_LIMITER_*: none, generalized minmodB detector + limiter (Sec. 3.3.2), plain minmod (Sec. 3.3.1) */
+    int limiter;     /* DG_LIMITER_*: none, generalized minmodB detector + limiter (Sec. 3.3.2), plain minmod
+                        (Sec. 3.3.1), or the moment limiter of Moe, Rossmanith and Seal (Sec. 3.3.3, Newtonian) */
     int precision;   /* DG_PRECISION_* */
     double gamma;    /* ideal-gas adiabatic index, > 1 */
     double lo[3];    /* periodic box [lo, hi) */
@@ -62,6 +63,7 @@ typedef struct {
     double beta;     /* slope-limiter beta (2 minmod, 1 MUSCL), > 0 */
     double d_atm;    /* SR fix: floor on D */
     double tau_atm;  /* SR fix: floor on tau as a fraction of D */
+    double mrs_alpha; /* DG_LIMITER_MRS: alpha~ >= 0 of the bound widening alpha~ h^{3/2} */
 } dg_mesh_desc;
 
 typedef struct dg_mesh dg_mesh;
@@ -116,7 +118,14 @@ dg_status dg_compute_dt(dg_mesh *mesh, const double *U, double cfl, double *dt, 
 dg_status dg_rk3_step(dg_mesh *mesh, double *U, double dt, double cfl, double *dt_used,
                       unsigned char *troubled, void *stream);
 
-/* Limiter alone, in place (Sec. 3.3.1, 3.3.2); troubled as in dg_rk3_step. */
+/* Limiter alone, in place (Sec. 3.3.1, 3.3.2, 3.3.3); troubled as in dg_rk3_step.
+ * DG_LIMITER_MRS (Sec. 3.3.3, eq:MRSSol; Newtonian meshes): per element, w the
+ * node primitives (rho, v, p) and w0 those of the cell average U0; with
+ * [m, M] = [min, max] of w0 over the element and its six face neighbours, widened
+ * to w0 -+ mrs_alpha h^{3/2} (h the largest element width), a scale
+ * theta = min(1, |(M - w0)/(max w - w0)|, |(m - w0)/(min w - w0)|) over the five
+ * primitives (a ratio counts 1 when its denominator is within 1e-12 |w0|) rescales
+ * every variable, U -> U0 + theta (U - U0); troubled gets 0x1f where theta < 1. */
 dg_status dg_limit(dg_mesh *mesh, double *U, unsigned char *troubled, void *stream);
 /* SR conserved-variable fix alone, in place (Sec. 2.1.4); no-op for Newtonian meshes. */
 dg_status dg_fix(dg_mesh *mesh, double *U, void *stream);
@@ -242,7 +251,8 @@ dg_status dg_mesh_set_c2p_net(dg_mesh *mesh, const dg_c2p_net *net);
  * meshes one by one with the same per-group options.  Device-side failures set
  * each mesh's status word (dg_sync_status per mesh).
  * Errors: DG_ERR_ARG for NULL or repeated meshes/states, FP64 meshes, or meshes on
- * another device; DG_ERR_CUDA for allocation failures. */
+ * another device, meshes with the moment limiter (DG_LIMITER_MRS); DG_ERR_CUDA for
+ * allocation failures. */
 typedef struct dg_ensemble dg_ensemble;
 dg_status dg_ensemble_create(dg_mesh *const *meshes, double *const *U, int count, dg_ensemble **out);
 void dg_ensemble_destroy(dg_ensemble *ens);

@@ -17,9 +17,11 @@ class Mesh:
     """Owns a dg_mesh created on the current CUDA device."""
 
     def __init__(self, system=0, K=(4, 4, 4), n=4, flux=0, limiter=0, precision=0, gamma=1.4,
-                 lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), tvb_M=0.0, beta=2.0, d_atm=1e-12, tau_atm=1e-14):
+                 lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), tvb_M=0.0, beta=2.0, d_atm=1e-12, tau_atm=1e-14,
+                 mrs_alpha=0.0):
         abi.load()
-        self.desc = make_desc(system, K, n, flux, limiter, precision, gamma, lo, hi, tvb_M, beta, d_atm, tau_atm)
+        self.desc = make_desc(system, K, n, flux, limiter, precision, gamma, lo, hi, tvb_M, beta, d_atm, tau_atm,
+                              mrs_alpha)
         self.h = abi.dg_mesh_create(self.desc)
         self.K, self.n = tuple(K), n
         self.E = K[0] * K[1] * K[2]

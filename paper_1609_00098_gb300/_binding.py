@@ -39,6 +39,7 @@ class dg_mesh_desc(ctypes.Structure):
         ("beta", ctypes.c_double),
         ("d_atm", ctypes.c_double),
         ("tau_atm", ctypes.c_double),
+        ("mrs_alpha", ctypes.c_double),
     ]
 
 
@@ -146,10 +147,11 @@ def _ptr(t, numel: int | None = None, dtype=None, name: str = "tensor"):
 
 def make_desc(system=0, K=(4, 4, 4), n=4, flux=0, limiter=0, precision=0, gamma=1.4,
               lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), tvb_M=0.0, beta=2.0, d_atm=1e-12,
-              tau_atm=1e-14) -> dg_mesh_desc:
+              tau_atm=1e-14, mrs_alpha=0.0) -> dg_mesh_desc:
     d = dg_mesh_desc()
     d.system, d.n, d.flux, d.limiter, d.precision = system, n, flux, limiter, precision
     d.gamma, d.tvb_M, d.beta, d.d_atm, d.tau_atm = gamma, tvb_M, beta, d_atm, tau_atm
+    d.mrs_alpha = mrs_alpha
     for a in range(3):
         d.K[a], d.lo[a], d.hi[a] = K[a], lo[a], hi[a]
     return d

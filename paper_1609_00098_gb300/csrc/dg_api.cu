@@ -435,6 +435,7 @@ void free_scratch(dg_mesh *m)
     for (int i = 0; i < 3; ++i) cudaFree(m->abL[i]);
     cudaFree(m->P);
     cudaFree(m->S);
+    cudaFree(m->mrsT);
     cudaFree(m->unphys);
     cudaFree(m->lam);
     cudaFree(m->dt);
@@ -455,7 +456,9 @@ dg_status dg_mesh_create(const dg_mesh_desc *d, dg_mesh **out)
     if (d->n < 2 || d->n > MAXN) return fail(DG_ERR_ARG, "n must be in 2..%d", MAXN);
     if (d->flux != 0 && d->flux != 1 && !(d->flux == 2 && d->system == 0))
         return fail(DG_ERR_ARG, "flux must be 0 (LLF), 1 (HLL) or, for the Newtonian system, 2 (Roe)");
-    if (d->limiter < 0 || d->limiter > 2) return fail(DG_ERR_ARG, "limiter must be 0, 1 or 2");
+    if (d->limiter < 0 || d->limiter > 3) return fail(DG_ERR_ARG, "limiter must be 0, 1, 2 or 3");
+    if (d->limiter == DG_LIMITER_MRS && (d->system != 0 || !(d->mrs_alpha >= 0.0)))
+        return fail(DG_ERR_ARG, "the moment limiter needs the Newtonian system and mrs_alpha >= 0");
     if (d->precision != 0 && d->precision != 1) return fail(DG_ERR_ARG, "precision must be 0 (FP64) or 1 (mixed)");
     if (!(d->gamma > 1.0)) return fail(DG_ERR_ARG, "gamma must be > 1");
     if (!(d->beta > 0.0) || !(d->tvb_M >= 0.0)) return fail(DG_ERR_ARG, "beta must be > 0 and tvb_M >= 0");
@@ -494,6 +497,7 @@ dg_status dg_mesh_create(const dg_mesh_desc *d, dg_mesh **out)
     }
     st = st ? st : cudaMalloc(&m->P, sizeof(double) * (size_t)E * 4 * m->nn);
     st = st ? st : cudaMalloc(&m->S, sizeof(double) * (size_t)E * 50);
+    if (d->limiter == DG_LIMITER_MRS) st = st ? st : cudaMalloc(&m->mrsT, sizeof(double) * (size_t)E * 20);
     st = st ? st : cudaMalloc(&m->unphys, (size_t)E);
     st = st ? st : cudaMalloc(&m->lam, sizeof(unsigned long long));
     st = st ? st : cudaMalloc(&m->dt, sizeof(double));
@@ -645,7 +649,9 @@ static dg_status rk3_step_mixed(dg_mesh *m, double *U, double dt, double cfl, do
             m->pi = 1 - m->pi;
             latest = m->pbuf[m->pi];
         }
-        if (lim) {
+        if (lim && m->d.limiter == DG_LIMITER_MRS) {
+            DG_LAUNCH(m, s, PROF_LIMIT, launch_mrs(m, outs[st], st == 2 ? troubled : nullptr, s));
+        } else if (lim) {
             LimitMixedArgs l = limit_mixed_args(m, outs[st], st == 2 ? troubled : nullptr);
             DG_LAUNCH(m, s, PROF_LIMIT, launch_limit_mixed(m->d.n, m->d.system, l, s));
         }
@@ -694,7 +700,9 @@ dg_status dg_rk3_step(dg_mesh *m, double *U, double dt, double cfl, double *dt_u
         a.ca = ca[st];
         a.cb = cb[st];
         DG_LAUNCH(m, s, PROF_STAGE, launch_stage_fp64(m->d.n, m->d.system, m->d.flux, a, m->E, s));
-        if (lim) {
+        if (lim && m->d.limiter == DG_LIMITER_MRS) {
+            DG_LAUNCH(m, s, PROF_LIMIT, launch_mrs(m, outs[st], st == 2 ? troubled : nullptr, s));
+        } else if (lim) {
             LimitArgs l = limit_args(m, outs[st], st == 2 ? troubled : nullptr);
             DG_LAUNCH(m, s, PROF_LIMIT, launch_limit(m->d.n, l, s));
         }
@@ -770,6 +778,10 @@ dg_status dg_limit(dg_mesh *m, double *U, unsigned char *troubled, void *stream)
     sa.unphys = (m->d.system == 1) ? m->unphys : nullptr;
     sa.T = m->T;
     DG_CUDA(launch_summaries(m->d.n, sa, m->E, s));
+    if (m->d.limiter == DG_LIMITER_MRS) {
+        DG_CUDA(launch_mrs(m, U, troubled, s));
+        return DG_OK;
+    }
     LimitArgs l = limit_args(m, U, troubled);
     DG_CUDA(launch_limit(m->d.n, l, s));
     return DG_OK;

@@ -102,6 +102,7 @@ struct dg_mesh {
     double *abL[3];
     long long ab_n;
     double ab_dt;
+    double *mrsT;            // MRS limiter: per element U0, w0, w_max, w_min (20 doubles)
     // optional per-kernel timing (dg_profile_enable)
     int prof_on;
     void *prof;              // host-side event log, owned by dg_api.cu
@@ -117,6 +118,7 @@ cudaError_t launch_limit(int n, const LimitArgs &a, cudaStream_t s);
 cudaError_t launch_primitives(const dg_mesh *m, const double *U, double *P, int fix, double *Ufix,
                               unsigned long long *lam, cudaStream_t s);
 cudaError_t launch_fix(const dg_mesh *m, double *U, cudaStream_t s);
+cudaError_t launch_mrs(const dg_mesh *m, double *U, unsigned char *troubled, cudaStream_t s);
 cudaError_t launch_ab3_combine(double *U, const double *L0, const double *L1, const double *L2, double dt,
                                long long count, cudaStream_t s);
 cudaError_t launch_dt(const dg_mesh *m, double cfl, double *dt, cudaStream_t s);

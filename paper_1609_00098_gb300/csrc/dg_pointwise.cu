@@ -91,6 +91,100 @@ __global__ void __launch_bounds__(kThreads) k_fix(double *U, long long total, in
     }
 }
 
+// Moment limiter of Moe, Rossmanith and Seal (Sec. 3.3.3, eq:MRSSol), Newtonian
+// system, with the oracle's operations: per element T = (U0[5], w0[5], w_max[5],
+// w_min[5]), w = (rho, vx, vy, vz, p) the node primitives and w0 those of the
+// LGL cell average U0 (summaries S[e][v][0]).  One warp per element.
+template <int NP>
+__global__ void __launch_bounds__(256) k_mrs_prepare(const double *U, const double *S, double *T, long long E,
+                                                     double g)
+{
+    constexpr int NN = NP * NP * NP;
+    const long long e = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (e >= E) return;
+    double wmax[5], wmin[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+        wmax[c] = -INFINITY;
+        wmin[c] = INFINITY;
+    }
+    for (int q = lane; q < NN; q += 32) {
+        double u[5], P[4];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) u[v] = U[(e * 5 + v) * NN + q];
+        ne_primitives(g, u, P);
+        const double w[5] = {u[0], P[0], P[1], P[2], P[3]};
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+            wmax[c] = fmax(wmax[c], w[c]);
+            wmin[c] = fmin(wmin[c], w[c]);
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 5; ++c)
+        for (int o = 16; o > 0; o >>= 1) {
+            wmax[c] = fmax(wmax[c], __shfl_xor_sync(0xffffffffu, wmax[c], o));
+            wmin[c] = fmin(wmin[c], __shfl_xor_sync(0xffffffffu, wmin[c], o));
+        }
+    if (lane == 0) {
+        double *Te = T + 20 * e;
+        double u0[5], P0[4];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) u0[v] = Te[v] = S[(e * 5 + v) * 10];
+        ne_primitives(g, u0, P0);
+        Te[5] = u0[0];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) Te[6 + c] = P0[c];
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+            Te[10 + c] = wmax[c];
+            Te[15 + c] = wmin[c];
+        }
+    }
+}
+
+// Theta = min over components of min(1, |(M - w0)/(w_max - w0)|, |(m - w0)/(w_min - w0)|)
+// with [m, M] the face neighbours' w0 widened to w0 -+ wid (wid = alpha~ h^{3/2}), a
+// ratio counting 1 when its denominator is within 1e-12 |w0|; then U -> U0 + Theta (U - U0).
+template <int NP>
+__global__ void __launch_bounds__(256) k_mrs_limit(double *U, const double *T, unsigned char *troubled, long long E,
+                                                   int K0, int K1, int K2, double wid)
+{
+    constexpr int NN = NP * NP * NP;
+    const long long e = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (e >= E) return;
+    const double *Te = T + 20 * e;
+    double theta = 1.0;
+    if (lane < 5) {
+        const int c = lane;
+        const int K[3] = {K0, K1, K2};
+        const double w0 = Te[5 + c];
+        double M = w0 + wid, mm = w0 - wid;
+        for (int a = 0; a < 3; ++a)
+            for (int sd = -1; sd <= 1; sd += 2) {
+                const double *Tn = T + 20 * elem_neighbour(e, K, a, sd);
+                M = fmax(M, Tn[5 + c]);
+                mm = fmin(mm, Tn[5 + c]);
+            }
+        const double dmax = Te[10 + c] - w0, dmin = Te[15 + c] - w0;
+        const double tiny = 1e-12 * fabs(w0);
+        if (fabs(dmax) > tiny) theta = fmin(theta, fabs((M - w0) / dmax));
+        if (fabs(dmin) > tiny) theta = fmin(theta, fabs((mm - w0) / dmin));
+    }
+    for (int o = 16; o > 0; o >>= 1) theta = fmin(theta, __shfl_xor_sync(0xffffffffu, theta, o));
+    if (lane == 0 && troubled) troubled[e] = theta < 1.0 ? 0x1f : 0;
+    if (!(theta < 1.0)) return;
+    for (int v = 0; v < 5; ++v) {
+        const double U0 = Te[v];
+        for (int q = lane; q < NN; q += 32) {
+            double *x = U + (e * 5 + v) * NN + q;
+            *x = U0 + theta * (*x - U0);
+        }
+    }
+}
+
 // U <- U + dt ((c0 L0 - c1 L1) + c2 L2), the third-order Adams-Bashforth
 // combination (Sec. 3.4) with c = (23, 16, 5)/12, in the oracle's operation order.
 __global__ void __launch_bounds__(kThreads) k_ab3(double *U, const double *L0, const double *L1, const double *L2,
@@ -215,6 +309,34 @@ cudaError_t launch_fix(const dg_mesh *m, double *U, cudaStream_t s)
     const long long total = m->E * m->nn;
     k_fix<<<grid_for(total, kThreads), kThreads, 0, s>>>(U, total, m->nn, m->d.d_atm, m->d.tau_atm);
     return cudaGetLastError();
+}
+
+template <int NP>
+cudaError_t launch_mrs_np(const dg_mesh *m, double *U, unsigned char *troubled, cudaStream_t s)
+{
+    const unsigned grid = (unsigned)((m->E * 32 + 255) / 256);
+    k_mrs_prepare<NP><<<grid, 256, 0, s>>>(U, m->S, m->mrsT, m->E, m->d.gamma);
+    double h = 0.0;
+    for (int a = 0; a < 3; ++a) h = fmax(h, m->dx[a]);
+    const double wid = m->d.mrs_alpha * h * sqrt(h);
+    k_mrs_limit<NP><<<grid, 256, 0, s>>>(U, m->mrsT, troubled, m->E, m->d.K[0], m->d.K[1], m->d.K[2], wid);
+    return cudaGetLastError();
+}
+
+// MRS pass over a state whose summaries S are current (the stage kernel's, or
+// dg_limiter_summaries').
+cudaError_t launch_mrs(const dg_mesh *m, double *U, unsigned char *troubled, cudaStream_t s)
+{
+    switch (m->d.n) {
+    case 2: return launch_mrs_np<2>(m, U, troubled, s);
+    case 3: return launch_mrs_np<3>(m, U, troubled, s);
+    case 4: return launch_mrs_np<4>(m, U, troubled, s);
+    case 5: return launch_mrs_np<5>(m, U, troubled, s);
+    case 6: return launch_mrs_np<6>(m, U, troubled, s);
+    case 7: return launch_mrs_np<7>(m, U, troubled, s);
+    case 8: return launch_mrs_np<8>(m, U, troubled, s);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_ab3_combine(double *U, const double *L0, const double *L1, const double *L2, double dt,
