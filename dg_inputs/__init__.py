@@ -16,6 +16,7 @@ library is measured on):
   * ``blast_sr``: spherical relativistic blast, rho=10, p=13.33 for r<0.3 else
     rho=1, p=1e-6, v=0, with 1% seeded density noise;
   * ``kh_ne``: Kelvin-Helmholtz shear layer, Newtonian;
+  * ``isentropic_vortex``: eq:isen_vortex (Sec. 6.3.1), Newtonian, at any t;
   * ``riemann_1d``: the Riemann problems of tab:Riemann_Problems (Sec. 6.1);
   * ``c2p_samples``: random primitive states for con2prim;
   * ``ensemble_recipe``: the (system, K, n) list of a ragged ensemble.
@@ -115,6 +116,23 @@ def kh_ne(xyz: np.ndarray, seed: int, p: float = 2.5, amp: float = 0.01) -> np.n
     u = uniform(seed, STREAM_NOISE, np.arange(x.size)).reshape(x.shape)
     vy = amp * (2.0 * u - 1.0)
     return _prim(rho, vx, vy, 0.0, p)
+
+
+VORTEX = dict(beta=5.0, x0=4.0, y0=4.0, vel=(1.0, 1.0, 0.0), gamma=1.4)  # tab:IsenVortexConvergence
+
+
+def isentropic_vortex(xyz: np.ndarray, t: float = 0.0, beta: float = 5.0, x0: float = 4.0, y0: float = 4.0,
+                      vel=(1.0, 1.0, 0.0), gamma: float = 1.4) -> np.ndarray:
+    """eq:isen_vortex at time t: with xt = x - x0 - U t, yt = y - y0 - V t and
+    r^2 = xt^2 + yt^2, rho = (1 - (gamma-1) beta^2 e^(1-r^2) / (8 gamma pi^2))^(1/(gamma-1)),
+    v = (U - yt f, V + xt f, W) with f = beta e^((1-r^2)/2) / (2 pi), p = rho^gamma."""
+    x, y, _ = xyz
+    xt = x - x0 - vel[0] * t
+    yt = y - y0 - vel[1] * t
+    r2 = xt * xt + yt * yt
+    rho = (1.0 - (gamma - 1.0) * beta * beta * np.exp(1.0 - r2) / (8.0 * gamma * math.pi ** 2)) ** (1.0 / (gamma - 1.0))
+    f = beta * np.exp(0.5 * (1.0 - r2)) / (2.0 * math.pi)
+    return _prim(rho, vel[0] - yt * f, vel[1] + xt * f, vel[2] + 0.0 * x, rho ** gamma)
 
 
 RIEMANN = {

@@ -58,6 +58,9 @@ class Desc(ctypes.Structure):
         ("d_atm", ctypes.c_double),
         ("tau_atm", ctypes.c_double),
         ("mrs_alpha", ctypes.c_double),
+        ("bc", ctypes.c_int * 3),
+        ("exact", ctypes.c_int),
+        ("exact_par", ctypes.c_double * 6),
     ]
 
 
@@ -92,6 +95,8 @@ def _load():
         "or_limit": (ll, [vp, _dp, _up]),
         "or_fix": (ll, [vp, _dp]),
         "or_rk3_step": (ll, [vp, _dp, ctypes.c_double, _up]),
+        "or_set_time": (None, [vp, ctypes.c_double]),
+        "or_get_time": (ctypes.c_double, [vp]),
         "or_norms": (None, [vp, _dp, _dp, _dp, _dp]),
         "or_totals": (None, [vp, _dp, _dp]),
         "or_num_flux": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int,
@@ -201,6 +206,9 @@ class MeshSpec:
     d_atm: float = 1e-12
     tau_atm: float = 1e-14
     mrs_alpha: float = 0.0
+    bc: tuple = (0, 0, 0)          # per axis: 0 periodic, 1 analytic exterior state
+    exact: int = 0                 # 1: isentropic vortex (eq:isen_vortex) supplies exterior states
+    exact_par: tuple = (0.0,) * 6  # isentropic vortex: beta, X0, Y0, U, V, W
     extra: dict = field(default_factory=dict)
 
 
@@ -227,6 +235,11 @@ class Mesh:
         d.d_atm = spec.d_atm
         d.tau_atm = spec.tau_atm
         d.mrs_alpha = spec.mrs_alpha
+        for a in range(3):
+            d.bc[a] = spec.bc[a]
+        d.exact = spec.exact
+        for i in range(6):
+            d.exact_par[i] = spec.exact_par[i]
         self._d = d
         self.h = lib.or_mesh_create(ctypes.byref(d))
         if not self.h:
@@ -292,6 +305,15 @@ class Mesh:
         n = self.lib.or_fix(self.h, _ptr(U))
         return U, n
 
+    @property
+    def t(self) -> float:
+        """Mesh time; enters the method only through analytic exterior states."""
+        return self.lib.or_get_time(self.h)
+
+    @t.setter
+    def t(self, value: float):
+        self.lib.or_set_time(self.h, value)
+
     def rk3_step(self, U, dt: float, troubled: np.ndarray | None = None) -> np.ndarray:
         U = _f64(U).copy()
         self.lib.or_rk3_step(self.h, _ptr(U), dt, None if troubled is None else _ptr(troubled, _up))
@@ -329,6 +351,7 @@ class Mesh:
                 U = self.rk3_step(U, dt)
                 continue
             U = U + dt * ((23.0 / 12.0 * L - 16.0 / 12.0 * hist[-1]) + 5.0 / 12.0 * hist[-2])
+            self.t = self.t + dt
             hist = [hist[-1], L]
             U, _ = self.limit(U)
             if self.spec.system == 1:

@@ -23,6 +23,7 @@ struct or_mesh {
     double w[OR_MAXN];  /* LGL weights */
     double D[OR_MAXN * OR_MAXN];
     double Vinv[OR_MAXN * OR_MAXN];
+    double t;           /* mesh time: enters only through analytic exterior states */
 };
 
 /* ------------------------------------------------------------------------ */
@@ -141,6 +142,14 @@ or_mesh *or_mesh_create(const or_desc *d)
     if (d->flux < 0 || d->flux > 2 || (d->flux == 2 && d->system != 0)) return NULL;  /* Roe: Newtonian only */
     if (d->limiter < 0 || d->limiter > 3 || (d->limiter == 3 && (d->system != 0 || !(d->mrs_alpha >= 0.0))))
         return NULL;  /* MRS: Newtonian only, alpha~ >= 0 */
+    int analytic = 0;
+    for (int a = 0; a < d->dim; ++a) {
+        if (d->bc[a] != 0 && d->bc[a] != 1) return NULL;
+        analytic |= d->bc[a];
+    }
+    if (d->exact < 0 || d->exact > 1) return NULL;
+    /* analytic exterior states: the isentropic vortex (Newtonian), no limiter */
+    if (analytic && (d->exact != 1 || d->system != 0 || d->limiter != 0)) return NULL;
     or_mesh *m = (or_mesh *)calloc(1, sizeof(or_mesh));
     m->d = *d;
     m->nn = 1;
@@ -160,6 +169,8 @@ or_mesh *or_mesh_create(const or_desc *d)
 }
 
 void or_mesh_destroy(or_mesh *m) { free(m); }
+void or_set_time(or_mesh *m, double t) { m->t = t; }
+double or_get_time(const or_mesh *m) { return m->t; }
 long long or_num_elements(const or_mesh *m) { return m->E; }
 int or_nodes_per_element(const or_mesh *m) { return m->nn; }
 
@@ -530,7 +541,43 @@ static long long node_id(const or_mesh *m, int i, int j, int k)
     return i + (long long)m->na[0] * (j + (long long)m->na[1] * k);
 }
 
-long long or_rhs(const or_mesh *m, const double *U, double *R)
+/* eq:isen_vortex at point x and time t; par = (beta, X0, Y0, U, V, W), P = rho^gamma */
+static void isentropic_vortex(const double *par, double g, const double *x, double t, double *pr)
+{
+    const double pi = 3.14159265358979323846;
+    const double beta = par[0];
+    const double xt = x[0] - par[1] - par[3] * t;
+    const double yt = x[1] - par[2] - par[4] * t;
+    const double r2 = xt * xt + yt * yt;
+    const double rho = pow(1.0 - (g - 1.0) * beta * beta / (8.0 * g * pi * pi) * exp(1.0 - r2), 1.0 / (g - 1.0));
+    const double f = beta / (2.0 * pi) * exp(0.5 * (1.0 - r2));
+    pr[0] = rho;
+    pr[1] = par[3] - yt * f;
+    pr[2] = par[4] + xt * f;
+    pr[3] = par[5];
+    pr[4] = pow(rho, g);
+}
+
+/* Exterior state of a boundary face node (Sec. 3.4: the interior numerical flux
+ * with the exterior solution supplied): the analytic solution at time t at the
+ * coordinates of the interior trace node (element e, node indices id),
+ * conserved, and its primitives as node_prim recovers them. */
+static void exterior_state(const or_mesh *m, long long e, const int *id, double t, double *u, double *P)
+{
+    int ec[3];
+    elem_coords(m, e, ec);
+    double x[3], pr[5];
+    for (int a = 0; a < 3; ++a) {
+        const double ak = m->d.lo[a] + ec[a] * m->dx[a];
+        const double bk = ak + m->dx[a];
+        x[a] = ak + 0.5 * (1.0 + xbar(m, a, id[a])) * (bk - ak);
+    }
+    isentropic_vortex(m->d.exact_par, m->d.gamma, x, t, pr);
+    prim2con_node(0, m->d.gamma, pr, u);
+    node_prim(0, m->d.gamma, u, P);
+}
+
+static long long rhs_at(const or_mesh *m, const double *U, double *R, double t)
 {
     const int nn = m->nn, n = m->d.n, dim = m->d.dim;
     const long long E = m->E;
@@ -574,15 +621,21 @@ long long or_rhs(const or_mesh *m, const double *U, double *R)
         free(F);
     }
 
-    /* surface terms, one axis after another */
+    /* surface terms, one axis after another; on an analytic axis the faces at
+     * lo and hi take the exterior state instead of the periodic neighbour */
     for (int a = 0; a < dim; ++a) {
         const double g = 2.0 / m->dx[a];
         const double liftN = g / m->w[n - 1];
         const double lift0 = g / m->w[0];
         const int b = (a + 1) % 3, c = (a + 2) % 3;
+        const int analytic = m->d.bc[a] == 1;
 #pragma omp parallel for schedule(static)
         for (long long e = 0; e < E; ++e) {
             const long long ep = neighbour(m, e, a, +1);
+            int ec[3];
+            elem_coords(m, e, ec);
+            const int hi_bnd = analytic && ec[a] == m->d.K[a] - 1;
+            const int lo_bnd = analytic && ec[a] == 0;
             for (int t1 = 0; t1 < m->na[c]; ++t1)
                 for (int t0 = 0; t0 < m->na[b]; ++t0) {
                     int iL[3], iR[3];
@@ -592,20 +645,30 @@ long long or_rhs(const or_mesh *m, const double *U, double *R)
                     const long long qL = node_id(m, iL[0], iL[1], iL[2]);
                     const long long qR = node_id(m, iR[0], iR[1], iR[2]);
                     double uL[5], uR[5], PL[4], PR[4], Fs[5], FL[5], FR[5];
-                    for (int v = 0; v < 5; ++v) {
-                        uL[v] = U[(e * 5 + v) * nn + qL];
-                        uR[v] = U[(ep * 5 + v) * nn + qR];
-                    }
-                    for (int cc = 0; cc < 4; ++cc) {
-                        PL[cc] = P[(e * 4 + cc) * nn + qL];
-                        PR[cc] = P[(ep * 4 + cc) * nn + qR];
+                    for (int v = 0; v < 5; ++v) uL[v] = U[(e * 5 + v) * nn + qL];
+                    for (int cc = 0; cc < 4; ++cc) PL[cc] = P[(e * 4 + cc) * nn + qL];
+                    if (hi_bnd) {
+                        exterior_state(m, e, iL, t, uR, PR);
+                    } else {
+                        for (int v = 0; v < 5; ++v) uR[v] = U[(ep * 5 + v) * nn + qR];
+                        for (int cc = 0; cc < 4; ++cc) PR[cc] = P[(ep * 4 + cc) * nn + qR];
                     }
                     num_flux(m, a, uL, PL, uR, PR, Fs, FL, FR);
                     for (int v = 0; v < 5; ++v) {
                         /* lower element: n_out = +e_a */
                         R[(e * 5 + v) * nn + qL] = R[(e * 5 + v) * nn + qL] - liftN * (Fs[v] - FL[v]);
                         /* upper element: n_out = -e_a, so (F*-F).n_out = -(F*_a - F_a) */
-                        R[(ep * 5 + v) * nn + qR] = R[(ep * 5 + v) * nn + qR] + lift0 * (Fs[v] - FR[v]);
+                        if (!hi_bnd)
+                            R[(ep * 5 + v) * nn + qR] = R[(ep * 5 + v) * nn + qR] + lift0 * (Fs[v] - FR[v]);
+                    }
+                    if (lo_bnd) {
+                        /* the element's lower face: exterior on the left, this element on the right */
+                        for (int v = 0; v < 5; ++v) uR[v] = U[(e * 5 + v) * nn + qR];
+                        for (int cc = 0; cc < 4; ++cc) PR[cc] = P[(e * 4 + cc) * nn + qR];
+                        exterior_state(m, e, iR, t, uL, PL);
+                        num_flux(m, a, uL, PL, uR, PR, Fs, FL, FR);
+                        for (int v = 0; v < 5; ++v)
+                            R[(e * 5 + v) * nn + qR] = R[(e * 5 + v) * nn + qR] + lift0 * (Fs[v] - FR[v]);
                     }
                 }
         }
@@ -613,6 +676,8 @@ long long or_rhs(const or_mesh *m, const double *U, double *R)
     free(P);
     return fails;
 }
+
+long long or_rhs(const or_mesh *m, const double *U, double *R) { return rhs_at(m, U, R, m->t); }
 
 double or_lambda_max(const or_mesh *m, const double *U)
 {
@@ -916,7 +981,7 @@ long long or_fix(const or_mesh *m, double *U)
  *   U1 = Un + dt L(Un);  U2 = 3/4 Un + 1/4 (U1 + dt L(U1));
  *   Un+1 = 1/3 Un + 2/3 (U2 + dt L(U2)),
  * with the limiter and then the SR fix applied after every stage (Sec. 3.3). */
-long long or_rk3_step(const or_mesh *m, double *U, double dt, unsigned char *troubled_last)
+long long or_rk3_step(or_mesh *m, double *U, double dt, unsigned char *troubled_last)
 {
     const long long tot = m->E * 5 * m->nn;
     double *Un = (double *)malloc(sizeof(double) * tot);
@@ -924,9 +989,10 @@ long long or_rk3_step(const or_mesh *m, double *U, double dt, unsigned char *tro
     memcpy(Un, U, sizeof(double) * tot);
     const double ca[3] = {0.0, 0.75, 1.0 / 3.0};
     const double cb[3] = {1.0, 0.25, 2.0 / 3.0};
+    const double ct[3] = {0.0, 1.0, 0.5};  /* stage times t + ct dt of U, U1, U2 */
     long long fails = 0;
     for (int s = 0; s < 3; ++s) {
-        fails += or_rhs(m, U, L);
+        fails += rhs_at(m, U, L, m->t + ct[s] * dt);
 #pragma omp parallel for schedule(static)
         for (long long q = 0; q < tot; ++q) {
             const double y = U[q] + dt * L[q];
@@ -935,6 +1001,7 @@ long long or_rk3_step(const or_mesh *m, double *U, double dt, unsigned char *tro
         or_limit(m, U, s == 2 ? troubled_last : NULL);
         or_fix(m, U);
     }
+    m->t = m->t + dt;
     free(Un);
     free(L);
     return fails;

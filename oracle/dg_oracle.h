@@ -42,6 +42,10 @@ typedef struct {
     double d_atm;    /* SR conserved fix: floor on D */
     double tau_atm;  /* SR conserved fix: floor on tau, as a fraction of D */
     double mrs_alpha; /* MRS: alpha~ of the bound widening alpha~ h^{3/2} */
+    int bc[3];       /* per axis: 0 periodic, 1 analytic exterior state (Sec. 3.4, boundary faces) */
+    int exact;       /* analytic solution supplying exterior states: 0 none, 1 isentropic vortex
+                        (eq:isen_vortex; Newtonian, P = rho^gamma) */
+    double exact_par[6]; /* isentropic vortex: beta, X0, Y0, U, V, W */
 } or_desc;
 
 typedef struct or_mesh or_mesh;
@@ -74,8 +78,12 @@ long long or_primitives(const or_mesh *m, const double *U, double *P);
 /* Point-wise numerical flux along +e_axis (LLF, HLL or Roe) for tests. */
 int or_num_flux(int system, double gamma, int flux, int axis, const double *uL, const double *uR,
                 double *Fs, double *FL, double *FR, double *speeds);
-/* Semi-discrete right-hand side, eq:411.  Returns number of con2prim failures. */
+/* Semi-discrete right-hand side, eq:411, at the mesh time (which only enters
+ * through analytic exterior states).  Returns number of con2prim failures. */
 long long or_rhs(const or_mesh *m, const double *U, double *dUdt);
+/* Mesh time t (0 at creation); or_rk3_step advances it by dt. */
+void   or_set_time(or_mesh *m, double t);
+double or_get_time(const or_mesh *m);
 /* max over nodes and active axes of the largest |characteristic speed| */
 double or_lambda_max(const or_mesh *m, const double *U);
 /* CFL step Delta t = C * dx_min / lambda_max (Sec. 3.4) */
@@ -88,7 +96,7 @@ long long or_limit(const or_mesh *m, double *U, unsigned char *troubled);
 /* SR conserved-variable fix (Sec. 2.1.4), in place.  Returns the number of changed nodes. */
 long long or_fix(const or_mesh *m, double *U);
 /* One SSP-RK3 step with limiter and fix after each stage.  Returns con2prim failures. */
-long long or_rk3_step(const or_mesh *m, double *U, double dt, unsigned char *troubled_last);
+long long or_rk3_step(or_mesh *m, double *U, double dt, unsigned char *troubled_last);
 /* L1 (eq:L1) and L2 norms of U - V per variable with LGL quadrature */
 void or_norms(const or_mesh *m, const double *U, const double *V, double *l1, double *l2);
 /* sum over the mesh of w J U per variable (discrete conserved totals) */
