@@ -64,7 +64,20 @@ typedef struct {
     double d_atm;    /* SR fix: floor on D */
     double tau_atm;  /* SR fix: floor on tau as a fraction of D */
     double mrs_alpha; /* DG_LIMITER_MRS: alpha~ >= 0 of the bound widening alpha~ h^{3/2} */
+    int bc[3];       /* DG_BC_* per axis: periodic, or analytic exterior states on the faces at lo and hi
+                        (Sec. 3.4: the interior numerical flux with the exterior solution supplied) */
+    int exact;       /* DG_EXACT_*: the analytic solution of analytic boundaries */
+    double exact_par[6]; /* DG_EXACT_ISENTROPIC_VORTEX: beta, X0, Y0, U, V, W of eq:isen_vortex */
 } dg_mesh_desc;
+
+/* Analytic boundaries need the Newtonian system, DG_EXACT_ISENTROPIC_VORTEX and no
+ * limiter.  The exterior state of a boundary face node is eq:isen_vortex (P = rho^gamma)
+ * at the coordinates of the interior trace node and the stage time: SSP-RK3 takes
+ * t, t + dt, t + dt/2 for its three stages, dg_rhs and Adams-Bashforth the mesh
+ * time t.  Exterior states use CUDA's exp and pow, so FP64 results agree with a
+ * libm evaluation to rounding rather than bit for bit. */
+enum { DG_BC_PERIODIC = 0, DG_BC_ANALYTIC = 1 };
+enum { DG_EXACT_NONE = 0, DG_EXACT_ISENTROPIC_VORTEX = 1 };
 
 typedef struct dg_mesh dg_mesh;
 
@@ -117,6 +130,13 @@ dg_status dg_compute_dt(dg_mesh *mesh, const double *U, double cfl, double *dt, 
  * bitmask of limited variables of the last stage. */
 dg_status dg_rk3_step(dg_mesh *mesh, double *U, double dt, double cfl, double *dt_used,
                       unsigned char *troubled, void *stream);
+
+/* Mesh time t (device-resident; 0 at creation).  Every dg_rk3_step and
+ * dg_ab3_step of a mesh with analytic boundaries advances it by the step taken
+ * (on periodic meshes time enters nowhere and it stays put).  dg_mesh_set_time
+ * is stream-ordered; dg_mesh_get_time synchronises `stream` and writes *t (host). */
+dg_status dg_mesh_set_time(dg_mesh *mesh, double t, void *stream);
+dg_status dg_mesh_get_time(dg_mesh *mesh, double *t, void *stream);
 
 /* Limiter alone, in place (Sec. 3.3.1, 3.3.2, 3.3.3); troubled as in dg_rk3_step.
  * DG_LIMITER_MRS (Sec. 3.3.3, eq:MRSSol; Newtonian meshes): per element, w the
@@ -206,6 +226,7 @@ dg_status dg_c2p_net_train(dg_c2p_net *net, long long count, const double *cons,
  * the GPU race on it.  A node without a physical primitive state gives non-finite
  * values in dUdt. */
 #define DG_RHS_STATIC_MAX_NODES 131072
+/* (periodic meshes only: DG_ERR_ARG for analytic boundaries) */
 dg_status dg_rhs_static(const dg_mesh_desc *desc, const double *U, double *dUdt, void *stream);
 
 /* Per-mesh options of the mixed-precision path (no effect on the FP64 path,

@@ -18,10 +18,10 @@ class Mesh:
 
     def __init__(self, system=0, K=(4, 4, 4), n=4, flux=0, limiter=0, precision=0, gamma=1.4,
                  lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), tvb_M=0.0, beta=2.0, d_atm=1e-12, tau_atm=1e-14,
-                 mrs_alpha=0.0):
+                 mrs_alpha=0.0, bc=(0, 0, 0), exact=0, exact_par=(0.0,) * 6):
         abi.load()
         self.desc = make_desc(system, K, n, flux, limiter, precision, gamma, lo, hi, tvb_M, beta, d_atm, tau_atm,
-                              mrs_alpha)
+                              mrs_alpha, bc, exact, exact_par)
         self.h = abi.dg_mesh_create(self.desc)
         self.K, self.n = tuple(K), n
         self.E = K[0] * K[1] * K[2]
@@ -103,6 +103,15 @@ class Mesh:
 
     def ab3_reset(self):
         abi.dg_ab3_reset(self.h)
+
+    @property
+    def t(self) -> float:
+        """Mesh time (advanced by steps of meshes with analytic boundaries)."""
+        return abi.dg_mesh_get_time(self.h)
+
+    @t.setter
+    def t(self, value):
+        abi.dg_mesh_set_time(self.h, value)
 
     def set_option(self, option, value):
         """Mixed-path option: abi.OPT_TENSOR_CORE_CONTRACTION or abi.OPT_C2P_KAPPA_SWITCH."""

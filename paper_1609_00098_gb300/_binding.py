@@ -40,6 +40,9 @@ class dg_mesh_desc(ctypes.Structure):
         ("d_atm", ctypes.c_double),
         ("tau_atm", ctypes.c_double),
         ("mrs_alpha", ctypes.c_double),
+        ("bc", ctypes.c_int * 3),
+        ("exact", ctypes.c_int),
+        ("exact_par", ctypes.c_double * 6),
     ]
 
 
@@ -71,6 +74,8 @@ SIGNATURES = {
     "dg_mesh_set_option": (_i, [_vp, _i, _d]),
     "dg_ab3_step": (_i, [_vp, _vp, _d, _vp, _vp]),
     "dg_ab3_reset": (_i, [_vp]),
+    "dg_mesh_set_time": (_i, [_vp, _d, _vp]),
+    "dg_mesh_get_time": (_i, [_vp, ctypes.POINTER(ctypes.c_double), _vp]),
     "dg_ensemble_create": (_i, [_vp, _vp, _i, ctypes.POINTER(_vp)]),
     "dg_ensemble_destroy": (None, [_vp]),
     "dg_ensemble_tune": (_i, [_vp, _vp]),
@@ -147,13 +152,17 @@ def _ptr(t, numel: int | None = None, dtype=None, name: str = "tensor"):
 
 def make_desc(system=0, K=(4, 4, 4), n=4, flux=0, limiter=0, precision=0, gamma=1.4,
               lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), tvb_M=0.0, beta=2.0, d_atm=1e-12,
-              tau_atm=1e-14, mrs_alpha=0.0) -> dg_mesh_desc:
+              tau_atm=1e-14, mrs_alpha=0.0, bc=(0, 0, 0), exact=0, exact_par=(0.0,) * 6) -> dg_mesh_desc:
     d = dg_mesh_desc()
     d.system, d.n, d.flux, d.limiter, d.precision = system, n, flux, limiter, precision
     d.gamma, d.tvb_M, d.beta, d.d_atm, d.tau_atm = gamma, tvb_M, beta, d_atm, tau_atm
     d.mrs_alpha = mrs_alpha
     for a in range(3):
         d.K[a], d.lo[a], d.hi[a] = K[a], lo[a], hi[a]
+        d.bc[a] = bc[a]
+    d.exact = exact
+    for i in range(6):
+        d.exact_par[i] = exact_par[i]
     return d
 
 
@@ -342,6 +351,16 @@ def dg_ab3_step(mesh, U, dt, troubled=None, stream=None):
 
 def dg_ab3_reset(mesh):
     _check(load().dg_ab3_reset(mesh))
+
+
+def dg_mesh_set_time(mesh, t, stream=None):
+    _check(load().dg_mesh_set_time(mesh, float(t), _stream(stream)))
+
+
+def dg_mesh_get_time(mesh, stream=None) -> float:
+    t = ctypes.c_double(0.0)
+    _check(load().dg_mesh_get_time(mesh, ctypes.byref(t), _stream(stream)))
+    return t.value
 
 
 def dg_mesh_set_c2p_net(mesh, net):

@@ -301,6 +301,7 @@ MeshSlot mixed_slot(const dg_mesh *m)
         sl.liftN[ax] = (float)(g / m->T.w[m->d.n - 1]);
     }
     sl.err = m->err;
+    sl.gh = m->gh;
     return sl;
 }
 
@@ -383,6 +384,7 @@ StageArgs stage_args(const dg_mesh *m)
         a.liftN[ax] = a.g[ax] / m->T.w[m->d.n - 1];
     }
     a.gamma = m->d.gamma;
+    a.gh = m->gh;
     a.T = m->T;
     return a;
 }
@@ -436,6 +438,9 @@ void free_scratch(dg_mesh *m)
     cudaFree(m->P);
     cudaFree(m->S);
     cudaFree(m->mrsT);
+    cudaFree(m->t);
+    cudaFree(const_cast<double *>(m->gh.U));
+    cudaFree(const_cast<double *>(m->gh.P));
     cudaFree(m->unphys);
     cudaFree(m->lam);
     cudaFree(m->dt);
@@ -459,6 +464,14 @@ dg_status dg_mesh_create(const dg_mesh_desc *d, dg_mesh **out)
     if (d->limiter < 0 || d->limiter > 3) return fail(DG_ERR_ARG, "limiter must be 0, 1, 2 or 3");
     if (d->limiter == DG_LIMITER_MRS && (d->system != 0 || !(d->mrs_alpha >= 0.0)))
         return fail(DG_ERR_ARG, "the moment limiter needs the Newtonian system and mrs_alpha >= 0");
+    int analytic = 0;
+    for (int a = 0; a < 3; ++a) {
+        if (d->bc[a] != DG_BC_PERIODIC && d->bc[a] != DG_BC_ANALYTIC) return fail(DG_ERR_ARG, "bc[%d] must be 0 or 1", a);
+        analytic |= d->bc[a];
+    }
+    if (d->exact != DG_EXACT_NONE && d->exact != DG_EXACT_ISENTROPIC_VORTEX) return fail(DG_ERR_ARG, "exact must be 0 or 1");
+    if (analytic && (d->system != 0 || d->exact != DG_EXACT_ISENTROPIC_VORTEX || d->limiter != DG_LIMITER_NONE))
+        return fail(DG_ERR_ARG, "analytic boundaries need the Newtonian system, the isentropic vortex and no limiter");
     if (d->precision != 0 && d->precision != 1) return fail(DG_ERR_ARG, "precision must be 0 (FP64) or 1 (mixed)");
     if (!(d->gamma > 1.0)) return fail(DG_ERR_ARG, "gamma must be > 1");
     if (!(d->beta > 0.0) || !(d->tvb_M >= 0.0)) return fail(DG_ERR_ARG, "beta must be > 0 and tvb_M >= 0");
@@ -498,6 +511,25 @@ dg_status dg_mesh_create(const dg_mesh_desc *d, dg_mesh **out)
     st = st ? st : cudaMalloc(&m->P, sizeof(double) * (size_t)E * 4 * m->nn);
     st = st ? st : cudaMalloc(&m->S, sizeof(double) * (size_t)E * 50);
     if (d->limiter == DG_LIMITER_MRS) st = st ? st : cudaMalloc(&m->mrsT, sizeof(double) * (size_t)E * 20);
+    st = st ? st : cudaMalloc(&m->t, sizeof(double));
+    if (st == cudaSuccess) st = cudaMemset(m->t, 0, sizeof(double));
+    for (int a = 0; a < 3; ++a) {
+        if (d->bc[a] != DG_BC_ANALYTIC) continue;
+        const long long cnt = (long long)d->K[(a + 1) % 3] * d->K[(a + 2) % 3];
+        m->gh.mask |= 1 << a;
+        m->gh.base[a][0] = m->nghost;
+        m->gh.base[a][1] = m->nghost + cnt;
+        m->nghost += 2 * cnt;
+    }
+    if (m->nghost) {
+        double *gU = nullptr, *gP = nullptr;
+        st = st ? st : cudaMalloc(&gU, sizeof(double) * (size_t)m->nghost * 5 * m->nn);
+        st = st ? st : cudaMalloc(&gP, sizeof(double) * (size_t)m->nghost * 4 * m->nn);
+        m->gh.U = gU;
+        m->gh.P = gP;
+        if (st == cudaSuccess) st = cudaMemset(gU, 0, sizeof(double) * (size_t)m->nghost * 5 * m->nn);
+        if (st == cudaSuccess) st = cudaMemset(gP, 0, sizeof(double) * (size_t)m->nghost * 4 * m->nn);
+    }
     st = st ? st : cudaMalloc(&m->unphys, (size_t)E);
     st = st ? st : cudaMalloc(&m->lam, sizeof(unsigned long long));
     st = st ? st : cudaMalloc(&m->dt, sizeof(double));
@@ -570,6 +602,7 @@ dg_status dg_rhs(dg_mesh *m, const double *U, double *dUdt, void *stream)
     if (dg_status s = check_mesh(m)) return s;
     if (!U || !dUdt || U == dUdt) return fail(DG_ERR_ARG, "U and dUdt must be distinct, non-NULL");
     cudaStream_t s = (cudaStream_t)stream;
+    if (m->gh.mask) DG_LAUNCH(m, s, PROF_OTHER, launch_exterior(m, 0.0, nullptr, 0.0, s));
     if (m->d.precision == DG_PRECISION_MIXED) {
         MixedArgs a = mixed_args(m);
         a.one.Us = U;
@@ -635,7 +668,9 @@ static dg_status rk3_step_mixed(dg_mesh *m, double *U, double dt, double cfl, do
     double *outs[3] = {m->W1, m->W2, U};
     const float ca[3] = {0.0f, 0.75f, (float)(1.0 / 3.0)};
     const float cb[3] = {1.0f, 0.25f, (float)(2.0 / 3.0)};
+    const double ct[3] = {0.0, 1.0, 0.5};  // stage times t + ct dt (analytic boundaries)
     for (int st = 0; st < 3; ++st) {
+        if (m->gh.mask) DG_LAUNCH(m, s, PROF_OTHER, launch_exterior(m, ct[st], a.one.dt_ptr, dt, s));
         a.one.Us = ins[st];
         a.one.out = outs[st];
         a.first = st == 0;
@@ -657,6 +692,7 @@ static dg_status rk3_step_mixed(dg_mesh *m, double *U, double dt, double cfl, do
         }
     }
     m->p_valid = carry ? 1 : 0;
+    if (m->gh.mask) DG_LAUNCH(m, s, PROF_OTHER, launch_time_add(m->t, a.one.dt_ptr, dt, s));
     if (dt_used) {
         if (cflmode) DG_CUDA(cudaMemcpyAsync(dt_used, m->dt, sizeof(double), cudaMemcpyDeviceToDevice, s));
         else DG_CUDA(launch_set(dt_used, dt, s));
@@ -688,11 +724,13 @@ dg_status dg_rk3_step(dg_mesh *m, double *U, double dt, double cfl, double *dt_u
     double *outs[3] = {m->W1, m->W2, U};
     const double ca[3] = {0.0, 0.75, 1.0 / 3.0};
     const double cb[3] = {1.0, 0.25, 2.0 / 3.0};
+    const double ct[3] = {0.0, 1.0, 0.5};  // stage times t + ct dt (analytic boundaries)
     for (int st = 0; st < 3; ++st) {
         // the SR fix of the previous stage's result is fused into its primitive pass
         DG_LAUNCH(m, s, PROF_PRIM,
                   launch_primitives(m, ins[st], m->P, sr && st > 0, ins[st], (cflmode && st == 0) ? m->lam : nullptr, s));
         if (cflmode && st == 0) DG_LAUNCH(m, s, PROF_DT, launch_dt(m, cfl, m->dt, s));
+        if (m->gh.mask) DG_LAUNCH(m, s, PROF_OTHER, launch_exterior(m, ct[st], a.dt_ptr, dt, s));
         a.Us = ins[st];
         a.Un = U;
         a.out = outs[st];
@@ -708,6 +746,7 @@ dg_status dg_rk3_step(dg_mesh *m, double *U, double dt, double cfl, double *dt_u
         }
     }
     if (sr) DG_LAUNCH(m, s, PROF_FIX, launch_fix(m, U, s));
+    if (m->gh.mask) DG_LAUNCH(m, s, PROF_OTHER, launch_time_add(m->t, a.dt_ptr, dt, s));
     if (dt_used) {
         if (cflmode) DG_CUDA(cudaMemcpyAsync(dt_used, m->dt, sizeof(double), cudaMemcpyDeviceToDevice, s));
         else DG_CUDA(launch_set(dt_used, dt, s));
@@ -744,9 +783,27 @@ dg_status dg_ab3_step(dg_mesh *m, double *U, double dt, unsigned char *troubled,
         if (dg_status st = dg_limit(m, U, troubled, stream)) return st;
         if (m->d.system == 1)
             if (dg_status st = dg_fix(m, U, stream)) return st;
+        if (m->gh.mask) DG_LAUNCH(m, s, PROF_OTHER, launch_time_add(m->t, nullptr, dt, s));
     }
     m->ab_n += 1;
     m->ab_dt = dt;
+    return DG_OK;
+}
+
+dg_status dg_mesh_set_time(dg_mesh *m, double t, void *stream)
+{
+    if (dg_status s = check_mesh(m)) return s;
+    DG_CUDA(launch_set(m->t, t, (cudaStream_t)stream));
+    return DG_OK;
+}
+
+dg_status dg_mesh_get_time(dg_mesh *m, double *t, void *stream)
+{
+    if (dg_status s = check_mesh(m)) return s;
+    if (!t) return fail(DG_ERR_ARG, "t is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    DG_CUDA(cudaMemcpyAsync(t, m->t, sizeof(double), cudaMemcpyDeviceToHost, s));
+    DG_CUDA(cudaStreamSynchronize(s));
     return DG_OK;
 }
 

@@ -267,6 +267,7 @@ dg_status dg_ensemble_create(dg_mesh *const *meshes, double *const *U, int count
         if (meshes[i]->device != dev) return set_error(DG_ERR_ARG, "every mesh must live on the current device");
         if (meshes[i]->d.precision != DG_PRECISION_MIXED)
             return set_error(DG_ERR_ARG, "the ensemble advances mixed-precision meshes only");
+        if (meshes[i]->gh.mask) return set_error(DG_ERR_ARG, "the ensemble advances periodic meshes only");
         if (meshes[i]->d.limiter == DG_LIMITER_MRS)
             return set_error(DG_ERR_ARG, "the ensemble runs the minmod limiters only, not the moment limiter");
         for (int j = 0; j < i; ++j)

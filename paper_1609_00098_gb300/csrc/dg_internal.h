@@ -22,6 +22,35 @@ __host__ __device__ inline long long elem_neighbour(long long e, const int K[3],
     return ec[0] + (long long)K[0] * (ec[1] + (long long)K[1] * ec[2]);
 }
 
+// Analytic outer boundaries: one ghost element per boundary face holds, on its
+// face nodes facing the mesh, the exterior state (U in state layout, P the FP64
+// primitives vx, vy, vz, p).  Ghosts of axis a, side s (0 lo, 1 hi) start at
+// base[a][s] and are ordered by the face's element coordinates (b, c) =
+// (a+1, a+2) mod 3, ec[b] fastest.
+struct Ghosts {
+    const double *U;
+    const double *P;
+    int mask;                // bit a: axis a analytic
+    long long base[3][2];
+};
+
+// Neighbour of e along axis a in direction s: the periodic neighbour (>= 0), or on
+// an analytic axis past the boundary -1 - (ghost index).
+__host__ __device__ inline long long elem_neighbour_bc(long long e, const int K[3], int a, int s, const Ghosts &G)
+{
+    int ec[3];
+    ec[0] = (int)(e % K[0]);
+    ec[1] = (int)((e / K[0]) % K[1]);
+    ec[2] = (int)(e / ((long long)K[0] * K[1]));
+    const int c = ec[a] + s;
+    if (((G.mask >> a) & 1) && (c < 0 || c >= K[a])) {
+        const int b = (a + 1) % 3, d = (a + 2) % 3;
+        return -1 - (G.base[a][s > 0 ? 1 : 0] + ec[b] + (long long)K[b] * ec[d]);
+    }
+    ec[a] = (c + K[a]) % K[a];
+    return ec[0] + (long long)K[0] * (ec[1] + (long long)K[1] * ec[2]);
+}
+
 // 1D LGL tables for one n, as passed by value to the kernels.
 struct Tables {
     double D[MAXN * MAXN];  // D[i*n+l] = ell_l'(xbar_i)
@@ -45,6 +74,7 @@ struct StageArgs {
     int first;             // first stage flag
     int mode;              // 0 write RHS, 1 stage update
     int K[3];
+    Ghosts gh;             // analytic boundaries (mask 0: periodic)
     double gamma;
     double g[3];           // 2/dx_a
     double lift0[3];       // (2/dx_a)/w_0
@@ -103,6 +133,9 @@ struct dg_mesh {
     long long ab_n;
     double ab_dt;
     double *mrsT;            // MRS limiter: per element U0, w0, w_max, w_min (20 doubles)
+    double *t;               // mesh time (device, 1 double)
+    dg::Ghosts gh;           // analytic boundaries: ghost exterior states (gh.mask 0: periodic)
+    long long nghost;
     // optional per-kernel timing (dg_profile_enable)
     int prof_on;
     void *prof;              // host-side event log, owned by dg_api.cu
@@ -119,6 +152,10 @@ cudaError_t launch_primitives(const dg_mesh *m, const double *U, double *P, int 
                               unsigned long long *lam, cudaStream_t s);
 cudaError_t launch_fix(const dg_mesh *m, double *U, cudaStream_t s);
 cudaError_t launch_mrs(const dg_mesh *m, double *U, unsigned char *troubled, cudaStream_t s);
+// Exterior states of the ghosts at time *t + ct * dt (dt = *dt_ptr if given).
+cudaError_t launch_exterior(const dg_mesh *m, double ct, const double *dt_ptr, double dt, cudaStream_t s);
+// *t += dt (dt = *dt_ptr if given).
+cudaError_t launch_time_add(double *t, const double *dt_ptr, double dt, cudaStream_t s);
 cudaError_t launch_ab3_combine(double *U, const double *L0, const double *L1, const double *L2, double dt,
                                long long count, cudaStream_t s);
 cudaError_t launch_dt(const dg_mesh *m, double cfl, double *dt, cudaStream_t s);

@@ -330,6 +330,7 @@ struct MeshSlot {
     const double *dt_ptr;
     double dt;
     int K[3];
+    Ghosts gh;              // analytic boundaries (Newtonian; mask 0: periodic)
     float g[3], lift0[3], liftN[3];
 };
 
@@ -566,10 +567,19 @@ __global__ void __launch_bounds__(StageShape<NP>::MAXT, StageShape<NP>::MIN_CTAS
         id[(ax + 1) % 3] = rem % NP;
         id[(ax + 2) % 3] = rem / NP;
         const int qn = id[0] + NP * (id[1] + NP * id[2]);
-        const long long en = elem_neighbour(e, sl.K, ax, side ? 1 : -1);
+        if (SYS == 0) {
+            // a negative neighbour is a ghost holding the analytic exterior state
+            const long long en = elem_neighbour_bc(e, sl.K, ax, side ? 1 : -1, sl.gh);
+            const double *src = en >= 0 ? sl.Us + en * 5 * NN : sl.gh.U + (-1 - en) * 5 * NN;
 #pragma unroll
-        for (int v = 0; v < 5; ++v) sFU[v * NF + f] = f64_to_f32(sl.Us[(en * 5 + v) * NN + qn]);
-        if (!GUESS) sFG[f] = sl.pin ? sl.pin[en * NN + qn] : -1.0f;
+            for (int v = 0; v < 5; ++v) sFU[v * NF + f] = f64_to_f32(src[v * NN + qn]);
+            sFG[f] = -1.0f;
+        } else {
+            const long long en = elem_neighbour(e, sl.K, ax, side ? 1 : -1);
+#pragma unroll
+            for (int v = 0; v < 5; ++v) sFU[v * NF + f] = f64_to_f32(sl.Us[(en * 5 + v) * NN + qn]);
+            if (!GUESS) sFG[f] = sl.pin ? sl.pin[en * NN + qn] : -1.0f;
+        }
     }
 
     if (own) {

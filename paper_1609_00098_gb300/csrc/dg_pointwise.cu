@@ -185,6 +185,81 @@ __global__ void __launch_bounds__(256) k_mrs_limit(double *U, const double *T, u
     }
 }
 
+// Exterior states of the analytic outer faces (Sec. 3.4): the isentropic vortex
+// (eq:isen_vortex, P = rho^gamma, par = beta, X0, Y0, U, V, W) at time
+// *t + ct dt and at the coordinates of the interior trace node (eq:AffineMap),
+// conserved and with its FP64 primitives, on ghost face node r of ghost gi.
+__global__ void __launch_bounds__(kThreads) k_exterior(double *gU, double *gP, Ghosts gh, long long total, int n,
+                                                     int K0, int K1, int K2, double lo0, double lo1, double lo2,
+                                                     double dx0, double dx1, double dx2, Tables T, double g,
+                                                     double b0, double b1, double b2, double b3, double b4,
+                                                     double b5, const double *t, double ct, const double *dt_ptr,
+                                                     double dt_val)
+{
+    const double pi = 3.14159265358979323846;
+    const int nf = n * n, nn = n * n * n;
+    const int K[3] = {K0, K1, K2};
+    const double lo[3] = {lo0, lo1, lo2}, dx[3] = {dx0, dx1, dx2};
+    const double dt = dt_ptr ? *dt_ptr : dt_val;
+    const double ts = *t + ct * dt;
+    for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < total;
+         w += (long long)gridDim.x * blockDim.x) {
+        const long long gi = w / nf;
+        const int r = (int)(w - gi * nf);
+        int a = -1, s = 0;
+        for (int aa = 0; aa < 3 && a < 0; ++aa) {
+            if (!((gh.mask >> aa) & 1)) continue;
+            const long long cnt = (long long)K[(aa + 1) % 3] * K[(aa + 2) % 3];
+            for (int ss = 0; ss < 2; ++ss)
+                if (gi >= gh.base[aa][ss] && gi < gh.base[aa][ss] + cnt) {
+                    a = aa;
+                    s = ss;
+                }
+        }
+        if (a < 0) continue;
+        const int b = (a + 1) % 3, c = (a + 2) % 3;
+        const long long fi = gi - gh.base[a][s];
+        int ec[3], id[3];
+        ec[b] = (int)(fi % K[b]);
+        ec[c] = (int)(fi / K[b]);
+        ec[a] = s ? K[a] - 1 : 0;
+        id[b] = r % n;
+        id[c] = r / n;
+        id[a] = s ? n - 1 : 0;
+        double x[3];
+        for (int d = 0; d < 3; ++d) {
+            const double ak = lo[d] + ec[d] * dx[d];
+            const double bk = ak + dx[d];
+            x[d] = ak + 0.5 * (1.0 + T.x[id[d]]) * (bk - ak);
+        }
+        const double beta = b0;
+        const double xt = x[0] - b1 - b3 * ts;
+        const double yt = x[1] - b2 - b4 * ts;
+        const double r2 = xt * xt + yt * yt;
+        const double rho = pow(1.0 - (g - 1.0) * beta * beta / (8.0 * g * pi * pi) * exp(1.0 - r2), 1.0 / (g - 1.0));
+        const double f = beta / (2.0 * pi) * exp(0.5 * (1.0 - r2));
+        const double vx = b3 - yt * f, vy = b4 + xt * f, vz = b5;
+        const double p = pow(rho, g);
+        const double v2 = vx * vx + vy * vy + vz * vz;
+        double u[5], P[4];
+        u[0] = rho;
+        u[1] = rho * vx;
+        u[2] = rho * vy;
+        u[3] = rho * vz;
+        u[4] = p / (g - 1.0) + 0.5 * rho * v2;
+        ne_primitives(g, u, P);
+        id[a] = s ? 0 : n - 1;  // the ghost's node facing the mesh
+        const int qn = id[0] + n * (id[1] + n * id[2]);
+        for (int v = 0; v < 5; ++v) gU[(gi * 5 + v) * nn + qn] = u[v];
+        for (int k = 0; k < 4; ++k) gP[(gi * 4 + k) * nn + qn] = P[k];
+    }
+}
+
+__global__ void k_time_add(double *t, const double *dt_ptr, double dt)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) *t = *t + (dt_ptr ? *dt_ptr : dt);
+}
+
 // U <- U + dt ((c0 L0 - c1 L1) + c2 L2), the third-order Adams-Bashforth
 // combination (Sec. 3.4) with c = (23, 16, 5)/12, in the oracle's operation order.
 __global__ void __launch_bounds__(kThreads) k_ab3(double *U, const double *L0, const double *L1, const double *L2,
@@ -337,6 +412,24 @@ cudaError_t launch_mrs(const dg_mesh *m, double *U, unsigned char *troubled, cud
     case 8: return launch_mrs_np<8>(m, U, troubled, s);
     default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_exterior(const dg_mesh *m, double ct, const double *dt_ptr, double dt, cudaStream_t s)
+{
+    if (!m->gh.mask) return cudaSuccess;
+    const long long total = m->nghost * m->d.n * m->d.n;
+    const double *b = m->d.exact_par;
+    k_exterior<<<grid_for(total, kThreads), kThreads, 0, s>>>(
+        const_cast<double *>(m->gh.U), const_cast<double *>(m->gh.P), m->gh, total, m->d.n, m->d.K[0], m->d.K[1],
+        m->d.K[2], m->d.lo[0], m->d.lo[1], m->d.lo[2], m->dx[0], m->dx[1], m->dx[2], m->T, m->d.gamma, b[0], b[1],
+        b[2], b[3], b[4], b[5], m->t, ct, dt_ptr, dt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_time_add(double *t, const double *dt_ptr, double dt, cudaStream_t s)
+{
+    k_time_add<<<1, 32, 0, s>>>(t, dt_ptr, dt);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_ab3_combine(double *U, const double *L0, const double *L1, const double *L2, double dt,

@@ -85,7 +85,8 @@ __global__ void __launch_bounds__(round_up32(NP *NP *NP)) k_stage_fp64(const Sta
         sW[t] = a.T.w[t];
         sRow1[t] = a.T.row1[t];
     }
-    if (t < 6) sNb[t] = elem_neighbour(e, a.K, t >> 1, (t & 1) ? 1 : -1);
+    if (t < 6) sNb[t] = SYS == 0 ? elem_neighbour_bc(e, a.K, t >> 1, (t & 1) ? 1 : -1, a.gh)
+                                 : elem_neighbour(e, a.K, t >> 1, (t & 1) ? 1 : -1);
 
     double u[5], P[4];
     if (t < NN) {
@@ -138,17 +139,24 @@ __global__ void __launch_bounds__(round_up32(NP *NP *NP)) k_stage_fp64(const Sta
             const int q = id[0] + NP * (id[1] + NP * id[2]);
             id[ax] = side ? 0 : NP - 1;
             const int qn = id[0] + NP * (id[1] + NP * id[2]);
-            const long long en = sNb[2 * ax + side];
+            long long en = sNb[2 * ax + side];
+            // a negative neighbour is a ghost holding the analytic exterior state
+            const double *Ub = a.Us, *Pb = a.P;
+            if (SYS == 0 && en < 0) {
+                Ub = a.gh.U;
+                Pb = a.gh.P;
+                en = -1 - en;
+            }
             double uo[5], Po[4], un[5], Pn[4];
 #pragma unroll
             for (int v = 0; v < 5; ++v) {
                 uo[v] = a.Us[(e * 5 + v) * NN + q];
-                un[v] = a.Us[(en * 5 + v) * NN + qn];
+                un[v] = Ub[(en * 5 + v) * NN + qn];
             }
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 Po[c] = a.P[(e * 4 + c) * NN + q];
-                Pn[c] = a.P[(en * 4 + c) * NN + qn];
+                Pn[c] = Pb[(en * 4 + c) * NN + qn];
             }
             double Fs[5], FL[5], FR[5];
             if (side) {
