@@ -248,8 +248,10 @@ dg_status dg_mesh_set_option(dg_mesh *mesh, int option, double value);
 /* Attach a learned-guess network to a mixed-precision SR mesh (net == NULL
  * detaches it).  With a network attached, every con2prim inside dg_rhs and
  * dg_rk3_step's stages starts its FP32 Newton from the network's guess, computed
- * in the stage kernel for the element's nodes and its neighbours' face nodes;
- * without one, it starts from the pressure of the previous pass (carried in
+ * in the stage kernel for the element's nodes and its neighbours' face nodes --
+ * except the first stage of a CFL step, whose input U^n the CFL pass has just
+ * solved with the network's guesses: it starts from those pressures.  Without a
+ * network, con2prim starts from the pressure of the previous pass (carried in
  * library scratch).  Newton stays the judge: the guess changes only the
  * iteration count and the result within the solver's stopping tolerance.  The
  * mesh does not own the network: it must stay alive while the mesh uses it, and

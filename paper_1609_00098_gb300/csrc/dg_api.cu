@@ -645,8 +645,11 @@ static dg_status rk3_step_mixed(dg_mesh *m, double *U, double dt, double cfl, do
     const bool sr = m->d.system == 1;
     const bool lim = m->d.limiter != 0;
     const bool cflmode = cfl > 0.0;
-    // with a learned guess attached, no pressures are carried between passes
+    // with a learned guess attached, no pressures are carried between steps; the
+    // CFL pass solves con2prim on U^n, the very state stage 1 starts from, and
+    // stage 1 takes those pressures instead of evaluating the network again
     const bool carry = sr && m->net == nullptr;
+    const bool reuse = sr && m->net != nullptr && cflmode;
     MixedArgs a = mixed_args(m);
     a.one.Un = U;
     a.one.dt = dt;
@@ -657,7 +660,8 @@ static dg_status rk3_step_mixed(dg_mesh *m, double *U, double dt, double cfl, do
     float *latest = (carry && m->p_valid) ? m->pbuf[m->pi] : nullptr;
     if (cflmode) {
         DG_CUDA(cudaMemsetAsync(m->lam, 0, sizeof(unsigned long long), s));
-        DG_LAUNCH(m, s, PROF_PRIM, launch_cfl_mixed(m, U, latest, carry ? m->pbuf[1 - m->pi] : nullptr, m->kappa_sw, s));
+        float *cfl_out = carry ? m->pbuf[1 - m->pi] : (reuse ? m->pbuf[0] : nullptr);
+        DG_LAUNCH(m, s, PROF_PRIM, launch_cfl_mixed(m, U, latest, cfl_out, m->kappa_sw, s));
         if (carry) {
             m->pi = 1 - m->pi;
             latest = m->pbuf[m->pi];
@@ -679,7 +683,13 @@ static dg_status rk3_step_mixed(dg_mesh *m, double *U, double dt, double cfl, do
         a.one.pin = latest;
         a.one.pout = carry ? m->pbuf[1 - m->pi] : nullptr;
         a.epb = m->epb > 0 ? m->epb : 1;
-        DG_LAUNCH(m, s, PROF_STAGE, launch_stage_mixed(m->d.n, m->d.system, m->d.flux, a, s));
+        MixedArgs as = a;
+        if (reuse && st == 0) {
+            as.netP = nullptr;
+            as.netW2 = nullptr;
+            as.one.pin = m->pbuf[0];
+        }
+        DG_LAUNCH(m, s, PROF_STAGE, launch_stage_mixed(m->d.n, m->d.system, m->d.flux, as, s));
         if (carry) {
             m->pi = 1 - m->pi;
             latest = m->pbuf[m->pi];
