@@ -132,14 +132,17 @@ def _init_state(pkg, mesh, torch):
     return mesh.from_prim(torch.from_numpy(prim).cuda())
 
 
-# DRAM bytes per k_stage_mixed launch (learned guess) on this workload (mean over
-# the three stages of a step), from the ncu capture summarised in
-# profiles/k_stage_mixed_sr_blast_16x16x16_n5.md.  Reported only while the
-# kernel's sources still hash to the value they had when it was taken.
-TRAFFIC_BYTES_PER_LAUNCH = 40891989.0
+# DRAM bytes per k_stage_mixed launch of the learned-guess steps on this workload
+# (mean over the three stages of a step: stage 1 runs the variant that starts from
+# the CFL pass's pressures, stages 2-3 the in-kernel network), from the ncu launch
+# list summarised in profiles/launches_sr_blast_16x16x16_n5.md.  Reported only
+# while the kernel's sources and the step's dispatch still hash to the value they
+# had when it was taken.
+TRAFFIC_BYTES_PER_LAUNCH = 40553849.0
 TRAFFIC_SOURCES = ("paper_1609_00098_gb300/csrc/dg_mixed.cuh", "paper_1609_00098_gb300/csrc/dg_physics.cuh",
-                   "paper_1609_00098_gb300/csrc/dg_internal.h", "paper_1609_00098_gb300/csrc/dg_c2p_net.cuh")
-TRAFFIC_SOURCES_SHA256 = "43d8b45b4e936f131d72911c2c29ca391818c0e26c0636e74a3a3efac83f188a"
+                   "paper_1609_00098_gb300/csrc/dg_internal.h", "paper_1609_00098_gb300/csrc/dg_c2p_net.cuh",
+                   "paper_1609_00098_gb300/csrc/dg_api.cu")
+TRAFFIC_SOURCES_SHA256 = "3aa08de43b7b2732aebe801bc603a15f28849f9b2ab45db9314a2801ac68a1b5"
 TRAFFIC_VARIANT = "learned"
 
 
