@@ -142,7 +142,7 @@ TRAFFIC_BYTES_PER_LAUNCH = 40553849.0
 TRAFFIC_SOURCES = ("paper_1609_00098_gb300/csrc/dg_mixed.cuh", "paper_1609_00098_gb300/csrc/dg_physics.cuh",
                    "paper_1609_00098_gb300/csrc/dg_internal.h", "paper_1609_00098_gb300/csrc/dg_c2p_net.cuh",
                    "paper_1609_00098_gb300/csrc/dg_api.cu")
-TRAFFIC_SOURCES_SHA256 = "3aa08de43b7b2732aebe801bc603a15f28849f9b2ab45db9314a2801ac68a1b5"
+TRAFFIC_SOURCES_SHA256 = "d1c47da7c4ff0164443bec1aa4f1c862de2081794a58c5c60ef01489ff0c57ec"
 TRAFFIC_VARIANT = "learned"
 
 

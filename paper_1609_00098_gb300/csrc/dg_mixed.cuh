@@ -702,8 +702,9 @@ __global__ void __launch_bounds__(StageShape<NP>::MAXT, StageShape<NP>::MIN_CTAS
         __syncthreads();
     }
 
-    // Surface terms (eq:411, lift of reading R1) for the face points of all three
-    // axes at once; the neighbour's face node is recovered here from its staged
+    // Surface terms (eq:411: each face taken once along +e_a, the lower element
+    // lifting -(2/dx_a)(F* - F_L)/w_N, the upper +(2/dx_a)(F* - F_R)/w_0) for the
+    // face points of all three axes at once; the neighbour's face node is recovered here from its staged
     // state.  Each axis's lift goes to its own array (over the flux arrays, no
     // longer read): within an axis a node lies on at most one face, so there are no
     // write conflicts, and the three are summed in a fixed order afterwards.

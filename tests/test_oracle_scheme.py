@@ -82,7 +82,7 @@ def test_ne_smooth_wave_exact_and_order():
         errs.append(m.norms(U, Uex)[1][0])
     orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
     assert orders[0] < orders[1] and orders[-1] > 3.5, (errs, orders)
-    # config-1 recipe: K=4, n=4, 10 CFL steps, error well below the wave amplitude
+    # smooth-wave recipe: K=4, n=4, 10 CFL steps, error well below the wave amplitude
     k = di.wave_numbers(1)
     m, U, Uex, t = _ne_wave(4, 4, steps=10, k=k)
     m2, U2, Uex2, _ = _ne_wave(8, 4, steps=20, k=k)
@@ -231,9 +231,10 @@ def test_ab3_conserves_and_matches_rk3_start():
 
 
 def test_ne_sod_table_roe_mrs_loose():
-    """tab:NE_sod, Roe-MRS rows (moment limiter of Sec. 3.3.3, reading R16):
-    errors within the band of the other Sod pins; order ~ 1 for alpha~ = 0.5 and
-    5 (the printed alpha~ = 50 row is itself irregular: 0.7, 0.5, 0.9)."""
+    """tab:NE_sod, Roe-MRS rows (moment limiter of Sec. 3.3.3, bounds from the
+    face neighbours' cell-average primitives): errors within the band of the other
+    Sod pins; order ~ 1 for alpha~ = 0.5 and 5 (the printed alpha~ = 50 row is
+    itself irregular: 0.7, 0.5, 0.9)."""
     rows = read_golden("ne_sod_roe_mrs.txt")
     for alpha in (0.5, 5.0, 50.0):
         sel = [(int(nx), ref) for n, a, nx, ref in rows if a == alpha]
