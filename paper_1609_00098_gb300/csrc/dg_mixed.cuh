@@ -224,9 +224,9 @@ __device__ __forceinline__ void ne_primitives32(float g, const float u[5], float
     P[4] = 1.0f;
 }
 
-// FP32 SR con2prim: the safeguarded Newton of the FP64 path in FP32, stopping
-// when the step is below 2^-21 p or the residual is at the FP32 noise level of
-// its terms.  Returns 0 ok, 1 unphysical in FP32, 2 no convergence; kappa gets
+// FP32 SR con2prim: the safeguarded Newton of the FP64 path in FP32 (with
+// geometric bisection across wide brackets), stopping when the step is below
+// 2^-21 p or the residual is at the FP32 noise level of its terms.  Returns 0 ok, 1 unphysical in FP32, 2 no convergence; kappa gets
 // tau/(rho eps), the amplification of input rounding into p.
 __device__ __forceinline__ int sr_con2prim32(float g, const float u[5], float guess, float P[NPRIM], float &kappa)
 {
@@ -252,8 +252,12 @@ __device__ __forceinline__ int sr_con2prim32(float g, const float u[5], float gu
         if (fabsf(f) <= noise) { status = 0; break; }
         if (f > 0.0f) { phi = p; hi_moved = true; } else { plo = p; lo_moved = true; }
         float pn = p - f / df;
+        // Newton steps that leave the bracket become bisections: geometric while the
+        // bracket spans more than a factor 4 (a cold state's pressure can sit many
+        // decades below the bracket's top, (g-1) tau, where halving needs ~20 steps),
+        // arithmetic below that
         if (!((pn > plo && pn < phi) || (pn == phi && !hi_moved) || (pn == plo && !lo_moved)))
-            pn = 0.5f * (plo + phi);
+            pn = phi > 4.0f * plo ? sqrtf(fmaxf(plo, 0x1p-40f * phi) * phi) : 0.5f * (plo + phi);
         const float dp = fabsf(pn - p);
         p = pn;
         if (dp <= 4.8e-7f * p || !(phi > plo)) { status = 0; break; }
@@ -271,7 +275,7 @@ __device__ __forceinline__ int sr_con2prim32(float g, const float u[5], float gu
 
 // FP64 Newton on the pressure from a starting value p0 (the FP32 result, or the
 // standard guess when p0 < 0), on the FP64 conserved state u: the bracket and
-// step rules of the FP64 con2prim, stopping when the step is below 2^-40 p or
+// step rules of sr_con2prim32 in FP64, stopping when the step is below 2^-40 p or
 // the residual is at the FP64 rounding level of its terms.  That level is
 // reached in a few steps even where tau/(rho eps) is huge, so the cost stays
 // bounded on cold states at the conserved-fix bound.
@@ -300,7 +304,7 @@ __device__ __forceinline__ int sr_polish64(double g, const double u[5], double p
         if (f > 0.0) { phi = p; hi_moved = true; } else { plo = p; lo_moved = true; }
         double pn = p - f / df;
         if (!((pn > plo && pn < phi) || (pn == phi && !hi_moved) || (pn == plo && !lo_moved)))
-            pn = 0.5 * (plo + phi);
+            pn = phi > 4.0 * plo ? sqrt(fmax(plo, 0x1p-40 * phi) * phi) : 0.5 * (plo + phi);
         const double dp = fabs(pn - p);
         p = pn;
         if (dp <= 0x1p-40 * p || !(phi > plo)) { status = 0; break; }
@@ -475,10 +479,27 @@ struct MixedSmem {
     static constexpr size_t FLAG = NB + sizeof(long long) * 7;      // 6 neighbours + element index
     static constexpr size_t SLOT = (FLAG + 2 * sizeof(int) + 15) / 16 * 16;
     static constexpr size_t ELEM = (SLOT + sizeof(MeshSlot) + 15) / 16 * 16;
-    __host__ __device__ static size_t net(int epb) { return ELEM * epb; }
-    __host__ __device__ static size_t feat(int epb) { return net(epb) + (sizeof(NetWeightsSmem) + 15) / 16 * 16; }
-    __host__ __device__ static size_t guess(int epb) { return feat(epb) + sizeof(float) * 6 * NN * epb; }
-    __host__ __device__ static size_t total(int epb, bool learned) { return learned ? guess(epb) + sizeof(float) * NN * epb : ELEM * epb; }
+    // Learned guess: the network's weights (one copy per CTA), and per element the
+    // features [NN][6] and guesses [NN] of its nodes.  They are dead once every
+    // thread holds its guess, before the element's MAIN region is first written,
+    // so where MAIN has room (n >= 5) they live inside it: the weights, element 0's
+    // features and guesses in element 0's MAIN, element s's in element s's.
+    // Otherwise they follow the elements.
+    static constexpr size_t NET_BYTES = (sizeof(NetWeightsSmem) + 15) / 16 * 16;
+    static constexpr size_t FEAT_BYTES = sizeof(float) * 6 * NN;
+    static constexpr size_t GUESS_BYTES = sizeof(float) * NN;
+    static constexpr bool NET_IN_MAIN = NET_BYTES + FEAT_BYTES + GUESS_BYTES <= MAIN;
+    __host__ __device__ static size_t net(int epb) { return NET_IN_MAIN ? 0 : ELEM * epb; }
+    __host__ __device__ static size_t feat(int epb, int s)
+    {
+        return NET_IN_MAIN ? ELEM * s + (s == 0 ? NET_BYTES : 0)
+                           : ELEM * epb + NET_BYTES + (FEAT_BYTES + GUESS_BYTES) * s;
+    }
+    __host__ __device__ static size_t guess(int epb, int s) { return feat(epb, s) + FEAT_BYTES; }
+    __host__ __device__ static size_t total(int epb, bool learned)
+    {
+        return learned && !NET_IN_MAIN ? ELEM * epb + NET_BYTES + (FEAT_BYTES + GUESS_BYTES) * epb : ELEM * epb;
+    }
 };
 
 // FP32 screen of the bounds of the conserved fix (Sec. 2.1.4) and of physicality;
@@ -534,31 +555,9 @@ __global__ void __launch_bounds__(StageShape<NP>::MAXT, StageShape<NP>::MIN_CTAS
     const bool own = live && t < NN;  // this thread holds node t of a live element
     unsigned errs = 0;
 
-    // Learned con2prim guesses for the CTA's nodes (rows sub * NN + t; the
-    // network runs on the tensor cores over 16-row tiles).  The neighbours' face
-    // nodes in the face loop start from the pressure of this element's node at
-    // the same point (the other side of the trace), solved by then.
-    float *sGuess = nullptr;
-    if (GUESS) {
-        NetWeightsSmem &W = *reinterpret_cast<NetWeightsSmem *>(smem_mixed + SM::net(a.epb));
-        float(*sFeat)[6] = reinterpret_cast<float(*)[6]>(smem_mixed + SM::feat(a.epb));
-        sGuess = reinterpret_cast<float *>(smem_mixed + SM::guess(a.epb));
-        net_stage_weights(W, a.netP, a.netW2);
-        if (t < NN) {
-            float u[5] = {1.0f, 0.0f, 0.0f, 0.0f, 1.0f};
-            if (own)
-#pragma unroll
-                for (int v = 0; v < 5; ++v) u[v] = f64_to_f32(sl.Us[(e * 5 + v) * NN + t]);
-            net_features(u, a.net_sc, sFeat[sub * NN + t]);
-        }
-        __syncthreads();
-        net_guess_rows(W, sFeat, sGuess, NN * a.epb, a.gamma, a.net_sc);
-        __syncthreads();
-        sGuess += sub * NN;
-    }
-
     // Neighbour face nodes of all three axes (point f = 2 NP^2 ax + NP^2 side + rem):
-    // their FP32 states and guesses, staged while the element's own nodes load.
+    // their FP32 states and guesses, staged first so that the loads overlap the
+    // network's phase and the element's own loads.
     for (int f = t; live && f < NF; f += TPE) {
         const int ax = f / (2 * NP * NP), fpa = f % (2 * NP * NP);
         const int side = fpa / (NP * NP), rem = fpa % (NP * NP);
@@ -582,6 +581,30 @@ __global__ void __launch_bounds__(StageShape<NP>::MAXT, StageShape<NP>::MIN_CTAS
         }
     }
 
+    // Learned con2prim guesses for the CTA's nodes (the network runs on the tensor
+    // cores over 16-row tiles, all warps of the CTA on each element's rows in turn).
+    // The neighbours' face nodes in the face loop start from the pressure of this
+    // element's node at the same point (the other side of the trace), solved by then.
+    float guess_net = -1.0f;
+    if (GUESS) {
+        NetWeightsSmem &W = *reinterpret_cast<NetWeightsSmem *>(smem_mixed + SM::net(a.epb));
+        net_stage_weights(W, a.netP, a.netW2);
+        if (t < NN) {
+            float u[5] = {1.0f, 0.0f, 0.0f, 0.0f, 1.0f};
+            if (own)
+#pragma unroll
+                for (int v = 0; v < 5; ++v) u[v] = f64_to_f32(sl.Us[(e * 5 + v) * NN + t]);
+            net_features(u, a.net_sc, reinterpret_cast<float(*)[6]>(smem_mixed + SM::feat(a.epb, sub))[t]);
+        }
+        __syncthreads();
+        for (int s2 = 0; s2 < a.epb; ++s2)
+            net_guess_rows(W, reinterpret_cast<const float(*)[6]>(smem_mixed + SM::feat(a.epb, s2)),
+                           reinterpret_cast<float *>(smem_mixed + SM::guess(a.epb, s2)), NN, a.gamma, a.net_sc);
+        __syncthreads();
+        if (t < NN) guess_net = reinterpret_cast<const float *>(smem_mixed + SM::guess(a.epb, sub))[t];
+        __syncthreads();  // the network's regions are dead from here on
+    }
+
     if (own) {
         float u[5];
 #pragma unroll
@@ -590,7 +613,7 @@ __global__ void __launch_bounds__(StageShape<NP>::MAXT, StageShape<NP>::MIN_CTAS
             sU[v * NN + t] = u[v];
         }
         float P[NPRIM];
-        const float guess = GUESS ? sGuess[t] : (sl.pin ? sl.pin[e * NN + t] : -1.0f);
+        const float guess = GUESS ? guess_net : (sl.pin ? sl.pin[e * NN + t] : -1.0f);
         if (SYS == 0) ne_primitives32(a.gamma, u, P);
         else errs |= sr_prims_mixed(a.gamma, a.gamma_d, a.kappa_sw, a.d_atm, a.tau_atm, u,
                                     sl.Us + e * 5 * NN + t, NN, guess, P);
@@ -704,10 +727,11 @@ __global__ void __launch_bounds__(StageShape<NP>::MAXT, StageShape<NP>::MIN_CTAS
 
     // Surface terms (eq:411: each face taken once along +e_a, the lower element
     // lifting -(2/dx_a)(F* - F_L)/w_N, the upper +(2/dx_a)(F* - F_R)/w_0) for the
-    // face points of all three axes at once; the neighbour's face node is recovered here from its staged
-    // state.  Each axis's lift goes to its own array (over the flux arrays, no
-    // longer read): within an axis a node lies on at most one face, so there are no
-    // write conflicts, and the three are summed in a fixed order afterwards.
+    // face points of all three axes at once; the neighbour's face node is
+    // recovered here from its staged state.  Each axis's lift goes to its own
+    // array (over the flux arrays, no longer read): within an axis a node lies on
+    // at most one face, so there are no write conflicts, and the three are summed
+    // in a fixed order afterwards.
     float *sA = sF;  // [3][5][NN]
     if (own)
 #pragma unroll
