@@ -323,9 +323,9 @@ MixedArgs mixed_args(const dg_mesh *m)
     a.d_atm = m->d.d_atm;
     a.tau_atm = m->d.tau_atm;
     if (m->net && m->d.system == 1) {
-        const void *w2 = nullptr;
-        net_device_view(m->net, &a.netP, &w2, a.net_sc);
-        a.netW2 = static_cast<const __nv_bfloat16 *>(w2);
+        const void *img = nullptr;
+        net_device_view(m->net, &img, a.net_sc);
+        a.netImg = static_cast<const NetWeightsSmem *>(img);
     }
     for (int i = 0; i < MAXN * MAXN; ++i) a.D32[i] = (float)m->T.D[i];
     for (int i = 0; i < MAXN; ++i) {
@@ -685,8 +685,7 @@ static dg_status rk3_step_mixed(dg_mesh *m, double *U, double dt, double cfl, do
         a.epb = m->epb > 0 ? m->epb : 1;
         MixedArgs as = a;
         if (reuse && st == 0) {
-            as.netP = nullptr;
-            as.netW2 = nullptr;
+            as.netImg = nullptr;
             as.one.pin = m->pbuf[0];
         }
         DG_LAUNCH(m, s, PROF_STAGE, launch_stage_mixed(m->d.n, m->d.system, m->d.flux, as, s));

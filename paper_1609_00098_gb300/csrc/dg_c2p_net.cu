@@ -384,6 +384,26 @@ __global__ void k_net_bf16(const float *P, __nv_bfloat16 *W2b, __nv_bfloat16 *W2
     W2tb[i * 64 + j] = __float2bfloat16_rn(P[OFF_W2 + k]);
 }
 
+// The shared-memory image of the weights for in-kernel inference (NetWeightsSmem)
+// from the FP32 parameters: W2 in BF16 with padded rows; W1, b1, W2, b2 halved.
+__global__ void k_net_image(const float *P, NetWeightsSmem *img)
+{
+    for (int k = threadIdx.x; k < 64 * NET_W2_LD; k += blockDim.x) {
+        const int j = k / NET_W2_LD, i = k % NET_W2_LD;
+        img->W2h[j][i] = __float2bfloat16_rn(i < 64 ? 0.5f * P[OFF_W2 + j * 64 + i] : 0.0f);
+    }
+    for (int j = threadIdx.x; j < 64; j += blockDim.x) {
+        img->W1b1h[j] = make_float4(0.5f * P[OFF_W1 + 3 * j], 0.5f * P[OFF_W1 + 3 * j + 1],
+                                    0.5f * P[OFF_W1 + 3 * j + 2], 0.5f * P[OFF_B1 + j]);
+        img->b2h[j] = 0.5f * P[OFF_B2 + j];
+        img->W3[j] = P[OFF_W3 + j];
+    }
+    if (threadIdx.x == 0) {
+        img->b3 = P[OFF_B3];
+        img->pad[0] = img->pad[1] = img->pad[2] = 0.0f;
+    }
+}
+
 }  // namespace dg
 
 // ---------------------------------------------------------------------------
@@ -392,6 +412,7 @@ struct dg_c2p_net {
     int device;
     float *P, *m, *v, *grad, *partial;
     __nv_bfloat16 *W2b, *W2tb;
+    dg::NetWeightsSmem *img;  // weights for in-kernel inference
     long long partial_blocks;
     long long step;
     float sc[6];
@@ -443,10 +464,9 @@ cudaError_t net_launch_tile(dg_c2p_net *n, bool train, const double *cons, const
 
 namespace dg {
 
-void net_device_view(const dg_c2p_net *n, const float **P, const void **W2b, float sc[6])
+void net_device_view(const dg_c2p_net *n, const void **img, float sc[6])
 {
-    *P = n->P;
-    *W2b = n->W2b;
+    *img = n->img;
     for (int i = 0; i < 6; ++i) sc[i] = n->sc[i];
 }
 
@@ -479,11 +499,13 @@ dg_status dg_c2p_net_create(const float *params, const double *scales, dg_c2p_ne
     e = e ? e : cudaMalloc(&n->grad, sizeof(float) * NET_PARAMS);
     e = e ? e : cudaMalloc(&n->W2b, sizeof(__nv_bfloat16) * 4096);
     e = e ? e : cudaMalloc(&n->W2tb, sizeof(__nv_bfloat16) * 4096);
+    e = e ? e : cudaMalloc(&n->img, sizeof(NetWeightsSmem));
     if (e == cudaSuccess) e = cudaMemcpy(n->P, params, sizeof(float) * NET_PARAMS, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(n->m, 0, sizeof(float) * NET_PARAMS);
     if (e == cudaSuccess) e = cudaMemset(n->v, 0, sizeof(float) * NET_PARAMS);
     if (e == cudaSuccess) {
         k_net_bf16<<<16, 256>>>(n->P, n->W2b, n->W2tb);
+        k_net_image<<<1, 256>>>(n->P, n->img);
         e = cudaDeviceSynchronize();
     }
     if (e != cudaSuccess) {
@@ -505,6 +527,7 @@ void dg_c2p_net_destroy(dg_c2p_net *n)
     cudaFree(n->partial);
     cudaFree(n->W2b);
     cudaFree(n->W2tb);
+    cudaFree(n->img);
     delete n;
 }
 
@@ -577,6 +600,8 @@ dg_status dg_c2p_net_train(dg_c2p_net *n, long long count, const double *cons, c
             NET_CUDA(cudaGetLastError());
         }
     }
+    k_net_image<<<1, 256, 0, s>>>(n->P, n->img);
+    NET_CUDA(cudaGetLastError());
     return DG_OK;
 }
 

@@ -74,15 +74,26 @@ __device__ __forceinline__ void load_b(uint32_t b[2], const __nv_bfloat16 *Bt, i
     b[1] = *reinterpret_cast<const uint32_t *>(Bt + (n0 + g) * ld + k0 + 2 * tq + 8);
 }
 
-// SiLU for in-kernel inference: z sigma(z) = z (1 + tanh(z/2)) / 2 with the
-// hardware tanh approximation (one MUFU operation instead of an exponential and
-// a reciprocal; relative error ~2^-11, far below the BF16 rounding of layer 2).
-__device__ __forceinline__ float silu_fast(float z)
+// In-kernel inference evaluates SiLU on halved pre-activations z' = z/2 (the image
+// below stores W1, b1, W2, b2 halved, an exact scaling): silu(z) = z sigma(z) =
+// z' (1 + tanh z'), one hardware tanh and one FMA.  tanh.approx has a relative
+// error near 2^-11, far below the BF16 rounding of layer 2's inputs.
+__device__ __forceinline__ float silu_half(float zh)
 {
     float t;
-    asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(0.5f * z));
-    const float hz = 0.5f * z;
-    return fmaf(hz, t, hz);
+    asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(zh));
+    return fmaf(zh, t, zh);
+}
+
+// The same for two values, packed as the BF16 pair that layer 2 takes as its A
+// operand: (lo, hi) -> BF16x2 of (silu(2 lo), silu(2 hi)), tanh and FMA in BF16x2.
+__device__ __forceinline__ uint32_t silu_half_bf16x2(float lo, float hi)
+{
+    uint32_t z, t, h;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(z) : "f"(hi), "f"(lo));
+    asm("tanh.approx.bf16x2 %0, %1;" : "=r"(t) : "r"(z));
+    asm("fma.rn.bf16x2 %0, %1, %2, %1;" : "=r"(h) : "r"(z), "r"(t));
+    return h;
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
@@ -91,113 +102,148 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
     return *reinterpret_cast<const uint32_t *>(&v);
 }
 
-// Network weights staged in shared memory for in-kernel inference.  W2's rows
-// are padded to 72 BF16 (144 bytes): the eight rows a B-fragment load touches then
-// fall in different banks.
-constexpr int NET_W2_LD = 72;
-struct NetWeightsSmem {
-    __nv_bfloat16 W2[64][NET_W2_LD];  // [j][i]: the B^T operand of layer 2
-    float W1[64][3], b1[64], b2[64], W3[64], b3;
-};
-
-// Stage the weights (all threads of the CTA take part; the caller synchronises).
-// W2 moves as 16-byte vectors, all loads issued before the stores, so a CTA
-// waits about one L2 round trip rather than one per element.
-__device__ __forceinline__ void net_stage_weights(NetWeightsSmem &W, const float *P, const __nv_bfloat16 *W2b)
+// Four 8 x 8 BF16 matrices from shared memory; this lane gives the address of one
+// row (lanes 8m..8m+7: the rows of matrix m).
+__device__ __forceinline__ void ldmatrix_x4(uint32_t r[4], const void *row)
 {
-    constexpr int NV = 64 * 64 * 2 / 16;  // uint4 vectors of W2, 8 per row
-    const uint4 *src = reinterpret_cast<const uint4 *>(W2b);
-    for (int k0 = 0; k0 < NV; k0 += 4 * (int)blockDim.x) {
-        uint4 r[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int k = k0 + j * blockDim.x + threadIdx.x;
-            if (k < NV) r[j] = __ldg(src + k);
-        }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int k = k0 + j * blockDim.x + threadIdx.x;
-            if (k < NV) *reinterpret_cast<uint4 *>(&W.W2[k >> 3][(k & 7) * 8]) = r[j];
-        }
-    }
-    for (int k = threadIdx.x; k < 192 + 64; k += blockDim.x) {
-        const float w1 = __ldg(P + OFF_W1 + k);  // W1 and b1 are contiguous
-        if (k < 192) (&W.W1[0][0])[k] = w1;
-        else W.b1[k - 192] = w1;
-    }
-    for (int k = threadIdx.x; k < 64; k += blockDim.x) {
-        W.b2[k] = __ldg(P + OFF_B2 + k);
-        W.W3[k] = __ldg(P + OFF_W3 + k);
-    }
-    if (threadIdx.x == 0) W.b3 = __ldg(P + OFF_B3);
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(row);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a)
+                 : "memory");
 }
 
+// Network weights for in-kernel inference, laid out as they sit in shared memory.
+// The library keeps this image in device memory (refreshed whenever the
+// parameters change) and each CTA fetches it with one bulk asynchronous copy.
+// W2's rows are padded to 72 BF16 (144 bytes): the eight rows an ldmatrix touches
+// then fall in different banks.  W1, b1, W2, b2 are stored halved (see silu_half).
+constexpr int NET_W2_LD = 72;
+struct NetWeightsSmem {
+    __nv_bfloat16 W2h[64][NET_W2_LD];  // W2 / 2, [j][i]: the B^T operand of layer 2
+    float4 W1b1h[64];                   // (W1[j][0], W1[j][1], W1[j][2], b1[j]) / 2
+    float b2h[64];                      // b2 / 2
+    float W3[64];
+    float b3, pad[3];
+};
+static_assert(sizeof(NetWeightsSmem) % 16 == 0, "bulk copies move multiples of 16 bytes");
+
+// The bulk copy: one thread initialises the barrier before a __syncthreads, one
+// thread issues the copy after it, and every thread waits before reading.
+__device__ __forceinline__ void net_bar_init(uint64_t *bar)
+{
+    const uint32_t b = (uint32_t)__cvta_generic_to_shared(bar);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void net_copy_issue(NetWeightsSmem *dst, const NetWeightsSmem *src, uint64_t *bar)
+{
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    const uint32_t b = (uint32_t)__cvta_generic_to_shared(bar);
+    constexpr uint32_t bytes = sizeof(NetWeightsSmem);
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(b),
+                 "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(d),
+                 "l"(src), "r"(bytes), "r"(b)
+                 : "memory");
+}
+
+// Poll the barrier's first phase at most `limit` times; false if the copy has not
+// landed by then.
+__device__ __forceinline__ bool net_copy_wait(uint64_t *bar, int limit)
+{
+    const uint32_t b = (uint32_t)__cvta_generic_to_shared(bar);
+    for (int i = 0; i < limit; ++i) {
+        uint32_t ok;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(ok)
+                     : "r"(b)
+                     : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+constexpr int NET_COPY_POLLS = 1 << 20;
+
 // Features and bracket data of one SR state, FP32: f = (x1, x2, x3, E, s, tau).
+// log10 x = log2 x * log10 2 with the hardware log2 (relative error ~2^-22).
 __device__ __forceinline__ void net_features(const float u[5], const float sc[6], float f[6])
 {
     const float D = u[0], tau = u[4];
     const float E = tau + D;
     const float smag = sqrtf(u[1] * u[1] + u[2] * u[2] + u[3] * u[3]);
-    f[0] = 2.0f * (log10f(tau / D) - sc[0]) / (sc[1] - sc[0]) - 1.0f;
+    constexpr float LOG10_2 = 0.30102999566398120f;
+    f[0] = 2.0f * (__log2f(tau / D) * LOG10_2 - sc[0]) / (sc[1] - sc[0]) - 1.0f;
     f[1] = 2.0f * smag / E - 1.0f;
-    f[2] = 2.0f * (log10f(D) - sc[2]) / (sc[3] - sc[2]) - 1.0f;
+    f[2] = 2.0f * (__log2f(D) * LOG10_2 - sc[2]) / (sc[3] - sc[2]) - 1.0f;
     f[3] = E;
     f[4] = smag;
     f[5] = tau;
 }
 
+// Halved layer-1 pre-activation of hidden unit w for features x.
+__device__ __forceinline__ float net_z1h(const float4 w, float x0, float x1, float x2)
+{
+    return fmaf(w.z, x2, fmaf(w.y, x1, fmaf(w.x, x0, w.w)));
+}
+
 // Pressure guesses for `rows` states whose features sF[r][6] (net_features) sit in
 // shared memory; writes sG[r].  Each warp takes 16-row tiles: layer 1 is evaluated
-// straight into the A fragments of layer 2 (every hidden value belongs to exactly
-// one lane), layer 2 runs as mma.sync m16n8k16 (BF16 in, FP32 accumulate), and
-// layer 3 is a per-row dot product reduced over the four lanes of a row.  States
-// with non-finite features (unphysical or non-positive D, tau) get -1, which
-// con2prim reads as "no guess".
+// straight into the BF16 A fragments of layer 2 (every hidden value belongs to
+// exactly one lane), layer 2 runs as mma.sync m16n8k16 (BF16 in, FP32 accumulate,
+// starting from the bias) with its B fragments loaded by ldmatrix, and layer 3 is a
+// per-row dot product reduced over the four lanes of a row.  States with non-finite
+// features (unphysical or non-positive D, tau) get -1, which con2prim reads as "no
+// guess".
 __device__ __forceinline__ void net_guess_rows(const NetWeightsSmem &W, const float (*sF)[6], float *sG, int rows,
                                                float gamma, const float sc[6])
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int g = lane >> 2, tq = lane & 3;
+    // this lane's ldmatrix row within a 16 (n) x 16 (k) block of W2h: matrices
+    // (n 0-7, k 0-7), (n 0-7, k 8-15), (n 8-15, k 0-7), (n 8-15, k 8-15)
+    const int lr_n = (lane & 7) + 8 * (lane >> 4), lr_k = 8 * ((lane >> 3) & 1);
     for (int r0 = warp * 16; r0 < rows; r0 += nwarps * 16) {
         const int ra = min(r0 + g, rows - 1), rb = min(r0 + g + 8, rows - 1);
         const float xa0 = sF[ra][0], xa1 = sF[ra][1], xa2 = sF[ra][2];
         const float xb0 = sF[rb][0], xb1 = sF[rb][1], xb2 = sF[rb][2];
         float acc[8][4];
 #pragma unroll
-        for (int nt = 0; nt < 8; ++nt)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) acc[nt][c] = 0.0f;
+        for (int nt = 0; nt < 8; ++nt) {
+            const float2 b = *reinterpret_cast<const float2 *>(&W.b2h[nt * 8 + 2 * tq]);
+            acc[nt][0] = b.x;
+            acc[nt][1] = b.y;
+            acc[nt][2] = b.x;
+            acc[nt][3] = b.y;
+        }
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk) {
-            float h[2][4];  // [row a/b][col 2tq, 2tq+1, 2tq+8, 2tq+9]
+            const int c0 = kk * 16 + 2 * tq;
+            const float4 w0 = W.W1b1h[c0], w1 = W.W1b1h[c0 + 1], w8 = W.W1b1h[c0 + 8], w9 = W.W1b1h[c0 + 9];
+            uint32_t af[4];  // rows (g, g+8) x hidden units (c0, c0+1 | c0+8, c0+9)
+            af[0] = silu_half_bf16x2(net_z1h(w0, xa0, xa1, xa2), net_z1h(w1, xa0, xa1, xa2));
+            af[1] = silu_half_bf16x2(net_z1h(w0, xb0, xb1, xb2), net_z1h(w1, xb0, xb1, xb2));
+            af[2] = silu_half_bf16x2(net_z1h(w8, xa0, xa1, xa2), net_z1h(w9, xa0, xa1, xa2));
+            af[3] = silu_half_bf16x2(net_z1h(w8, xb0, xb1, xb2), net_z1h(w9, xb0, xb1, xb2));
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int j = kk * 16 + 2 * tq + (q & 1) + 8 * (q >> 1);
-                h[0][q] = silu_fast(W.W1[j][0] * xa0 + W.W1[j][1] * xa1 + W.W1[j][2] * xa2 + W.b1[j]);
-                h[1][q] = silu_fast(W.W1[j][0] * xb0 + W.W1[j][1] * xb1 + W.W1[j][2] * xb2 + W.b1[j]);
-            }
-            uint32_t af[4];
-            af[0] = pack_bf16(h[0][0], h[0][1]);
-            af[1] = pack_bf16(h[1][0], h[1][1]);
-            af[2] = pack_bf16(h[0][2], h[0][3]);
-            af[3] = pack_bf16(h[1][2], h[1][3]);
-#pragma unroll
-            for (int nt = 0; nt < 8; ++nt) {
-                uint32_t bf[2];
-                load_b(bf, &W.W2[0][0], NET_W2_LD, kk * 16, nt * 8, lane);
-                mma_bf16(acc[nt], af, bf);
+            for (int nt2 = 0; nt2 < 4; ++nt2) {
+                uint32_t bq[4];
+                ldmatrix_x4(bq, &W.W2h[nt2 * 16 + lr_n][kk * 16 + lr_k]);
+                mma_bf16(acc[2 * nt2], af, bq);
+                mma_bf16(acc[2 * nt2 + 1], af, bq + 2);
             }
         }
         float ya = 0.0f, yb = 0.0f;
 #pragma unroll
-        for (int nt = 0; nt < 8; ++nt)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const int col = nt * 8 + 2 * tq + (c & 1);
-                const float v = W.W3[col] * silu_fast(acc[nt][c] + W.b2[col]);
-                if (c < 2) ya += v;
-                else yb += v;
-            }
+        for (int nt = 0; nt < 8; ++nt) {
+            const float2 w3 = *reinterpret_cast<const float2 *>(&W.W3[nt * 8 + 2 * tq]);
+            ya = fmaf(w3.x, silu_half(acc[nt][0]), ya);
+            ya = fmaf(w3.y, silu_half(acc[nt][1]), ya);
+            yb = fmaf(w3.x, silu_half(acc[nt][2]), yb);
+            yb = fmaf(w3.y, silu_half(acc[nt][3]), yb);
+        }
         ya += __shfl_xor_sync(0xffffffffu, ya, 1);
         ya += __shfl_xor_sync(0xffffffffu, ya, 2);
         yb += __shfl_xor_sync(0xffffffffu, yb, 1);

@@ -242,8 +242,7 @@ cudaError_t launch_step(dg_ensemble *en, double cfl, bool first, cudaStream_t s)
         for (EnsGroup &g : en->groups) {
             MixedArgs a = stage_args_for(g, (first && st == 0) ? g.d_stage_first : g.d_stage[st], st);
             if (g.reuse && st == 0) {  // stage 1 starts from the CFL pass's pressures
-                a.netP = nullptr;
-                a.netW2 = nullptr;
+                a.netImg = nullptr;
             }
             e = launch_stage_mixed(g.n, g.system, g.flux, a, s);
             if (e != cudaSuccess) return e;

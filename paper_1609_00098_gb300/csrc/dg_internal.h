@@ -180,8 +180,9 @@ MeshSlot mixed_slot(const dg_mesh *m);
 LimitMixedArgs limit_mixed_args(const dg_mesh *m, double *U, unsigned char *troubled);
 LimitSlot limit_slot(const dg_mesh *m, double *U, unsigned char *troubled);
 
-// Device view of a learned-guess network: FP32 parameters, BF16 W2 [j][i], scales.
-void net_device_view(const dg_c2p_net *n, const float **P, const void **W2b, float sc[6]);
+// Device view of a learned-guess network: the shared-memory image of its weights
+// (a NetWeightsSmem in device memory), and its feature scales.
+void net_device_view(const dg_c2p_net *n, const void **img, float sc[6]);
 
 // Host LGL tables (long double Newton; closed-form LGL differentiation matrix).
 void lgl_tables(int n, Tables &T);

@@ -354,8 +354,7 @@ struct MixedArgs {
     float kappa_sw;
     double d_atm, tau_atm;
     int tc;                          // volume contraction: 1 split-BF16x3 tensor cores, 0 FP32 FMA
-    const float *netP;               // learned-guess network (FP32 parameters), or nullptr
-    const __nv_bfloat16 *netW2;      // its W2 in BF16 [j][i]
+    const NetWeightsSmem *netImg;    // learned-guess network: its shared-memory image, or nullptr
     float net_sc[6];                 // its feature scales
     float D32[MAXN * MAXN];
     double w64[MAXN], row1_64[MAXN];
@@ -385,8 +384,7 @@ struct CflArgs {
     double gamma_d;
     float kappa_sw;
     double d_atm, tau_atm;
-    const float *netP;             // learned-guess network, or nullptr
-    const __nv_bfloat16 *netW2;
+    const NetWeightsSmem *netImg;  // learned-guess network: its shared-memory image, or nullptr
     float net_sc[6];
 };
 
@@ -533,6 +531,7 @@ __global__ void __launch_bounds__(StageShape<NP>::MAXT, StageShape<NP>::MIN_CTAS
     MeshSlot &sl = *reinterpret_cast<MeshSlot *>(base + SM::SLOT);
     __shared__ float sD[NP * NP];
     __shared__ double sW64[NP], sRow164[NP];
+    __shared__ uint64_t sNetBar;  // completion of the network weights' bulk copy
 
     const long long ge = (long long)blockIdx.x * a.epb + sub;
     const bool live = sub < a.epb && ge < a.nelem;  // uniform within the element's warps
@@ -544,12 +543,17 @@ __global__ void __launch_bounds__(StageShape<NP>::MAXT, StageShape<NP>::MIN_CTAS
             sNb[6] = a.slots ? ge - a.elem0[m] : ge;
         }
     }
+    if (GUESS && threadIdx.x == 0) net_bar_init(&sNetBar);
     for (int i = threadIdx.x; i < NP * NP; i += blockDim.x) sD[i] = a.D32[i];
     if (threadIdx.x < NP) {
         sW64[threadIdx.x] = a.w64[threadIdx.x];
         sRow164[threadIdx.x] = a.row1_64[threadIdx.x];
     }
     __syncthreads();
+    // the network's weights travel by one bulk asynchronous copy while the face
+    // nodes and the features load
+    if (GUESS && threadIdx.x == 0)
+        net_copy_issue(reinterpret_cast<NetWeightsSmem *>(smem_mixed + SM::net(a.epb)), a.netImg, &sNetBar);
     const long long e = live ? sNb[6] : 0;
     if (live && t < 6) sNb[t] = elem_neighbour(e, sl.K, t >> 1, (t & 1) ? 1 : -1);
     const bool own = live && t < NN;  // this thread holds node t of a live element
@@ -587,14 +591,18 @@ __global__ void __launch_bounds__(StageShape<NP>::MAXT, StageShape<NP>::MIN_CTAS
     // element's node at the same point (the other side of the trace), solved by then.
     float guess_net = -1.0f;
     if (GUESS) {
-        NetWeightsSmem &W = *reinterpret_cast<NetWeightsSmem *>(smem_mixed + SM::net(a.epb));
-        net_stage_weights(W, a.netP, a.netW2);
+        const NetWeightsSmem &W = *reinterpret_cast<const NetWeightsSmem *>(smem_mixed + SM::net(a.epb));
         if (t < NN) {
             float u[5] = {1.0f, 0.0f, 0.0f, 0.0f, 1.0f};
             if (own)
 #pragma unroll
                 for (int v = 0; v < 5; ++v) u[v] = f64_to_f32(sl.Us[(e * 5 + v) * NN + t]);
             net_features(u, a.net_sc, reinterpret_cast<float(*)[6]>(smem_mixed + SM::feat(a.epb, sub))[t]);
+        }
+        if (!net_copy_wait(&sNetBar, NET_COPY_POLLS)) {
+            // flag it, and give the copy one more bounded wait before its region is reused
+            errs |= ERRBIT_TIMEOUT;
+            net_copy_wait(&sNetBar, NET_COPY_POLLS);
         }
         __syncthreads();
         for (int s2 = 0; s2 < a.epb; ++s2)
@@ -1014,7 +1022,7 @@ cudaError_t launch_stage_mixed_np(int system, int flux, const MixedArgs &a, cuda
     if (a.nelem <= 0) return cudaSuccess;
     const long long blocks = (a.nelem + a.epb - 1) / a.epb;
     const dim3 grid((unsigned)blocks), block(SS::TPE * a.epb);
-    const bool learned = system == 1 && a.netP != nullptr;
+    const bool learned = system == 1 && a.netImg != nullptr;
     const size_t smem = MixedSmem<NP>::total(a.epb, learned);
     void (*kern)(const MixedArgs);
     if (system == 0 && flux == 2) kern = k_stage_mixed<NP, 0, 2, 0>;

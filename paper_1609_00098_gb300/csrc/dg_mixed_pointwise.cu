@@ -27,7 +27,12 @@ __global__ void __launch_bounds__(kThreads) k_cfl_mixed(const CflArgs a)
 {
     extern __shared__ __align__(16) unsigned char cfl_smem[];
     CflNetSmem &N = *reinterpret_cast<CflNetSmem *>(cfl_smem);
-    if (GUESS) net_stage_weights(N.W, a.netP, a.netW2);
+    __shared__ uint64_t bar;  // completion of the network weights' bulk copy
+    if (GUESS) {
+        if (threadIdx.x == 0) net_bar_init(&bar);
+        __syncthreads();
+        if (threadIdx.x == 0) net_copy_issue(&N.W, a.netImg, &bar);
+    }
     int m = 0;
     long long c = blockIdx.x;
     if (a.slots) {
@@ -44,15 +49,19 @@ __global__ void __launch_bounds__(kThreads) k_cfl_mixed(const CflArgs a)
 #pragma unroll
         for (int v = 0; v < 5; ++v) u[v] = f64_to_f32(sl.Un[(e * 5 + v) * a.nn + q]);
     float guess = (sl.pin && act) ? sl.pin[g] : -1.0f;
+    unsigned errs = 0;
     if (GUESS) {
         net_features(u, a.net_sc, N.feat[threadIdx.x]);
+        if (!net_copy_wait(&bar, NET_COPY_POLLS)) {
+            errs |= ERRBIT_TIMEOUT;
+            net_copy_wait(&bar, NET_COPY_POLLS);
+        }
         __syncthreads();
         net_guess_rows(N.W, N.feat, N.guess, kThreads, a.gamma, a.net_sc);
         __syncthreads();
         guess = N.guess[threadIdx.x];
     }
     float lmax = 0.0f;
-    unsigned errs = 0;
     if (act) {
         if (SYS == 0) {
             ne_primitives32(a.gamma, u, P);
@@ -97,9 +106,9 @@ CflArgs cfl_args(const dg_mesh *m, float kappa_sw)
     a.d_atm = m->d.d_atm;
     a.tau_atm = m->d.tau_atm;
     if (m->d.system == 1 && m->net != nullptr) {
-        const void *w2 = nullptr;
-        net_device_view(m->net, &a.netP, &w2, a.net_sc);
-        a.netW2 = static_cast<const __nv_bfloat16 *>(w2);
+        const void *img = nullptr;
+        net_device_view(m->net, &img, a.net_sc);
+        a.netImg = static_cast<const NetWeightsSmem *>(img);
     }
     return a;
 }
@@ -110,7 +119,7 @@ cudaError_t launch_cfl_batch(int system, const CflArgs &a, long long nchunks, cu
     const unsigned grid = (unsigned)nchunks;
     if (system == 0) {
         k_cfl_mixed<0, 0><<<grid, kThreads, 0, s>>>(a);
-    } else if (a.netP == nullptr) {
+    } else if (a.netImg == nullptr) {
         k_cfl_mixed<1, 0><<<grid, kThreads, 0, s>>>(a);
     } else {
         const size_t smem = sizeof(CflNetSmem);
