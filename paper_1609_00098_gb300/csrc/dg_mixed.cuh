@@ -975,22 +975,39 @@ __global__ void __launch_bounds__(256) k_limit_mixed(const LimitMixedArgs a)
     if (fl & 1) mask = 0x1fu;
     if (lane == 0 && sl.troubled) sl.troubled[e] = (unsigned char)mask;
     if (!mask && !(fl & 2)) return;
-    double m0[5], s0[5], s1[5], s2[5];
+    // The replacement m0 + s0 h0(i) + s1 h1(j) + s2 h2(k) (h_a = (dx_a/2) xbar): the
+    // part m0 + s0 h0(i) + s1 h1(j) is built once per (i, j) plane point and
+    // variable, so a node costs one FP64 FMA per limited variable.
+    __shared__ double sAB[8][5][NP * NP];  // per warp of the CTA
+    __shared__ double sH2[8][NP];
+    const int wl = (threadIdx.x >> 5) & 7;
+    double s2[5];
 #pragma unroll
-    for (int v = 0; v < 5; ++v) {
-        m0[v] = __shfl_sync(0xffffffffu, U0, 3 * v);
-        s0[v] = __shfl_sync(0xffffffffu, slope, 3 * v);
-        s1[v] = __shfl_sync(0xffffffffu, slope, 3 * v + 1);
-        s2[v] = __shfl_sync(0xffffffffu, slope, 3 * v + 2);
+    for (int v = 0; v < 5; ++v) s2[v] = __shfl_sync(0xffffffffu, slope, 3 * v + 2);
+    if (mask) {
+        double m0[5], s0[5], s1[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+            m0[v] = __shfl_sync(0xffffffffu, U0, 3 * v);
+            s0[v] = __shfl_sync(0xffffffffu, slope, 3 * v);
+            s1[v] = __shfl_sync(0xffffffffu, slope, 3 * v + 1);
+        }
+        for (int ij = lane; ij < NP * NP; ij += 32) {
+            const double h0 = sl.hdx[0] * a.x[ij % NP], h1 = sl.hdx[1] * a.x[ij / NP];
+#pragma unroll
+            for (int v = 0; v < 5; ++v) sAB[wl][v][ij] = fma(s1[v], h1, fma(s0[v], h0, m0[v]));
+        }
+        if (lane < NP) sH2[wl][lane] = sl.hdx[2] * a.x[lane];
+        __syncwarp();
     }
     for (int q = lane; q < NN; q += 32) {
-        const int i = q % NP, j = (q / NP) % NP, k = q / (NP * NP);
-        const double h0 = sl.hdx[0] * a.x[i], h1 = sl.hdx[1] * a.x[j], h2 = sl.hdx[2] * a.x[k];
+        const int ij = q % (NP * NP), k = q / (NP * NP);
+        const double h2 = mask ? sH2[wl][k] : 0.0;
         double u[5];
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
             const long long ix = (e * 5 + v) * NN + q;
-            u[v] = (mask & (1u << v)) ? m0[v] + s0[v] * h0 + s1[v] * h1 + s2[v] * h2 : sl.U[ix];
+            u[v] = (mask & (1u << v)) ? fma(s2[v], h2, sAB[wl][v][ij]) : sl.U[ix];
         }
         unsigned nm = mask;
         if (SYS == 1) {
