@@ -855,9 +855,12 @@ __global__ void __launch_bounds__(StageShape<NP>::MAXT, StageShape<NP>::MIN_CTAS
     if (bad) atomicOr(&sFlag[0], 1);
     if (needfix) atomicOr(&sFlag[1], 1);
     __syncthreads();
-    // partial sums over t0 for every (axis, plane, t1, variable), then over t1
-    for (int id = t; live && id < 15 * NP * NP; id += TPE) {
-        const int v = id % 5, t1 = (id / 5) % NP, ia = (id / (5 * NP)) % NP, ax = id / (5 * NP * NP);
+    // Line sums P_a[ia][t1] = sum_t0 w_t0 U (axis a at index ia, t0 along the next
+    // axis, t1 along the one after) for a = x (sums over y) and a = z (sums over x),
+    // then Q_x and Q_z over t1; the planes across y reuse the x sums:
+    // Q_y[j] = sum_k w_k P_z[k][j].  Two FP64 FMAs per node and variable.
+    for (int id = t; live && id < 10 * NP * NP; id += TPE) {
+        const int v = id % 5, t1 = (id / 5) % NP, ia = (id / (5 * NP)) % NP, ax = id < 5 * NP * NP ? 0 : 2;
         const int b = (ax + 1) % 3, c = (ax + 2) % 3;
         const double *Vv = sV + v * NN;
         double r = 0.0;
@@ -868,13 +871,16 @@ __global__ void __launch_bounds__(StageShape<NP>::MAXT, StageShape<NP>::MIN_CTAS
             id3[c] = t1;
             r = fma(sW64[t0], Vv[id3[0] + NP * (id3[1] + NP * id3[2])], r);
         }
-        sPart[id] = r;
+        sPart[((ax * NP + ia) * NP + t1) * 5 + v] = r;
     }
     __syncthreads();
     for (int id = t; live && id < 15 * NP; id += TPE) {
         const int ax = id / (5 * NP), ia = (id / 5) % NP, v = id % 5;
         double q = 0.0;
-        for (int t1 = 0; t1 < NP; ++t1) q = fma(sW64[t1], sPart[((ax * NP + ia) * NP + t1) * 5 + v], q);
+        if (ax == 1)
+            for (int k = 0; k < NP; ++k) q = fma(sW64[k], sPart[((2 * NP + k) * NP + ia) * 5 + v], q);
+        else
+            for (int t1 = 0; t1 < NP; ++t1) q = fma(sW64[t1], sPart[((ax * NP + ia) * NP + t1) * 5 + v], q);
         sQ[(ax * NP + ia) * 5 + v] = q;
     }
     __syncthreads();
