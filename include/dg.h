@@ -239,8 +239,9 @@ dg_status dg_rhs_static(const dg_mesh_desc *desc, const double *U, double *dUdt,
  *     above which the FP32 con2prim result is finished by FP64 Newton on the FP64
  *     state (it also bounds W^2 for the FP32 wave speeds); in [1, 1e30].
  *   DG_OPT_ELEMENTS_PER_CTA (default 1): elements per CTA of the mixed stage
- *     kernel, a power of two up to 256 / (n^3 rounded up to 32) (at least 1);
- *     the result does not depend on it.
+ *     kernel, a power of two up to 256 / (n^3 rounded up to 32) (at least 1;
+ *     for n = 5, which runs 160 threads per element, up to 2); the result does
+ *     not depend on it.
  * Errors: DG_ERR_ARG for an unknown option or a value out of range. */
 enum { DG_OPT_TENSOR_CORE_CONTRACTION = 1, DG_OPT_C2P_KAPPA_SWITCH = 2, DG_OPT_ELEMENTS_PER_CTA = 3 };
 dg_status dg_mesh_set_option(dg_mesh *mesh, int option, double value);
