@@ -434,6 +434,7 @@ void free_scratch(dg_mesh *m)
     cudaFree(m->W2);
     cudaFree(m->pbuf[0]);
     cudaFree(m->pbuf[1]);
+    cudaFree(m->pfull);
     for (int i = 0; i < 3; ++i) cudaFree(m->abL[i]);
     cudaFree(m->P);
     cudaFree(m->S);
@@ -507,6 +508,7 @@ dg_status dg_mesh_create(const dg_mesh_desc *d, dg_mesh **out)
     if (mixed && d->system == 1) {
         st = st ? st : cudaMalloc(&m->pbuf[0], sizeof(float) * (size_t)E * m->nn);
         st = st ? st : cudaMalloc(&m->pbuf[1], sizeof(float) * (size_t)E * m->nn);
+        st = st ? st : cudaMalloc(&m->pfull, sizeof(float) * 5 * (size_t)E * m->nn);
     }
     st = st ? st : cudaMalloc(&m->P, sizeof(double) * (size_t)E * 4 * m->nn);
     st = st ? st : cudaMalloc(&m->S, sizeof(double) * (size_t)E * 50);
@@ -645,11 +647,12 @@ static dg_status rk3_step_mixed(dg_mesh *m, double *U, double dt, double cfl, do
     const bool sr = m->d.system == 1;
     const bool lim = m->d.limiter != 0;
     const bool cflmode = cfl > 0.0;
-    // with a learned guess attached, no pressures are carried between steps; the
+    // with a learned guess attached, no pressures are carried between steps.  The
     // CFL pass solves con2prim on U^n, the very state stage 1 starts from, and
-    // stage 1 takes those pressures instead of evaluating the network again
+    // stage 1 takes those primitives (own and neighbour face nodes) instead of
+    // solving again
     const bool carry = sr && m->net == nullptr;
-    const bool reuse = sr && m->net != nullptr && cflmode;
+    const bool pgiven = sr && cflmode;
     MixedArgs a = mixed_args(m);
     a.one.Un = U;
     a.one.dt = dt;
@@ -660,8 +663,9 @@ static dg_status rk3_step_mixed(dg_mesh *m, double *U, double dt, double cfl, do
     float *latest = (carry && m->p_valid) ? m->pbuf[m->pi] : nullptr;
     if (cflmode) {
         DG_CUDA(cudaMemsetAsync(m->lam, 0, sizeof(unsigned long long), s));
-        float *cfl_out = carry ? m->pbuf[1 - m->pi] : (reuse ? m->pbuf[0] : nullptr);
-        DG_LAUNCH(m, s, PROF_PRIM, launch_cfl_mixed(m, U, latest, cfl_out, m->kappa_sw, s));
+        DG_LAUNCH(m, s, PROF_PRIM,
+                  launch_cfl_mixed(m, U, latest, carry ? m->pbuf[1 - m->pi] : nullptr, pgiven ? m->pfull : nullptr,
+                                   m->kappa_sw, s));
         if (carry) {
             m->pi = 1 - m->pi;
             latest = m->pbuf[m->pi];
@@ -684,9 +688,9 @@ static dg_status rk3_step_mixed(dg_mesh *m, double *U, double dt, double cfl, do
         a.one.pout = carry ? m->pbuf[1 - m->pi] : nullptr;
         a.epb = m->epb > 0 ? m->epb : 1;
         MixedArgs as = a;
-        if (reuse && st == 0) {
+        if (pgiven && st == 0) {
             as.netImg = nullptr;
-            as.one.pin = m->pbuf[0];
+            as.one.Pin = m->pfull;
         }
         DG_LAUNCH(m, s, PROF_STAGE, launch_stage_mixed(m->d.n, m->d.system, m->d.flux, as, s));
         if (carry) {

@@ -61,7 +61,7 @@ struct EnsGroup {
     std::vector<int> members;
     long long nelem = 0, nchunks = 0;
     int epb = 1, tc = 1;
-    bool reuse = false;          // learned guess: stage 1 takes the CFL pass's pressures
+    bool pgiven = false;         // SR: stage 1 takes the CFL pass's primitives
     MixedArgs proto;             // group-level stage arguments (members[0])
     CflArgs cproto;
     LimitMixedArgs lproto;
@@ -123,14 +123,15 @@ void free_group(EnsGroup &g)
 // Slot tables of a group: the pointers of every member for each pass of a step.
 // Pressure buffers (warm start, no network) follow the same alternation as
 // dg_rk3_step: CFL reads pbuf[0] and writes pbuf[1], stage 1 reads pbuf[1] and
-// writes pbuf[0], stage 2 the reverse, stage 3 as stage 1.  With a learned guess
-// (no carry) the CFL pass writes pbuf[0] and stage 1 reads it, as in dg_rk3_step.
+// writes pbuf[0], stage 2 the reverse, stage 3 as stage 1.  For SR meshes the CFL
+// pass also writes its primitives of U^n (pfull), which stage 1 takes instead of
+// solving con2prim, as in dg_rk3_step.
 cudaError_t build_group(dg_ensemble *en, EnsGroup &g)
 {
     const dg_mesh *m0 = en->meshes[g.members[0]];
     const bool carry = m0->d.system == 1 && m0->net == nullptr;
-    const bool reuse = m0->d.system == 1 && m0->net != nullptr;
-    g.reuse = reuse;
+    const bool pgiven = m0->d.system == 1;
+    g.pgiven = pgiven;
     std::vector<MeshSlot> st[3], first, rhs;
     std::vector<LimitSlot> li[3];
     std::vector<CflSlot> cf, cf1;
@@ -149,7 +150,7 @@ cudaError_t build_group(dg_ensemble *en, EnsGroup &g)
             sl.out = outs[s];
             sl.pin = (s == 1) ? pr[0] : pr[1];
             sl.pout = (s == 1) ? pr[1] : pr[0];
-            if (reuse && s == 0) sl.pin = m->pbuf[0];
+            if (pgiven && s == 0) sl.Pin = m->pfull;
             sl.S = m->d.limiter ? m->S : nullptr;
             sl.flags = (m->d.limiter && m->d.system == 1) ? m->unphys : nullptr;
             sl.dt_ptr = m->dt;
@@ -166,7 +167,8 @@ cudaError_t build_group(dg_ensemble *en, EnsGroup &g)
         std::memset(&c, 0, sizeof(c));
         c.Un = U;
         c.pin = pr[0];
-        c.pout = reuse ? m->pbuf[0] : pr[1];
+        c.pout = pr[1];
+        c.Pout = pgiven ? m->pfull : nullptr;
         c.lam = m->lam;
         c.err = m->err;
         c.nodes = m->E * m->nn;
@@ -241,7 +243,7 @@ cudaError_t launch_step(dg_ensemble *en, double cfl, bool first, cudaStream_t s)
     for (int st = 0; st < 3 && e == cudaSuccess; ++st) {
         for (EnsGroup &g : en->groups) {
             MixedArgs a = stage_args_for(g, (first && st == 0) ? g.d_stage_first : g.d_stage[st], st);
-            if (g.reuse && st == 0) {  // stage 1 starts from the CFL pass's pressures
+            if (g.pgiven && st == 0) {  // stage 1 takes the CFL pass's primitives
                 a.netImg = nullptr;
             }
             e = launch_stage_mixed(g.n, g.system, g.flux, a, s);

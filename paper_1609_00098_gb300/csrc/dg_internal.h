@@ -122,6 +122,7 @@ struct dg_mesh {
     unsigned int *err;       // sticky status word
     // mixed-precision scratch (precision == DG_PRECISION_MIXED)
     float *pbuf[2];          // SR pressures of the last two passes (con2prim warm starts)
+    float *pfull;            // SR: the CFL pass's FP32 primitives [e][5][node] of U^n, for stage 1
     int pi, p_valid;         // index of the latest pressure buffer, and whether it holds one
     float kappa_sw;          // conditioning above which FP32 con2prim is polished in FP64
     const dg_c2p_net *net;   // attached learned-guess network (mixed SR path), or nullptr
@@ -168,7 +169,8 @@ struct MixedArgs;
 struct LimitMixedArgs;
 cudaError_t launch_stage_mixed(int n, int system, int flux, const MixedArgs &a, cudaStream_t s);
 cudaError_t launch_limit_mixed(int n, int system, const LimitMixedArgs &a, cudaStream_t s);
-cudaError_t launch_cfl_mixed(const dg_mesh *m, const double *Un, const float *pin, float *pout, float kappa_sw,
+cudaError_t launch_cfl_mixed(const dg_mesh *m, const double *Un, const float *pin, float *pout, float *Pout,
+                             float kappa_sw,
                              cudaStream_t s);
 struct CflArgs;
 struct MeshSlot;

@@ -328,6 +328,8 @@ struct MeshSlot {
     double *out;            // stage output U_{s+1} (mode 1) or dU/dt (mode 0)
     const float *pin;       // SR pressures of the previous pass [e][node] (guesses), or nullptr
     float *pout;            // SR pressures of this stage's input [e][node], or nullptr
+    const float *Pin;       // SR: FP32 primitives [e][NPRIM][node] of U_s already solved (the
+                            // CFL pass's, for stage 1), or nullptr: no con2prim then
     double *S;              // limiter summaries of the output [e][5][10], or nullptr
     unsigned char *flags;   // SR: bit 0 unphysical node, bit 1 a node needs the fix (limiter on)
     unsigned int *err;
@@ -369,6 +371,7 @@ struct CflSlot {
     const double *Un;
     const float *pin;              // previous pass's pressures (guesses), or nullptr
     float *pout;                   // this pass's pressures, or nullptr
+    float *Pout;                   // SR: this pass's FP32 primitives [e][NPRIM][node], or nullptr
     unsigned long long *lam;
     unsigned int *err;
     long long nodes;
@@ -625,9 +628,15 @@ __global__ void __launch_bounds__(StageShape<NP>::MAXT, StageShape<NP>::MIN_CTAS
         }
         float P[NPRIM];
         const float guess = GUESS ? guess_net : (sl.pin ? sl.pin[e * NN + t] : -1.0f);
-        if (SYS == 0) ne_primitives32(a.gamma, u, P);
-        else errs |= sr_prims_mixed(a.gamma, a.gamma_d, a.kappa_sw, a.d_atm, a.tau_atm, u,
-                                    sl.Us + e * 5 * NN + t, NN, guess, P);
+        if (SYS == 0) {
+            ne_primitives32(a.gamma, u, P);
+        } else if (sl.Pin) {
+#pragma unroll
+            for (int c = 0; c < NPRIM; ++c) P[c] = sl.Pin[(e * NPRIM + c) * NN + t];
+        } else {
+            errs |= sr_prims_mixed(a.gamma, a.gamma_d, a.kappa_sw, a.d_atm, a.tau_atm, u, sl.Us + e * 5 * NN + t,
+                                   NN, guess, P);
+        }
         if (SYS == 1 && sl.pout) sl.pout[e * NN + t] = P[3];
 #pragma unroll
         for (int c = 0; c < NPRIM; ++c) sP[c * NN + t] = P[c];
@@ -769,6 +778,10 @@ __global__ void __launch_bounds__(StageShape<NP>::MAXT, StageShape<NP>::MIN_CTAS
         const float gn = GUESS ? Po[3] : sFG[f];
         if (SYS == 0) {
             ne_primitives32(a.gamma, un, Pn);
+        } else if (sl.Pin) {
+            const long long en = sNb[2 * ax + side];
+#pragma unroll
+            for (int c = 0; c < NPRIM; ++c) Pn[c] = sl.Pin[(en * NPRIM + c) * NN + qn];
         } else {
             const long long en = sNb[2 * ax + side];
             errs |= sr_prims_mixed(a.gamma, a.gamma_d, a.kappa_sw, a.d_atm, a.tau_atm, un,

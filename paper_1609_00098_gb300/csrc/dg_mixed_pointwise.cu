@@ -69,6 +69,9 @@ __global__ void __launch_bounds__(kThreads) k_cfl_mixed(const CflArgs a)
             errs |= sr_prims_mixed(a.gamma, a.gamma_d, a.kappa_sw, a.d_atm, a.tau_atm, u, sl.Un + e * 5 * a.nn + q,
                                    a.nn, guess, P);
             if (sl.pout) sl.pout[g] = P[3];
+            if (sl.Pout)
+#pragma unroll
+                for (int c = 0; c < NPRIM; ++c) sl.Pout[(e * NPRIM + c) * a.nn + q] = P[c];
         }
 #pragma unroll
         for (int ax = 0; ax < 3; ++ax) {
@@ -132,13 +135,14 @@ cudaError_t launch_cfl_batch(int system, const CflArgs &a, long long nchunks, cu
     return cudaGetLastError();
 }
 
-cudaError_t launch_cfl_mixed(const dg_mesh *m, const double *Un, const float *pin, float *pout, float kappa_sw,
-                             cudaStream_t s)
+cudaError_t launch_cfl_mixed(const dg_mesh *m, const double *Un, const float *pin, float *pout, float *Pout,
+                             float kappa_sw, cudaStream_t s)
 {
     CflArgs a = cfl_args(m, kappa_sw);
     a.one.Un = Un;
     a.one.pin = pin;
     a.one.pout = pout;
+    a.one.Pout = Pout;
     return launch_cfl_batch(m->d.system, a, (a.one.nodes + kThreads - 1) / kThreads, s);
 }
 
