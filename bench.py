@@ -133,16 +133,16 @@ def _init_state(pkg, mesh, torch):
 
 
 # DRAM bytes per k_stage_mixed launch of the learned-guess steps on this workload
-# (mean over the three stages of a step: stage 1 runs the variant that starts from
-# the CFL pass's pressures, stages 2-3 the in-kernel network), from the ncu launch
+# (mean over the three stages of a step: stage 1 runs the variant that takes the
+# CFL pass's primitives, stages 2-3 the in-kernel network), from the ncu launch
 # list summarised in profiles/launches_sr_blast_16x16x16_n5.md.  Reported only
 # while the kernel's sources and the step's dispatch still hash to the value they
 # had when it was taken.
-TRAFFIC_BYTES_PER_LAUNCH = 40553849.0
+TRAFFIC_BYTES_PER_LAUNCH = 44846485.0
 TRAFFIC_SOURCES = ("paper_1609_00098_gb300/csrc/dg_mixed.cuh", "paper_1609_00098_gb300/csrc/dg_physics.cuh",
                    "paper_1609_00098_gb300/csrc/dg_internal.h", "paper_1609_00098_gb300/csrc/dg_c2p_net.cuh",
                    "paper_1609_00098_gb300/csrc/dg_api.cu")
-TRAFFIC_SOURCES_SHA256 = "d1c47da7c4ff0164443bec1aa4f1c862de2081794a58c5c60ef01489ff0c57ec"
+TRAFFIC_SOURCES_SHA256 = "4385445bb40f6045a7c8104f2d26ca8fde9eff4dfc788b4fbf20b389d592d0f0"
 TRAFFIC_VARIANT = "learned"
 
 
@@ -161,13 +161,14 @@ def _algorithmic(nodes, precision, learned=False):
     Both paths keep FP64 stage states: stage 1 reads U^n and writes U^1 (80 B/node);
     stages 2, 3 read U_s and U^n and write U_{s+1} (120 B/node).  The warm-started
     mixed SR path also reads the previous pass's FP32 pressure (4 B) and writes its
-    own (4 B).  With the learned guess computed in the kernel, stages 2, 3 carry no
-    pressure and stage 1 reads the CFL pass's pressures of U^n (4 B)."""
+    own (4 B).  Stage 1 of an SR CFL step reads the CFL pass's FP32 primitives of
+    U^n (20 B) instead of solving con2prim; with the learned guess computed in the
+    kernel, stages 2, 3 carry no pressure."""
     if precision == 0:
         return nodes * (80 + 120 + 120) / 3.0
     if learned:
-        return nodes * (84 + 120 + 120) / 3.0
-    return nodes * (88 + 128 + 128) / 3.0
+        return nodes * (100 + 120 + 120) / 3.0
+    return nodes * (104 + 128 + 128) / 3.0
 
 
 def _train_guess_net(pkg, torch):
