@@ -142,7 +142,7 @@ TRAFFIC_BYTES_PER_LAUNCH = 44846485.0
 TRAFFIC_SOURCES = ("paper_1609_00098_gb300/csrc/dg_mixed.cuh", "paper_1609_00098_gb300/csrc/dg_physics.cuh",
                    "paper_1609_00098_gb300/csrc/dg_internal.h", "paper_1609_00098_gb300/csrc/dg_c2p_net.cuh",
                    "paper_1609_00098_gb300/csrc/dg_api.cu")
-TRAFFIC_SOURCES_SHA256 = "4385445bb40f6045a7c8104f2d26ca8fde9eff4dfc788b4fbf20b389d592d0f0"
+TRAFFIC_SOURCES_SHA256 = "e2a6b3dfa95e682fdec0922119915bb5f32d1c2d50db9cb3152a352a24eb942d"
 TRAFFIC_VARIANT = "learned"
 
 

@@ -96,12 +96,6 @@ __device__ __forceinline__ uint32_t silu_half_bf16x2(float lo, float hi)
     return h;
 }
 
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
-{
-    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-    return *reinterpret_cast<const uint32_t *>(&v);
-}
-
 // Four 8 x 8 BF16 matrices from shared memory; this lane gives the address of one
 // row (lanes 8m..8m+7: the rows of matrix m).
 __device__ __forceinline__ void ldmatrix_x4(uint32_t r[4], const void *row)
