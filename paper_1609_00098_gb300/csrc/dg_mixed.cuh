@@ -214,6 +214,16 @@ __device__ __forceinline__ void num_flux_jump32(float g, int a, const float uL[5
     }
 }
 
+// Node-index stride of axis x (1, NP, NP^2) and a component chosen by a runtime
+// axis, both by selection: indexing a register array with a runtime value would
+// move it to local memory.
+template <int NP>
+__device__ __forceinline__ int axis_stride(int x)
+{
+    return x == 0 ? 1 : (x == 1 ? NP : NP * NP);
+}
+__device__ __forceinline__ float pick3(int k, float x0, float x1, float x2) { return k == 0 ? x0 : (k == 1 ? x1 : x2); }
+
 __device__ __forceinline__ void ne_primitives32(float g, const float u[5], float P[NPRIM])
 {
     const float inv = 1.0f / u[0];
@@ -571,11 +581,9 @@ __global__ void __launch_bounds__(StageShape<NP>::MAXT, StageShape<NP>::MIN_CTAS
     for (int f = t; live && f < NF; f += TPE) {
         const int ax = f / (2 * NP * NP), fpa = f % (2 * NP * NP);
         const int side = fpa / (NP * NP), rem = fpa % (NP * NP);
-        int id[3];
-        id[ax] = side ? 0 : NP - 1;
-        id[(ax + 1) % 3] = rem % NP;
-        id[(ax + 2) % 3] = rem / NP;
-        const int qn = id[0] + NP * (id[1] + NP * id[2]);
+        const int b = ax == 2 ? 0 : ax + 1, c = ax == 0 ? 2 : ax - 1;
+        const int qn = (side ? 0 : NP - 1) * axis_stride<NP>(ax) + (rem % NP) * axis_stride<NP>(b) +
+                       (rem / NP) * axis_stride<NP>(c);
         if (SYS == 0) {
             // a negative neighbour is a ghost holding the analytic exterior state
             const long long en = elem_neighbour_bc(e, sl.K, ax, side ? 1 : -1, sl.gh);
@@ -760,46 +768,62 @@ __global__ void __launch_bounds__(StageShape<NP>::MAXT, StageShape<NP>::MIN_CTAS
     for (int f = t; live && f < NF; f += TPE) {
         const int ax = f / (2 * NP * NP), fpa = f % (2 * NP * NP);
         const int side = fpa / (NP * NP), rem = fpa % (NP * NP);
-        int id[3];
-        id[ax] = side ? NP - 1 : 0;
-        id[(ax + 1) % 3] = rem % NP;
-        id[(ax + 2) % 3] = rem / NP;
-        const int q = id[0] + NP * (id[1] + NP * id[2]);
-        id[ax] = side ? 0 : NP - 1;
-        const int qn = id[0] + NP * (id[1] + NP * id[2]);
-        float uo[5], Po[NPRIM], un[5], Pn[NPRIM];
+        // the face's normal axis and its tangential axes b, c in cyclic order
+        const int b = ax == 2 ? 0 : ax + 1, c = ax == 0 ? 2 : ax - 1;
+        const int sa = axis_stride<NP>(ax);
+        const int tq = (rem % NP) * axis_stride<NP>(b) + (rem / NP) * axis_stride<NP>(c);
+        const int q = (side ? NP - 1 : 0) * sa + tq;
+        const int qn = (side ? 0 : NP - 1) * sa + tq;
+        // Both traces in the face frame (normal, b, c components): the flux routines
+        // then run with axis 0 and keep their arrays in registers.  The neighbour's
+        // con2prim works in the mesh frame, its result is rotated after.
+        float uo[5], Po[NPRIM], um[5], Pm[NPRIM];
+        uo[0] = sU[q];
+        uo[1] = sU[(1 + ax) * NN + q];
+        uo[2] = sU[(1 + b) * NN + q];
+        uo[3] = sU[(1 + c) * NN + q];
+        uo[4] = sU[4 * NN + q];
+        Po[0] = sP[ax * NN + q];
+        Po[1] = sP[b * NN + q];
+        Po[2] = sP[c * NN + q];
+        Po[3] = sP[3 * NN + q];
+        Po[4] = sP[4 * NN + q];
 #pragma unroll
-        for (int v = 0; v < 5; ++v) {
-            uo[v] = sU[v * NN + q];
-            un[v] = sFU[v * NF + f];
-        }
-#pragma unroll
-        for (int c = 0; c < NPRIM; ++c) Po[c] = sP[c * NN + q];
+        for (int v = 0; v < 5; ++v) um[v] = sFU[v * NF + f];
         const float gn = GUESS ? Po[3] : sFG[f];
         if (SYS == 0) {
-            ne_primitives32(a.gamma, un, Pn);
+            ne_primitives32(a.gamma, um, Pm);
         } else if (sl.Pin) {
             const long long en = sNb[2 * ax + side];
 #pragma unroll
-            for (int c = 0; c < NPRIM; ++c) Pn[c] = sl.Pin[(en * NPRIM + c) * NN + qn];
+            for (int k = 0; k < NPRIM; ++k) Pm[k] = sl.Pin[(en * NPRIM + k) * NN + qn];
         } else {
             const long long en = sNb[2 * ax + side];
-            errs |= sr_prims_mixed(a.gamma, a.gamma_d, a.kappa_sw, a.d_atm, a.tau_atm, un,
-                                   sl.Us + en * 5 * NN + qn, NN, gn, Pn);
+            errs |= sr_prims_mixed(a.gamma, a.gamma_d, a.kappa_sw, a.d_atm, a.tau_atm, um,
+                                   sl.Us + en * 5 * NN + qn, NN, gn, Pm);
         }
-        float dL[5], dR[5];
-        float *acc = sA + ax * 5 * NN + q;
+        const float un[5] = {um[0], pick3(ax, um[1], um[2], um[3]), pick3(b, um[1], um[2], um[3]),
+                             pick3(c, um[1], um[2], um[3]), um[4]};
+        const float Pn[NPRIM] = {pick3(ax, Pm[0], Pm[1], Pm[2]), pick3(b, Pm[0], Pm[1], Pm[2]),
+                                 pick3(c, Pm[0], Pm[1], Pm[2]), Pm[3], Pm[4]};
+        float dL[5], dR[5], o[5];
         if (side) {
-            num_flux_jump32<SYS, FLX>(a.gamma, ax, uo, Po, un, Pn, dL, dR);
+            num_flux_jump32<SYS, FLX>(a.gamma, 0, uo, Po, un, Pn, dL, dR);
             const float lN = sl.liftN[ax];
 #pragma unroll
-            for (int v = 0; v < 5; ++v) acc[v * NN] = -lN * dL[v];
+            for (int v = 0; v < 5; ++v) o[v] = -lN * dL[v];
         } else {
-            num_flux_jump32<SYS, FLX>(a.gamma, ax, un, Pn, uo, Po, dL, dR);
+            num_flux_jump32<SYS, FLX>(a.gamma, 0, un, Pn, uo, Po, dL, dR);
             const float l0 = sl.lift0[ax];
 #pragma unroll
-            for (int v = 0; v < 5; ++v) acc[v * NN] = l0 * dR[v];
+            for (int v = 0; v < 5; ++v) o[v] = l0 * dR[v];
         }
+        float *acc = sA + ax * 5 * NN + q;
+        acc[0] = o[0];
+        acc[(1 + ax) * NN] = o[1];
+        acc[(1 + b) * NN] = o[2];
+        acc[(1 + c) * NN] = o[3];
+        acc[4 * NN] = o[4];
     }
     __syncthreads();
     if (own)
@@ -880,13 +904,8 @@ __global__ void __launch_bounds__(StageShape<NP>::MAXT, StageShape<NP>::MIN_CTAS
         const int b = (ax + 1) % 3, c = (ax + 2) % 3;
         const double *Vv = sV + v * NN;
         double r = 0.0;
-        for (int t0 = 0; t0 < NP; ++t0) {
-            int id3[3];
-            id3[ax] = ia;
-            id3[b] = t0;
-            id3[c] = t1;
-            r = fma(sW64[t0], Vv[id3[0] + NP * (id3[1] + NP * id3[2])], r);
-        }
+        const int base_node = ia * axis_stride<NP>(ax) + t1 * axis_stride<NP>(c), st0 = axis_stride<NP>(b);
+        for (int t0 = 0; t0 < NP; ++t0) r = fma(sW64[t0], Vv[base_node + t0 * st0], r);
         sPart[((ax * NP + ia) * NP + t1) * 5 + v] = r;
     }
     __syncthreads();
