@@ -486,33 +486,35 @@ struct MixedSmem {
     // neighbour face-node states [5][NF] and guesses [NF] (face phase), later the
     // summaries' partial sums [3][NP][NP][5] (FP64)
     static constexpr size_t FACE = (MAIN + 15) / 16 * 16;
-    static constexpr size_t FACE_BYTES = sizeof(float) * 6 * NF > sizeof(double) * 15 * NP * NP
-                                             ? sizeof(float) * 6 * NF : sizeof(double) * 15 * NP * NP;
+    // (the guess array holds max(NF, NN) floats: the learned variant puts its
+    // nodes' guesses there, and for n >= 7 an element has more nodes than face points)
+    static constexpr size_t FACE_FLOATS = 5 * NF + (NF > NN ? NF : NN);
+    static constexpr size_t FACE_BYTES = sizeof(float) * FACE_FLOATS > sizeof(double) * 15 * NP * NP
+                                             ? sizeof(float) * FACE_FLOATS : sizeof(double) * 15 * NP * NP;
     static constexpr size_t Q = (FACE + FACE_BYTES + 15) / 16 * 16;
     static constexpr size_t NB = Q + sizeof(double) * 3 * NP * 5;
     static constexpr size_t FLAG = NB + sizeof(long long) * 7;      // 6 neighbours + element index
     static constexpr size_t SLOT = (FLAG + 2 * sizeof(int) + 15) / 16 * 16;
     static constexpr size_t ELEM = (SLOT + sizeof(MeshSlot) + 15) / 16 * 16;
     // Learned guess: the network's weights (one copy per CTA), and per element the
-    // features [NN][6] and guesses [NN] of its nodes.  They are dead once every
-    // thread holds its guess, before the element's MAIN region is first written,
-    // so where MAIN has room (n >= 5) they live inside it: the weights, element 0's
-    // features and guesses in element 0's MAIN, element s's in element s's.
-    // Otherwise they follow the elements.
+    // features [NN][6] of its nodes.  They are dead once the network has run, before
+    // the element's MAIN region is first written, so where MAIN has room (n >= 5)
+    // they live inside it: the weights and element 0's features in element 0's
+    // MAIN, element s's features in element s's.  Otherwise they follow the
+    // elements.  The guesses go to the element's face-guess array (FACE + 5 NF
+    // floats), which the learned variant does not otherwise use.
     static constexpr size_t NET_BYTES = (sizeof(NetWeightsSmem) + 15) / 16 * 16;
     static constexpr size_t FEAT_BYTES = sizeof(float) * 6 * NN;
-    static constexpr size_t GUESS_BYTES = sizeof(float) * NN;
-    static constexpr bool NET_IN_MAIN = NET_BYTES + FEAT_BYTES + GUESS_BYTES <= MAIN;
+    static constexpr bool NET_IN_MAIN = NET_BYTES + FEAT_BYTES <= MAIN;
     __host__ __device__ static size_t net(int epb) { return NET_IN_MAIN ? 0 : ELEM * epb; }
     __host__ __device__ static size_t feat(int epb, int s)
     {
-        return NET_IN_MAIN ? ELEM * s + (s == 0 ? NET_BYTES : 0)
-                           : ELEM * epb + NET_BYTES + (FEAT_BYTES + GUESS_BYTES) * s;
+        return NET_IN_MAIN ? ELEM * s + (s == 0 ? NET_BYTES : 0) : ELEM * epb + NET_BYTES + FEAT_BYTES * s;
     }
-    __host__ __device__ static size_t guess(int epb, int s) { return feat(epb, s) + FEAT_BYTES; }
+    __host__ __device__ static size_t guess(int s) { return ELEM * s + FACE + sizeof(float) * 5 * NF; }
     __host__ __device__ static size_t total(int epb, bool learned)
     {
-        return learned && !NET_IN_MAIN ? ELEM * epb + NET_BYTES + (FEAT_BYTES + GUESS_BYTES) * epb : ELEM * epb;
+        return learned && !NET_IN_MAIN ? ELEM * epb + NET_BYTES + FEAT_BYTES * epb : ELEM * epb;
     }
 };
 
@@ -603,7 +605,6 @@ __global__ void __launch_bounds__(StageShape<NP>::MAXT, StageShape<NP>::MIN_CTAS
     // cores over 16-row tiles, all warps of the CTA on each element's rows in turn).
     // The neighbours' face nodes in the face loop start from the pressure of this
     // element's node at the same point (the other side of the trace), solved by then.
-    float guess_net = -1.0f;
     if (GUESS) {
         const NetWeightsSmem &W = *reinterpret_cast<const NetWeightsSmem *>(smem_mixed + SM::net(a.epb));
         if (t < NN) {
@@ -621,10 +622,8 @@ __global__ void __launch_bounds__(StageShape<NP>::MAXT, StageShape<NP>::MIN_CTAS
         __syncthreads();
         for (int s2 = 0; s2 < a.epb; ++s2)
             net_guess_rows(W, reinterpret_cast<const float(*)[6]>(smem_mixed + SM::feat(a.epb, s2)),
-                           reinterpret_cast<float *>(smem_mixed + SM::guess(a.epb, s2)), NN, a.gamma, a.net_sc);
-        __syncthreads();
-        if (t < NN) guess_net = reinterpret_cast<const float *>(smem_mixed + SM::guess(a.epb, sub))[t];
-        __syncthreads();  // the network's regions are dead from here on
+                           reinterpret_cast<float *>(smem_mixed + SM::guess(s2)), NN, a.gamma, a.net_sc);
+        __syncthreads();  // the guesses are in sFG; the network's regions are dead from here on
     }
 
     if (own) {
@@ -635,7 +634,7 @@ __global__ void __launch_bounds__(StageShape<NP>::MAXT, StageShape<NP>::MIN_CTAS
             sU[v * NN + t] = u[v];
         }
         float P[NPRIM];
-        const float guess = GUESS ? guess_net : (sl.pin ? sl.pin[e * NN + t] : -1.0f);
+        const float guess = GUESS ? sFG[t] : (sl.pin ? sl.pin[e * NN + t] : -1.0f);
         if (SYS == 0) {
             ne_primitives32(a.gamma, u, P);
         } else if (sl.Pin) {
@@ -760,11 +759,9 @@ __global__ void __launch_bounds__(StageShape<NP>::MAXT, StageShape<NP>::MIN_CTAS
     // array (over the flux arrays, no longer read): within an axis a node lies on
     // at most one face, so there are no write conflicts, and the three are summed
     // in a fixed order afterwards.
+    // (sA[ax] is written only at the nodes on an ax-face; the sum below reads it
+    // only there, so nothing needs clearing first)
     float *sA = sF;  // [3][5][NN]
-    if (own)
-#pragma unroll
-        for (int c = 0; c < 15; ++c) sA[c * NN + t] = 0.0f;
-    __syncthreads();
     for (int f = t; live && f < NF; f += TPE) {
         const int ax = f / (2 * NP * NP), fpa = f % (2 * NP * NP);
         const int side = fpa / (NP * NP), rem = fpa % (NP * NP);
@@ -826,10 +823,14 @@ __global__ void __launch_bounds__(StageShape<NP>::MAXT, StageShape<NP>::MIN_CTAS
         acc[4 * NN] = o[4];
     }
     __syncthreads();
-    if (own)
+    if (own) {
+        const int i = t % NP, j = (t / NP) % NP, k = t / (NP * NP);
+        const bool fx = i == 0 || i == NP - 1, fy = j == 0 || j == NP - 1, fz = k == 0 || k == NP - 1;
 #pragma unroll
         for (int v = 0; v < 5; ++v)
-            sR[v * NN + t] += (sA[v * NN + t] + sA[(5 + v) * NN + t]) + sA[(10 + v) * NN + t];
+            sR[v * NN + t] += ((fx ? sA[v * NN + t] : 0.0f) + (fy ? sA[(5 + v) * NN + t] : 0.0f)) +
+                              (fz ? sA[(10 + v) * NN + t] : 0.0f);
+    }
     if (errs) atomicOr(sl.err, errs);
 
     // Stage update in FP64: U_{s+1} = U_s + [ca (U^n - U_s) + cb dt R], the bracket

@@ -103,6 +103,31 @@ def test_learned_guess_rhs_and_detach(pkg, trained):
     assert el.max() < 1e-4 and ep.max() < 1e-4, (el, ep)
 
 
+@pytest.mark.parametrize("n", [7, 8])
+def test_learned_guess_more_nodes_than_face_points(pkg, trained, n):
+    """n = 7, 8: an element has more nodes than face points, and the guesses of all
+    its nodes must fit the face-guess array.  RHS against the oracle at the FP32
+    level, and three steps within the 1e-6 bar."""
+    om = oracle.Mesh(oracle.MeshSpec(system=1, K=(3, 2, 2), n=n, flux=1, limiter=1, gamma=G))
+    gm = pkg.Mesh(system=1, K=(3, 2, 2), n=n, flux=1, limiter=1, gamma=G, precision=1)
+    gm.set_c2p_net(trained)
+    U = om.from_prim(di.blast_sr(om.coords(), seed=4))
+    Ro = om.rhs(U)
+    Rl = gm.rhs(_gpu(U)).cpu().numpy()
+    assert gm.sync_status() == 0
+    sc = np.abs(Ro).max(axis=(0, 2))
+    sc = np.maximum(sc, 1e-2 * sc.max())
+    assert (np.abs(Rl - Ro).max(axis=(0, 2)) / sc).max() < 1e-4
+    Ug = _gpu(U)
+    for _ in range(3):
+        h = om.cfl_dt(U, 0.2)
+        U = om.rk3_step(U, h)
+        gm.rk3_step(Ug, dt=h)
+    assert gm.sync_status() == 0
+    d = _rel_l2(om, Ug.cpu().numpy(), U)
+    assert np.all(d <= 1e-6), d
+
+
 def test_learned_guess_cfl_steps_conserve(pkg, trained):
     """CFL-driven steps with the learned guess: device status clean, totals
     conserved to FP32 rounding of the fluxes."""
