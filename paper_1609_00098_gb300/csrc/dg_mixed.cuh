@@ -470,10 +470,10 @@ struct StageShape {
     static constexpr int MAXT = NP == 5 ? 2 * TPE : (TPE > 256 ? TPE : 256);
     static constexpr int MAX_EPB = MAXT / TPE;
     // CTAs of MAXT threads that must fit on an SM: this caps the registers at 64
-    // per thread (80 for n = 7).  A few spills, but occupancy matters more: at
-    // n = 5 a 90-96 register build was 4-8 % slower, and capping n = 6, 7, 8 (they
-    // used 92-114) made the 256-mesh ensemble step 24 % faster.
-    static constexpr int MIN_CTAS = NP == 5 ? 3 : (NN <= 128 ? 4 : (NP == 6 ? 4 : 2));
+    // per thread (56 for n = 7).  Spills, but occupancy matters more: at n = 5 a
+    // 90-96 register build was 4-8 % slower, and capping n = 6, 7, 8 (they used
+    // 92-114) made the 256-mesh ensemble step 26 % faster.
+    static constexpr int MIN_CTAS = NP == 5 ? 3 : (NN <= 128 ? 4 : (NP == 6 ? 4 : (NP == 7 ? 3 : 2)));
 };
 
 // Shared memory of k_stage_mixed: per element (stride ELEM) the main arrays,
