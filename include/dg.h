@@ -298,7 +298,8 @@ int dg_ensemble_mesh_group(const dg_ensemble *ens, int i);
 dg_status dg_ensemble_dt(const dg_ensemble *ens, double *dt, void *stream);
 
 /* Synchronise `stream`, then read and clear the mesh's device status word.
- * Returns DG_OK, DG_ERR_C2P or DG_ERR_UNPHYSICAL (first set), or DG_ERR_CUDA. */
+ * Returns DG_OK, DG_ERR_C2P, DG_ERR_UNPHYSICAL or DG_ERR_TIMEOUT (a bounded wait
+ * for the learned guess's weights ran out; first set), or DG_ERR_CUDA. */
 dg_status dg_sync_status(dg_mesh *mesh, void *stream);
 
 /* Per-kernel timing.  When enabled, the library records a CUDA event pair on the
