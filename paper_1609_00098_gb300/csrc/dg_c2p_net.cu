@@ -393,8 +393,10 @@ __global__ void k_net_image(const float *P, NetWeightsSmem *img)
         img->W2h[j][i] = __float2bfloat16_rn(i < 64 ? 0.5f * P[OFF_W2 + j * 64 + i] : 0.0f);
     }
     for (int j = threadIdx.x; j < 64; j += blockDim.x) {
-        img->W1b1h[j] = make_float4(0.5f * P[OFF_W1 + 3 * j], 0.5f * P[OFF_W1 + 3 * j + 1],
-                                    0.5f * P[OFF_W1 + 3 * j + 2], 0.5f * P[OFF_B1 + j]);
+        img->W1b1h[j] = make_float4(__uint_as_float(to_tf32(0.5f * P[OFF_W1 + 3 * j])),
+                                    __uint_as_float(to_tf32(0.5f * P[OFF_W1 + 3 * j + 1])),
+                                    __uint_as_float(to_tf32(0.5f * P[OFF_W1 + 3 * j + 2])),
+                                    __uint_as_float(to_tf32(0.5f * P[OFF_B1 + j])));
         img->b2h[j] = 0.5f * P[OFF_B2 + j];
         img->W3[j] = P[OFF_W3 + j];
     }

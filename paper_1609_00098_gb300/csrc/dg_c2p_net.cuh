@@ -96,6 +96,25 @@ __device__ __forceinline__ uint32_t silu_half_bf16x2(float lo, float hi)
     return h;
 }
 
+// TF32 rounding (round to nearest, ties away) of an FP32 value, as an FP32 bit pattern.
+__device__ __forceinline__ uint32_t to_tf32(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+// D = A B + D for one m16n8k8 TF32 tile whose A has columns 4-7 zero (a2 = a3 = 0)
+// and whose B has rows 4-7 zero (b1 = 0): a K = 4 product on the tensor cores.
+__device__ __forceinline__ void mma_tf32_k4(float d[4], uint32_t a0, uint32_t a1, uint32_t b0)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%6}, {%7,%6}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(0u), "r"(b0));
+}
+
 // Four 8 x 8 BF16 matrices from shared memory; this lane gives the address of one
 // row (lanes 8m..8m+7: the rows of matrix m).
 __device__ __forceinline__ void ldmatrix_x4(uint32_t r[4], const void *row)
@@ -115,7 +134,7 @@ __device__ __forceinline__ void ldmatrix_x4(uint32_t r[4], const void *row)
 constexpr int NET_W2_LD = 72;
 struct NetWeightsSmem {
     __nv_bfloat16 W2h[64][NET_W2_LD];  // W2 / 2, [j][i]: the B^T operand of layer 2
-    float4 W1b1h[64];                   // (W1[j][0], W1[j][1], W1[j][2], b1[j]) / 2
+    float4 W1b1h[64];                   // (W1[j][0], W1[j][1], W1[j][2], b1[j]) / 2, TF32-rounded
     float b2h[64];                      // b2 / 2
     float W3[64];
     float b3, pad[3];
@@ -177,18 +196,13 @@ __device__ __forceinline__ void net_features(const float u[5], const float sc[6]
     f[5] = tau;
 }
 
-// Halved layer-1 pre-activation of hidden unit w for features x.
-__device__ __forceinline__ float net_z1h(const float4 w, float x0, float x1, float x2)
-{
-    return fmaf(w.z, x2, fmaf(w.y, x1, fmaf(w.x, x0, w.w)));
-}
-
 // Pressure guesses for `rows` states whose features sF[r][6] (net_features) sit in
-// shared memory; writes sG[r].  Each warp takes 16-row tiles: layer 1 is evaluated
-// straight into the BF16 A fragments of layer 2 (every hidden value belongs to
-// exactly one lane), layer 2 runs as mma.sync m16n8k16 (BF16 in, FP32 accumulate,
-// starting from the bias) with its B fragments loaded by ldmatrix, and layer 3 is a
-// per-row dot product reduced over the four lanes of a row.  States with non-finite
+// shared memory; writes sG[r].  Each warp takes 16-row tiles.  Layer 1 runs as
+// TF32 mma.sync m16n8k8 with K = 4 (the three features and a constant 1 for the
+// bias); its accumulator fragments are laid out as layer 2's A fragments, which
+// the BF16x2 SiLU packs directly.  Layer 2 runs as mma.sync m16n8k16 (BF16 in, FP32
+// accumulate, starting from the bias) with its B fragments loaded by ldmatrix, and
+// layer 3 is a per-row dot product reduced over the four lanes of a row.  States with non-finite
 // features (unphysical or non-positive D, tau) get -1, which con2prim reads as "no
 // guess".
 __device__ __forceinline__ void net_guess_rows(const NetWeightsSmem &W, const float (*sF)[6], float *sG, int rows,
@@ -201,8 +215,9 @@ __device__ __forceinline__ void net_guess_rows(const NetWeightsSmem &W, const fl
     const int lr_n = (lane & 7) + 8 * (lane >> 4), lr_k = 8 * ((lane >> 3) & 1);
     for (int r0 = warp * 16; r0 < rows; r0 += nwarps * 16) {
         const int ra = min(r0 + g, rows - 1), rb = min(r0 + g + 8, rows - 1);
-        const float xa0 = sF[ra][0], xa1 = sF[ra][1], xa2 = sF[ra][2];
-        const float xb0 = sF[rb][0], xb1 = sF[rb][1], xb2 = sF[rb][2];
+        // layer 1's A fragment: column tq of rows ra, rb is feature tq (tq < 3) or 1
+        const uint32_t fa = to_tf32(tq < 3 ? sF[ra][tq] : 1.0f), fb = to_tf32(tq < 3 ? sF[rb][tq] : 1.0f);
+        const float *w1 = reinterpret_cast<const float *>(W.W1b1h);  // [64][4]
         float acc[8][4];
 #pragma unroll
         for (int nt = 0; nt < 8; ++nt) {
@@ -214,13 +229,15 @@ __device__ __forceinline__ void net_guess_rows(const NetWeightsSmem &W, const fl
         }
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk) {
-            const int c0 = kk * 16 + 2 * tq;
-            const float4 w0 = W.W1b1h[c0], w1 = W.W1b1h[c0 + 1], w8 = W.W1b1h[c0 + 8], w9 = W.W1b1h[c0 + 9];
-            uint32_t af[4];  // rows (g, g+8) x hidden units (c0, c0+1 | c0+8, c0+9)
-            af[0] = silu_half_bf16x2(net_z1h(w0, xa0, xa1, xa2), net_z1h(w1, xa0, xa1, xa2));
-            af[1] = silu_half_bf16x2(net_z1h(w0, xb0, xb1, xb2), net_z1h(w1, xb0, xb1, xb2));
-            af[2] = silu_half_bf16x2(net_z1h(w8, xa0, xa1, xa2), net_z1h(w9, xa0, xa1, xa2));
-            af[3] = silu_half_bf16x2(net_z1h(w8, xb0, xb1, xb2), net_z1h(w9, xb0, xb1, xb2));
+            // halved pre-activations of hidden units 16 kk .. 16 kk + 15 (two n-tiles)
+            float z0[4] = {0.0f, 0.0f, 0.0f, 0.0f}, z1[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            mma_tf32_k4(z0, fa, fb, __float_as_uint(w1[(16 * kk + g) * 4 + tq]));
+            mma_tf32_k4(z1, fa, fb, __float_as_uint(w1[(16 * kk + 8 + g) * 4 + tq]));
+            uint32_t af[4];  // rows (g, g+8) x hidden units (16 kk + 2tq, +1 | +8, +9)
+            af[0] = silu_half_bf16x2(z0[0], z0[1]);
+            af[1] = silu_half_bf16x2(z0[2], z0[3]);
+            af[2] = silu_half_bf16x2(z1[0], z1[1]);
+            af[3] = silu_half_bf16x2(z1[2], z1[3]);
 #pragma unroll
             for (int nt2 = 0; nt2 < 4; ++nt2) {
                 uint32_t bq[4];
