@@ -520,6 +520,18 @@ struct MixedSmem {
     }
 };
 
+// Physicality (bit 0 set if unphysical, as sr_unphysical) and whether the conserved
+// fix of Sec. 2.1.4 would change u (bit 1, as a nonzero sr_fix), from one FP64
+// evaluation of S^2 and tau (tau + 2D), without the fix's rescaling.
+__device__ __forceinline__ unsigned sr_check64(double d_atm, double tau_atm, const double u[5])
+{
+    const double s2 = u[1] * u[1] + u[2] * u[2] + u[3] * u[3];
+    const double tt = u[4] * (u[4] + 2.0 * u[0]);
+    const bool bad = !(u[0] > 0.0) || !(u[4] > 0.0) || !(s2 < tt);
+    const bool fix = !(u[0] >= d_atm) || !(u[4] >= tau_atm * u[0]) || s2 > (1.0 - 1e-12) * tt;
+    return (bad ? 1u : 0u) | (fix ? 2u : 0u);
+}
+
 // FP32 screen of the bounds of the conserved fix (Sec. 2.1.4) and of physicality;
 // nodes that fail it are decided in FP64.
 __device__ __forceinline__ bool sr_screen32(const float u[5], float d_atm, float tau_atm)
@@ -869,13 +881,13 @@ __global__ void __launch_bounds__(StageShape<NP>::MAXT, StageShape<NP>::MIN_CTAS
 #pragma unroll
         for (int v = 0; v < 5; ++v) u32[v] = f64_to_f32(val[v]);
         if (sr_screen32(u32, (float)a.d_atm, (float)a.tau_atm)) {
-            bad = sr_unphysical(val);
-            double w[5] = {val[0], val[1], val[2], val[3], val[4]};
-            if (sr_fix(a.d_atm, a.tau_atm, w)) {
-                needfix = true;
-                if (!a.lim)
-#pragma unroll
-                    for (int v = 0; v < 5; ++v) val[v] = w[v];
+            if (a.lim) {
+                // the limiter runs the fix; here only its decision and physicality
+                const unsigned c = sr_check64(a.d_atm, a.tau_atm, val);
+                bad = c & 1u;
+                needfix = c & 2u;
+            } else {
+                sr_fix(a.d_atm, a.tau_atm, val);
             }
         }
     }
@@ -950,7 +962,8 @@ __global__ void __launch_bounds__(StageShape<NP>::MAXT, StageShape<NP>::MIN_CTAS
 // with the divisions by dx and dx/beta taken as products with host reciprocals.
 // A limited variable becomes U0 + sum_a slope_a (x_a - x_a0) (eq:MinModSol) in
 // FP64; then (SR) the conserved fix of Sec. 2.1.4 runs in FP64 on every node that
-// an FP32 screen of its bounds does not clear.  Elements that are neither
+// an FP32 screen of its bounds does not clear (such nodes are gathered, so the
+// FP64 fix runs in as few warp passes as possible).  Elements that are neither
 // troubled nor flagged by the stage kernel as needing the fix are left alone.
 // Like the stage kernel, a launch covers one mesh or a ragged batch of meshes.
 struct LimitSlot {
@@ -1044,34 +1057,54 @@ __global__ void __launch_bounds__(256) k_limit_mixed(const LimitMixedArgs a)
         if (lane < NP) sH2[wl][lane] = sl.hdx[2] * a.x[lane];
         __syncwarp();
     }
-    for (int q = lane; q < NN; q += 32) {
+    // Node values: the replacement of the limited variables, else the stage state.
+    auto node = [&](int q, double u[5]) {
         const int ij = q % (NP * NP), k = q / (NP * NP);
         const double h2 = mask ? sH2[wl][k] : 0.0;
-        double u[5];
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
             const long long ix = (e * 5 + v) * NN + q;
             u[v] = (mask & (1u << v)) ? fma(s2[v], h2, sAB[wl][v][ij]) : sl.U[ix];
         }
-        unsigned nm = mask;
-        if (SYS == 1) {
-            float u32[5];
+    };
+    // Nodes the FP32 screen does not clear are listed and fixed afterwards in full
+    // warps: a warp-wide FP64 instruction costs the same with one lane active.
+    __shared__ unsigned short sFix[8][NN];
+    int nfix = 0;
+    for (int q0 = 0; q0 < NN; q0 += 32) {
+        const int q = q0 + lane;
+        bool need = false;
+        if (q < NN) {
+            double u[5];
+            node(q, u);
+            if (SYS == 1) {
+                float u32[5];
 #pragma unroll
-            for (int v = 0; v < 5; ++v) u32[v] = f64_to_f32(u[v]);
-            if (sr_screen32(u32, (float)a.d_atm, (float)a.tau_atm)) {
-                double w[5] = {u[0], u[1], u[2], u[3], u[4]};
-                if (sr_fix(a.d_atm, a.tau_atm, w))
-#pragma unroll
-                    for (int v = 0; v < 5; ++v)
-                        if (w[v] != u[v]) {
-                            nm |= 1u << v;
-                            u[v] = w[v];
-                        }
+                for (int v = 0; v < 5; ++v) u32[v] = f64_to_f32(u[v]);
+                need = sr_screen32(u32, (float)a.d_atm, (float)a.tau_atm);
             }
-        }
+            if (!need)
 #pragma unroll
-        for (int v = 0; v < 5; ++v)
-            if (nm & (1u << v)) sl.U[(e * 5 + v) * NN + q] = u[v];
+                for (int v = 0; v < 5; ++v)
+                    if (mask & (1u << v)) sl.U[(e * 5 + v) * NN + q] = u[v];
+        }
+        if (SYS == 1) {
+            const unsigned b = __ballot_sync(0xffffffffu, need);
+            if (need) sFix[wl][nfix + __popc(b & ((1u << lane) - 1u))] = (unsigned short)q;
+            nfix += __popc(b);
+        }
+    }
+    if (SYS == 1 && nfix) {
+        __syncwarp();
+        for (int r = lane; r < nfix; r += 32) {
+            const int q = sFix[wl][r];
+            double u[5];
+            node(q, u);
+            const unsigned nm = mask | sr_fix(a.d_atm, a.tau_atm, u);
+#pragma unroll
+            for (int v = 0; v < 5; ++v)
+                if (nm & (1u << v)) sl.U[(e * 5 + v) * NN + q] = u[v];
+        }
     }
 }
 

@@ -250,13 +250,14 @@ __device__ __forceinline__ double max_speed(double g, const double u[5], const d
 }
 
 // SR conserved-variable fix (Sec. 2.1.4): D >= d_atm, tau >= tau_atm D and
-// S^2 <= (1 - 1e-12) tau (tau + 2D).  Returns true if u changed.
-__device__ __forceinline__ bool sr_fix(double d_atm, double tau_atm, double u[5])
+// S^2 <= (1 - 1e-12) tau (tau + 2D).  Returns the variables it set, as a bit
+// mask (bit v for u[v]; the three momenta together), 0 if u is unchanged.
+__device__ __forceinline__ unsigned sr_fix(double d_atm, double tau_atm, double u[5])
 {
-    bool ch = false;
-    if (!(u[0] >= d_atm)) { u[0] = d_atm; ch = true; }
+    unsigned ch = 0;
+    if (!(u[0] >= d_atm)) { u[0] = d_atm; ch |= 1u; }
     const double tmin = tau_atm * u[0];
-    if (!(u[4] >= tmin)) { u[4] = tmin; ch = true; }
+    if (!(u[4] >= tmin)) { u[4] = tmin; ch |= 16u; }
     const double s2 = u[1] * u[1] + u[2] * u[2] + u[3] * u[3];
     const double s2max = (1.0 - 1e-12) * (u[4] * (u[4] + 2.0 * u[0]));
     if (s2 > s2max) {
@@ -264,7 +265,7 @@ __device__ __forceinline__ bool sr_fix(double d_atm, double tau_atm, double u[5]
         u[1] *= f;
         u[2] *= f;
         u[3] *= f;
-        ch = true;
+        ch |= 14u;
     }
     return ch;
 }
