@@ -989,8 +989,13 @@ struct LimitMixedArgs {
     double x[MAXN];         // LGL nodes
 };
 
+// Warps (elements) per CTA of the limiter: small CTAs spread a one-wave launch
+// evenly over the SMs (with 8 warps per CTA, 4,096 elements left some SMs a third
+// more work than others).
+constexpr int kLimitWarps = 4;
+
 template <int NP, int SYS>
-__global__ void __launch_bounds__(256) k_limit_mixed(const LimitMixedArgs a)
+__global__ void __launch_bounds__(32 * kLimitWarps) k_limit_mixed(const LimitMixedArgs a)
 {
     constexpr int NN = NP * NP * NP;
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -1035,9 +1040,9 @@ __global__ void __launch_bounds__(256) k_limit_mixed(const LimitMixedArgs a)
     // The replacement m0 + s0 h0(i) + s1 h1(j) + s2 h2(k) (h_a = (dx_a/2) xbar): the
     // part m0 + s0 h0(i) + s1 h1(j) is built once per (i, j) plane point and
     // variable, so a node costs one FP64 FMA per limited variable.
-    __shared__ double sAB[8][5][NP * NP];  // per warp of the CTA
-    __shared__ double sH2[8][NP];
-    const int wl = (threadIdx.x >> 5) & 7;
+    __shared__ double sAB[kLimitWarps][5][NP * NP];  // per warp of the CTA
+    __shared__ double sH2[kLimitWarps][NP];
+    const int wl = threadIdx.x >> 5;
     double s2[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) s2[v] = __shfl_sync(0xffffffffu, slope, 3 * v + 2);
@@ -1069,7 +1074,7 @@ __global__ void __launch_bounds__(256) k_limit_mixed(const LimitMixedArgs a)
     };
     // Nodes the FP32 screen does not clear are listed and fixed afterwards in full
     // warps: a warp-wide FP64 instruction costs the same with one lane active.
-    __shared__ unsigned short sFix[8][NN];
+    __shared__ unsigned short sFix[kLimitWarps][NN];
     int nfix = 0;
     for (int q0 = 0; q0 < NN; q0 += 32) {
         const int q = q0 + lane;
@@ -1136,10 +1141,9 @@ template <int NP>
 cudaError_t launch_limit_mixed_np(int system, const LimitMixedArgs &a, cudaStream_t s)
 {
     if (a.E <= 0) return cudaSuccess;
-    const long long threads = a.E * 32;
-    const unsigned grid = (unsigned)((threads + 255) / 256);
-    if (system == 0) k_limit_mixed<NP, 0><<<grid, 256, 0, s>>>(a);
-    else k_limit_mixed<NP, 1><<<grid, 256, 0, s>>>(a);
+    const unsigned grid = (unsigned)((a.E + kLimitWarps - 1) / kLimitWarps);  // one warp per element
+    if (system == 0) k_limit_mixed<NP, 0><<<grid, 32 * kLimitWarps, 0, s>>>(a);
+    else k_limit_mixed<NP, 1><<<grid, 32 * kLimitWarps, 0, s>>>(a);
     return cudaGetLastError();
 }
 

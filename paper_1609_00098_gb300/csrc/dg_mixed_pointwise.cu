@@ -23,7 +23,7 @@ struct CflNetSmem {
 // and (warm start) the pressures for the first stage.  GUESS: con2prim starts from
 // the learned network's guess, evaluated per chunk on the tensor cores.
 template <int SYS, int GUESS>
-__global__ void __launch_bounds__(kThreads) k_cfl_mixed(const CflArgs a)
+__global__ void __launch_bounds__(kThreads, 4) k_cfl_mixed(const CflArgs a)
 {
     extern __shared__ __align__(16) unsigned char cfl_smem[];
     CflNetSmem &N = *reinterpret_cast<CflNetSmem *>(cfl_smem);
