@@ -253,7 +253,7 @@ dg_status dg_mesh_set_option(dg_mesh *mesh, int option, double value);
  * except the first stage of a CFL step, whose input U^n the CFL pass has just
  * solved with the network's guesses: it starts from those pressures.  Without a
  * network, con2prim starts from the pressure of the previous pass (carried in
- * library scratch).  Newton stays the judge: the guess changes only the
+ * library scratch).  Newton decides the result: the guess changes only the
  * iteration count and the result within the solver's stopping tolerance.  The
  * mesh does not own the network: it must stay alive while the mesh uses it, and
  * training it in place changes the guesses of later calls.  Errors: DG_ERR_ARG

@@ -3,8 +3,8 @@
 TEST INFRASTRUCTURE ONLY (part of the oracle; see oracle/__init__.py).
 
 The network maps three scaled invariants of the SR conserved state to a scaled
-log-pressure; con2prim's safeguarded Newton (Sec. 2.1.2) starts from it and stays
-the judge of the result.  Architecture 3 -> 64 -> 64 -> 1 with SiLU activations,
+log-pressure; con2prim's safeguarded Newton (Sec. 2.1.2) starts from it and alone
+decides the result.  Architecture 3 -> 64 -> 64 -> 1 with SiLU activations,
 4,481 parameters laid out flat as
 
     W1[64][3], b1[64], W2[64][64], b2[64], W3[64], b3[1]

@@ -165,7 +165,7 @@ def test_mrs_leaves_linear_data_alone():
     m = _mrs_mesh(8, 4, 0.0, dim=3)
     x, y, z = m.coords()
     prim = np.stack([1.5 + 0.2 * x, 0.3 + 0 * x, -0.2 + 0 * x, 0.1 + 0 * x, 1.0 + 0.1 * x])
-    # periodic wrap breaks linearity at the box edge: judge interior elements only
+    # periodic wrap breaks linearity at the box edge: check interior elements only
     U = m.from_prim(prim)
     V, t = m.limit(U)
     xc = x.reshape(m.E, -1).mean(axis=1)
