@@ -296,8 +296,6 @@ def _measure(pkg, torch, precision, args, dist, U0, net=None):
     if net is not None:
         mesh.set_c2p_net(net)
     shape = None
-    if precision == 1:
-        shape = _tune_launch_shape(pkg, mesh, U0)
     U = U0.clone()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     for _ in range(args.warmup):
@@ -305,6 +303,9 @@ def _measure(pkg, torch, precision, args, dist, U0, net=None):
     torch.cuda.synchronize()
     if mesh.sync_status() != 0:
         raise RuntimeError("warm-up steps reported a device error")
+    if precision == 1:
+        # tuned on the warmed-up state, the one the timed steps start from
+        shape = _tune_launch_shape(pkg, mesh, U)
     graph = torch.cuda.CUDAGraph()
     side = torch.cuda.Stream()
     side.wait_stream(torch.cuda.current_stream())
@@ -344,7 +345,7 @@ def _measure(pkg, torch, precision, args, dist, U0, net=None):
 def _tune_launch_shape(pkg, mesh, U0):
     """Pick the stage kernel's elements per CTA and volume contraction for this
     mesh with the library's autotuner (a one-mesh ensemble times the candidates
-    on the initial state), and set them on the mesh (untimed)."""
+    on a copy of the given state), and set them on the mesh (untimed)."""
     U = U0.clone()
     ens = pkg.abi.dg_ensemble_create([mesh.h], [U])
     try:
