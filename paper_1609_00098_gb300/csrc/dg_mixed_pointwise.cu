@@ -21,7 +21,8 @@ struct CflNetSmem {
 // CFL pass: FP32 primitives of U^n at every node, the largest wave speed (block
 // max, then an integer atomicMax on the bit pattern: exact and order-independent),
 // and (warm start) the pressures for the first stage.  GUESS: con2prim starts from
-// the learned network's guess, evaluated per chunk on the tensor cores.
+// the learned network's guess, evaluated per chunk on the tensor cores.  Four CTAs
+// per SM cap the registers at 64 (the SR variants used 74-80, three CTAs).
 template <int SYS, int GUESS>
 __global__ void __launch_bounds__(kThreads, 4) k_cfl_mixed(const CflArgs a)
 {
