@@ -142,7 +142,7 @@ TRAFFIC_BYTES_PER_LAUNCH = 38690727.0
 TRAFFIC_SOURCES = ("paper_1609_00098_gb300/csrc/dg_mixed.cuh", "paper_1609_00098_gb300/csrc/dg_physics.cuh",
                    "paper_1609_00098_gb300/csrc/dg_internal.h", "paper_1609_00098_gb300/csrc/dg_c2p_net.cuh",
                    "paper_1609_00098_gb300/csrc/dg_api.cu")
-TRAFFIC_SOURCES_SHA256 = "7fafa9cd8a731ea0f28b6f9b9dfa47e10df571221a1093a7bf73d4d878dc3618"
+TRAFFIC_SOURCES_SHA256 = "b2f0d951b38752a732040ff7c665d4a125ae41b1c6a8c7c5cf13899394c49ee4"
 TRAFFIC_VARIANT = "learned"
 
 
