@@ -5,6 +5,47 @@
 
 namespace dg {
 
+// Sign tests, minmod (eq:MinMod) and magnitude comparisons of doubles done on
+// their bit patterns, on the integer ALU instead of the FP64 pipe (which bounds
+// this kernel).  They decide exactly as the floating-point forms, NaN included:
+// - a double is > 0 iff its bits, read as a signed integer, lie in (0, +inf];
+// - it is < 0 iff its sign bit is set and its magnitude bits lie in (0, inf]
+//   (-0 is not negative);
+// - doubles of one sign are ordered like their bits, reversed for negatives, so
+//   among three positive or three negative doubles the one closest to 0 (the
+//   minmod pick) has the smallest bit pattern as a signed integer;
+// - |x| > c and |x| <= c for a finite c >= 0 compare the magnitude bits with c's.
+constexpr long long kMagBits = 0x7fffffffffffffffLL;
+constexpr long long kInfBits = 0x7ff0000000000000LL;
+
+__device__ __forceinline__ bool bits_pos(long long b) { return b > 0 && b <= kInfBits; }
+__device__ __forceinline__ bool bits_neg(long long b)
+{
+    const long long m = b & kMagBits;
+    return b < 0 && m != 0 && m <= kInfBits;
+}
+
+__device__ __forceinline__ double minmod3_bits(double a1, double a2, double a3)
+{
+    const long long b1 = __double_as_longlong(a1), b2 = __double_as_longlong(a2), b3 = __double_as_longlong(a3);
+    const bool pos = bits_pos(b1) & bits_pos(b2) & bits_pos(b3);
+    const bool neg = bits_neg(b1) & bits_neg(b2) & bits_neg(b3);
+    return (pos | neg) ? __longlong_as_double(min(b1, min(b2, b3))) : 0.0;
+}
+
+// |x| > c, for finite c >= 0
+__device__ __forceinline__ bool abs_gt(double x, double c)
+{
+    const long long m = __double_as_longlong(x) & kMagBits;
+    return m > __double_as_longlong(c) && m <= kInfBits;
+}
+
+// |x| <= c, for finite c >= 0
+__device__ __forceinline__ bool abs_le(double x, double c)
+{
+    return (__double_as_longlong(x) & kMagBits) <= __double_as_longlong(c);
+}
+
 // ---------------------------------------------------------------------------
 // Limiter of the mixed path on FP64 stage states, one warp per element.  Lane
 // 3v + a (v < 5, a < 3) decides variable v along axis a: the MinModN face tests
@@ -70,13 +111,13 @@ __global__ void __launch_bounds__(32 * kLimitWarps) k_limit_mixed(const LimitMix
         flag = (a.limiter == 2);
         if (a.limiter == 1) {
             const double ulo = Se[1 + 2 * ax], uhi = Se[2 + 2 * ax];
-            const double vl = U0 - minmod3(U0 - ulo, U0 - U0m, U0p - U0);
-            const double vr = U0 + minmod3(uhi - U0, U0 - U0m, U0p - U0);
-            if (fabs(vl - ulo) > 1e-8 || fabs(vr - uhi) > 1e-8) flag = 1;
+            const double vl = U0 - minmod3_bits(U0 - ulo, U0 - U0m, U0p - U0);
+            const double vr = U0 + minmod3_bits(uhi - U0, U0 - U0m, U0p - U0);
+            if (abs_gt(vl - ulo, 1e-8) || abs_gt(vr - uhi, 1e-8)) flag = 1;
         }
         const double s1 = 2.0 * Se[7 + ax] * sl.inv_dx[ax];
-        slope = (fabs(s1) <= sl.tvb[ax]) ? s1
-                                         : minmod3(s1, (U0p - U0) * sl.beta_dx[ax], (U0 - U0m) * sl.beta_dx[ax]);
+        slope = abs_le(s1, sl.tvb[ax]) ? s1
+                                       : minmod3_bits(s1, (U0p - U0) * sl.beta_dx[ax], (U0 - U0m) * sl.beta_dx[ax]);
     }
     const unsigned fb = __ballot_sync(0xffffffffu, flag);
     unsigned mask = 0;
