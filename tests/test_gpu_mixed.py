@@ -241,6 +241,30 @@ def test_elements_per_cta_do_not_change_results(pkg, n, epb):
         pkg.abi.dg_c2p_net_destroy(net)
 
 
+@pytest.mark.parametrize("K,n,system,epb", [((1, 1, 1), 2, 0, 1), ((1, 3, 1), 8, 1, 1), ((7, 1, 2), 3, 1, 4),
+                                            ((3, 1, 1), 5, 1, 2)])
+def test_mixed_edge_case_shapes(pkg, K, n, system, epb):
+    """Self-periodic K = 1 axes, ragged element counts (not a multiple of the
+    stage kernel's elements per CTA nor of the limiter's warps per CTA),
+    anisotropic boxes and both extreme n on the mixed path: two steps within the
+    mixed bar (1e-6 relative L2) of the oracle."""
+    om = oracle.Mesh(oracle.MeshSpec(system=system, K=K, n=n, flux=1, limiter=1, gamma=1.4 if system == 0 else 4 / 3,
+                                     lo=(0, -2, 0), hi=(1, 1, 0.25)))
+    gm = pkg.Mesh(system=system, K=K, n=n, flux=1, limiter=1, gamma=1.4 if system == 0 else 4 / 3,
+                  lo=(0, -2, 0), hi=(1, 1, 0.25), precision=1)
+    gm.set_option(pkg.abi.OPT_ELEMENTS_PER_CTA, epb)
+    xyz = om.coords()
+    U = om.from_prim(di.smooth_wave_ne(xyz, k=(1, 1, 1)) if system == 0 else di.blast_sr(xyz, seed=3))
+    Ug = _gpu(U)
+    for _ in range(2):
+        h = 0.5 * om.cfl_dt(U, 0.2)
+        U = om.rk3_step(U, h)
+        gm.rk3_step(Ug, dt=h)
+    assert gm.sync_status() == 0
+    d = _rel_l2(om, Ug.cpu().numpy(), U)
+    assert np.all(d <= 1e-6), d
+
+
 def test_mixed_roe(pkg):
     """Roe flux on the mixed path: RHS to FP32 rounding of the oracle's, and ten
     shear-layer steps within the 1e-6 bar."""
