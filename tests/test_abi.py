@@ -53,7 +53,14 @@ def test_argument_errors_need_no_gpu(lib_path):
     """Invalid descriptors are rejected synchronously, before any CUDA call."""
     import paper_1609_00098_gb300 as pkg
     for bad in (dict(n=1), dict(n=9), dict(system=2), dict(flux=3), dict(limiter=5), dict(gamma=1.0),
-                dict(K=(0, 1, 1)), dict(hi=(0.0, 1.0, 1.0)), dict(beta=0.0)):
+                dict(K=(0, 1, 1)), dict(hi=(0.0, 1.0, 1.0)), dict(beta=0.0), dict(tvb_M=-1.0),
+                dict(precision=2), dict(gamma=float("nan")),
+                dict(system=1, flux=2),                                   # Roe is Newtonian only
+                dict(system=1, limiter=3), dict(limiter=3, mrs_alpha=-1.0),  # MRS: Newtonian, alpha >= 0
+                dict(bc=(2, 0, 0)), dict(exact=2),
+                dict(bc=(1, 0, 0)),                                       # analytic faces need an exact solution
+                dict(bc=(1, 0, 0), exact=1, system=1),                    # ... the Newtonian system
+                dict(bc=(0, 1, 0), exact=1, limiter=1)):                  # ... and no limiter
         with pytest.raises(pkg.DGError) as ei:
             pkg.abi.dg_mesh_create(pkg.make_desc(**bad))
         assert ei.value.status == pkg.abi.DG_ERR_ARG
