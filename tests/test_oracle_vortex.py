@@ -118,6 +118,35 @@ def test_stage_times_keep_third_order():
     assert abs(runs[2][0].t - 0.4) < 1e-12
 
 
+def _run_composed(dt, ct, T=0.4, x0=8.5, y0=8.5):
+    """SSP-RK3 (Shu-Osher form) composed from the oracle's RHS, with the exterior
+    states of stage s taken at t + ct[s] dt."""
+    m = oracle.Mesh(_spec((8, 8, 1), 4, x0=x0, y0=y0))
+    U = m.from_prim(di.isentropic_vortex(m.coords(), 0.0, x0=x0, y0=y0))
+    t = 0.0
+    for _ in range(int(round(T / dt))):
+        m.t = t + ct[0] * dt
+        U1 = U + dt * m.rhs(U)
+        m.t = t + ct[1] * dt
+        U2 = 0.75 * U + 0.25 * (U1 + dt * m.rhs(U1))
+        m.t = t + ct[2] * dt
+        U = U / 3.0 + (2.0 / 3.0) * (U2 + dt * m.rhs(U2))
+        t += dt
+    return m, U
+
+
+def test_planted_stage_times_drop_to_first_order():
+    """The same SSP-RK3 composed from the oracle's RHS: with the stage times
+    (0, 1, 1/2) it reproduces the oracle's step to rounding; with every stage's
+    exterior state planted at t, the dt-halving ratio falls from ~8 to ~2."""
+    m, Uc = _run_composed(0.02, (0.0, 1.0, 0.5))
+    _, Uo = _run_fixed(0.02)
+    assert m.norms(Uc, Uo)[0].sum() <= 1e-12 * m.norms(Uo, np.zeros_like(Uo))[0].sum()
+    runs = [_run_composed(0.04 / 2 ** k, (0.0, 0.0, 0.0)) for k in range(3)]
+    d = [m.norms(runs[k][1], runs[k + 1][1])[0].sum() for k in range(2)]
+    assert 1.5 < d[0] / d[1] < 3.0, d
+
+
 @pytest.mark.parametrize("flux", [0, 1, 2])
 def test_uniform_flow_through_analytic_boundaries(flux):
     """beta = 0: the exterior state equals the interior one, every numerical flux
