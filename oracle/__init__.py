@@ -73,7 +73,9 @@ def _load():
     global _lib
     if _lib is not None:
         return _lib
-    lib = ctypes.CDLL(build())
+    # DG_ORACLE_LIB names another build of this same source (the planted-mistake
+    # tests load copies with one deliberate error through it)
+    lib = ctypes.CDLL(os.environ.get("DG_ORACLE_LIB") or build())
     vp = ctypes.c_void_p
     ll = ctypes.c_longlong
     sig = {

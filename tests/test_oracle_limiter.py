@@ -128,7 +128,10 @@ def test_fix_bounds():
     D, tau = F[0, 0], F[0, 4]
     s2 = F[0, 1] ** 2 + F[0, 2] ** 2 + F[0, 3] ** 2
     assert np.all(D >= 1e-12) and np.all(tau >= 1e-14 * D)
-    assert np.all(s2 <= (1 - 1e-12) * tau * (tau + 2 * D) * (1 + 1e-15))
+    bound = (1 - 1e-12) * tau * (tau + 2 * D)
+    assert np.all(s2 <= bound * (1 + 1e-15))
+    # the rescaled momentum sits on the bound (the fix takes no more than it must)
+    assert abs(s2[3] / bound[3] - 1) < 2e-15 and np.array_equal(F[0, 1:4, :3], U[0, 1:4, :3])
     _, _, st = oracle.con2prim(4 / 3, F[0])
     assert np.all(st == 0)
 

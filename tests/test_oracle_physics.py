@@ -123,15 +123,18 @@ def test_hll_reduces_to_upwind(system, gamma, vx):
 
 @pytest.mark.parametrize("system,gamma", [(0, 1.4), (1, 4.0 / 3.0)])
 def test_llf_equals_hll_for_symmetric_speeds(system, gamma):
-    # static states with equal sound speed: c_max = -c_min = alpha, and then
-    # the HLL formula is algebraically the LLF one
+    # static states with equal sound speed but different density and pressure
+    # (p / rho fixed, so c^2 = g p / rho, and in SR h and c_s, agree): c_max =
+    # -c_min = alpha, and then the HLL formula is algebraically the LLF one,
+    # dissipation term included (the jump U_R - U_L is not zero)
     pl = np.array([[1.0], [0.0], [0.0], [0.0], [1.0]])
-    pr = np.array([[1.0], [0.0], [0.0], [0.0], [1.0]])
+    pr = np.array([[2.0], [0.0], [0.0], [0.0], [2.0]])
     uL = oracle.prim2con(system, gamma, pl)[:, 0]
-    uR = oracle.prim2con(system, gamma, pr)[:, 0] * 1.0
-    uR[1] = 0.0
-    F0, *_ = oracle.num_flux(system, gamma, 0, 1, uL, uR)
+    uR = oracle.prim2con(system, gamma, pr)[:, 0]
+    F0, FL, FR, sp = oracle.num_flux(system, gamma, 0, 1, uL, uR)
     F1, *_ = oracle.num_flux(system, gamma, 1, 1, uL, uR)
+    assert sp[0] == -sp[1] and abs(sp[1] - sp[3]) <= 1e-15 * sp[1]
+    assert np.abs(F0 - 0.5 * (FL + FR)).max() > 0.1  # the dissipation term is in play
     assert np.allclose(F0, F1, rtol=1e-14, atol=1e-15)
 
 

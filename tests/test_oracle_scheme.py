@@ -105,6 +105,37 @@ def test_rk3_temporal_order():
     assert 2.7 < o1 < 3.4 and 2.7 < o2 < 3.4, (e, o1, o2)
 
 
+def _composed_wave_orders(w2, w3):
+    """Temporal orders of a Shu-Osher three-stage step composed from the oracle's
+    RHS with stage weights w2, w3 (U2 = w2 U + (1 - w2)(U1 + dt L), and likewise
+    w3), measured as in test_rk3_temporal_order; also the last state at dt = 0.008."""
+    sols = []
+    for dt in (0.008, 0.004, 0.002, 0.00025):
+        m = oracle.Mesh(oracle.MeshSpec(system=0, dim=1, K=(2, 1, 1), n=6, flux=0, gamma=1.4))
+        U = m.from_prim(di.smooth_wave_ne(m.coords(), 0.0, k=(1, 1, 1), vel=(1.0, 0.0, 0.0)))
+        for _ in range(int(round(0.4 / dt))):
+            U1 = U + dt * m.rhs(U)
+            U2 = w2 * U + (1.0 - w2) * (U1 + dt * m.rhs(U1))
+            U = w3 * U + (1.0 - w3) * (U2 + dt * m.rhs(U2))
+        sols.append(U)
+    e = [np.abs(s - sols[-1]).max() for s in sols[:3]]
+    return [math.log2(e[0] / e[1]), math.log2(e[1] / e[2])], sols[0]
+
+
+def test_planted_rk3_weights_fail_the_order_pin():
+    """The order pin catches a transcription error in the SSP-RK3 weights: the
+    step composed from the oracle's RHS with the Shu-Osher weights (3/4, 1/3)
+    reproduces the oracle's step to rounding and third order, while each planted
+    weight (1/2 or 1/4 for 3/4, 2/3 for 1/3) measures first order."""
+    orders, U = _composed_wave_orders(0.75, 1.0 / 3.0)
+    assert all(2.7 < o < 3.4 for o in orders), orders
+    _, Uo, _, _ = _ne_wave(2, 6, T=0.4, dt=0.008, dim=1)
+    assert np.abs(U - Uo).max() <= 1e-13 * np.abs(Uo).max()
+    for w2, w3 in ((0.5, 1.0 / 3.0), (0.25, 1.0 / 3.0), (0.75, 2.0 / 3.0)):
+        orders, _ = _composed_wave_orders(w2, w3)
+        assert all(o < 1.5 for o in orders), (w2, w3, orders)
+
+
 @pytest.mark.parametrize("system,limiter,flux", [(0, 0, 0), (0, 1, 1), (1, 1, 1), (1, 2, 0)])
 def test_discrete_conservation(system, limiter, flux):
     """Periodic mesh, single-valued F* at each face and the diagonal LGL mass
