@@ -193,6 +193,33 @@ def test_mrs_keeps_smooth_extrema_only_with_alpha():
     assert counts[0] > 0 and counts[1] == 0, counts
 
 
+def test_mrs_theta_closed_form_for_an_isolated_bump():
+    """eq:MRSSol (R16) on a density bump in one element of a uniform flow at rest:
+    velocity and pressure are constant, so only the density bounds act, the
+    neighbours' means lie below the bump's, and Theta = alpha h^{3/2} /
+    (rho_max - rho_0), h the element width.  The bump element becomes U0 +
+    Theta (U - U0); the others are untouched."""
+    K, n, alpha = 8, 4, 0.3
+    m = _mrs_mesh(K, n, alpha)
+    x = m.coords()[0]
+    e0 = 3
+    xc, h = (e0 + 0.5) / K, 1.0 / K
+    xi = (x - xc) / (0.5 * h)
+    bump = np.where(np.abs(x - xc) <= 0.5 * h + 1e-15, 0.2 * (1.0 - xi ** 2), 0.0)
+    prim = np.stack([1.0 + bump, np.zeros_like(x), np.zeros_like(x), np.zeros_like(x), np.ones_like(x)])
+    U = m.from_prim(prim)
+    L, t = m.limit(U)
+    S = m.summaries(U)
+    rho0 = S[e0, 0, 0]
+    theta = alpha * h ** 1.5 / (U[e0, 0].max() - rho0)
+    assert 0.2 < theta < 0.8
+    assert t[e0] != 0 and np.count_nonzero(t) == 1
+    U0 = S[e0, :, 0][:, None]
+    assert np.allclose(L[e0], U0 + theta * (U[e0] - U0), rtol=1e-13, atol=1e-14)
+    others = np.arange(m.E) != e0
+    assert np.array_equal(L[others], U[others])
+
+
 def test_mrs_needs_newtonian_and_nonnegative_alpha():
     for kw in (dict(system=1, gamma=4.0 / 3.0, mrs_alpha=1.0), dict(system=0, gamma=1.4, mrs_alpha=-1.0)):
         with pytest.raises(Exception):

@@ -138,6 +138,25 @@ def test_llf_equals_hll_for_symmetric_speeds(system, gamma):
     assert np.allclose(F0, F1, rtol=1e-14, atol=1e-15)
 
 
+@pytest.mark.parametrize("system,gamma,flux", [(0, 1.4, 0), (0, 1.4, 1), (0, 1.4, 2), (1, 4.0 / 3.0, 0),
+                                               (1, 4.0 / 3.0, 1)])
+def test_numerical_flux_mirror_symmetry(system, gamma, flux):
+    """The numerical fluxes of Sec. 3.2 treat both sides alike: mirroring x -> -x
+    (swap the states, flip their x momenta) flips the flux, F*(R u_R, R u_L) =
+    -R F*(u_L, u_R) with R = diag(1, -1, 1, 1, 1).  The states differ in density,
+    pressure and velocity, so each side has its own speeds."""
+    pl = np.array([[1.0], [0.3], [0.1], [0.0], [1.0]])
+    pr = np.array([[0.4], [-0.5], [0.2], [0.1], [0.3]]) if system == 0 else \
+        np.array([[0.4], [-0.6], [0.2], [0.1], [0.3]])
+    uL = oracle.prim2con(system, gamma, pl)[:, 0]
+    uR = oracle.prim2con(system, gamma, pr)[:, 0]
+    R = np.array([1.0, -1.0, 1.0, 1.0, 1.0])
+    Fs, _, _, sp = oracle.num_flux(system, gamma, flux, 0, uL, uR)
+    Fm, _, _, _ = oracle.num_flux(system, gamma, flux, 0, R * uR, R * uL)
+    assert max(abs(sp[0]), abs(sp[1])) != max(abs(sp[2]), abs(sp[3]))
+    assert np.allclose(Fm, -R * Fs, rtol=1e-13, atol=1e-14), (Fm, -R * Fs)
+
+
 def test_sr_speeds_limits():
     # at v = 0 the SR speeds are -+cs with cs^2 = g p / (rho h)
     g = 4.0 / 3.0

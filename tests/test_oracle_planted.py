@@ -54,6 +54,23 @@ PLANTED = {
     # the element slope U_x = 2 c_1 / dx without its factor 2
     "limiter_slope_factor": ("minmodB(2.0 * Se[7 + a] / m->dx[a],", "minmodB(Se[7 + a] / m->dx[a],",
                              ["tests/test_oracle_limiter.py"]),
+    # CFL: dx_min as the element half-width instead of the smallest LGL node gap (R4)
+    "cfl_dxmin": ("double h = 0.5 * m->dx[a] * (m->x[1] - m->x[0]);", "double h = 0.5 * m->dx[a];",
+                  ["tests/test_oracle_scheme.py::test_cfl_dt_closed_form",
+                   "tests/test_oracle_scheme.py::test_ne_smooth_wave_exact_and_order"]),
+    # eq:LLF with alpha from the left state only
+    "llf_alpha_one_side": ("double al = fmax(fmax(fabs(lminL), fabs(lmaxL)), fmax(fabs(lminR), fabs(lmaxR)));",
+                           "double al = fmax(fabs(lminL), fabs(lmaxL));",
+                           ["tests/test_oracle_physics.py::test_numerical_flux_mirror_symmetry"]),
+    # prim2con (stable form) with the p (W^2 - 1) term of tau dropped
+    "prim2con_dropped_term": ("u[4] = rho * W * (W2v2 / (W + 1.0)) + rhoeps * W * W + p * W2v2;",
+                              "u[4] = rho * W * (W2v2 / (W + 1.0)) + rhoeps * W * W;",
+                              ["tests/test_oracle_physics.py"]),
+    # the differentiation matrix's diagonal with the wrong sign (negative-sum trick)
+    "dmat_diagonal_sign": ("D[i * n + i] = -s;", "D[i * n + i] = s;", ["tests/test_oracle_lgl.py"]),
+    # MRS bound widening alpha h instead of alpha h^{3/2} (eq:MRSSol, R16)
+    "mrs_width_exponent": ("const double wid = m->d.mrs_alpha * h * sqrt(h);", "const double wid = m->d.mrs_alpha * h;",
+                           ["tests/test_oracle_limiter.py::test_mrs_theta_closed_form_for_an_isolated_bump"]),
     # the fix's momentum bound tau (tau + 2 D) with the factor 2 dropped
     "fix_bound": ("(1.0 - 1e-12) * (*tau * (*tau + 2.0 * *D));", "(1.0 - 1e-12) * (*tau * (*tau + *D));",
                   ["tests/test_oracle_limiter.py::test_fix_bounds"]),

@@ -91,6 +91,20 @@ def test_ne_smooth_wave_exact_and_order():
     assert e1 < 0.1 * wave and e2 < e1 / 8, (e1, e2, wave)
 
 
+def test_cfl_dt_closed_form():
+    """Sec. 3.4 with reading R4: dt = C dx_min / lambda_max, dx_min the smallest
+    gap between neighbouring LGL nodes on the physical grid, min_a (dx_a/2)(1 -
+    1/sqrt(5)) for n = 4 (nodes -1, -1/sqrt 5, 1/sqrt 5, 1), and lambda_max = |v| + c
+    for a uniform Newtonian state (c^2 = gamma p / rho)."""
+    m = oracle.Mesh(oracle.MeshSpec(system=0, K=(4, 2, 8), n=4, flux=0, gamma=1.4))
+    xyz = m.coords()
+    one = np.ones_like(xyz[0])
+    U = m.from_prim(np.stack([2.0 * one, -0.5 * one, 0.0 * one, 0.0 * one, 3.0 * one]))
+    lam = 0.5 + math.sqrt(1.4 * 3.0 / 2.0)
+    ref = 0.2 * (0.5 / 8) * (1.0 - 1.0 / math.sqrt(5.0)) / lam
+    assert abs(m.cfl_dt(U, 0.2) / ref - 1.0) < 1e-14
+
+
 def test_rk3_temporal_order():
     """Shu-Osher SSP-RK3 is third order in time: halving dt at a fixed, spatially
     converged mesh divides the error by ~8."""
