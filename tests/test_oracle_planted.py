@@ -54,6 +54,19 @@ PLANTED = {
     # the element slope U_x = 2 c_1 / dx without its factor 2
     "limiter_slope_factor": ("minmodB(2.0 * Se[7 + a] / m->dx[a],", "minmodB(Se[7 + a] / m->dx[a],",
                              ["tests/test_oracle_limiter.py"]),
+    # eq:411 volume term with the wrong sign
+    "volume_sign": ("acc = acc + (2.0 / m->dx[a]) * s;", "acc = acc - (2.0 / m->dx[a]) * s;",
+                    ["tests/test_oracle_scheme.py::test_ne_smooth_wave_exact_and_order"]),
+    # limiter summaries: the upper face mean taken one node line inside the element
+    "summary_face_index": ("S[2 + 2 * a] = ubar[n - 1];", "S[2 + 2 * a] = ubar[n - 2];",
+                           ["tests/test_oracle_limiter.py::test_linear_data_not_limited"]),
+    # limiter summaries: the element slope from the P2 instead of the P1 Legendre coefficient (R5)
+    "summary_p1_row": ("for (int i = 0; i < n; ++i) c1 = c1 + m->Vinv[1 * n + i] * ubar[i];",
+                       "for (int i = 0; i < n; ++i) c1 = c1 + m->Vinv[2 * n + i] * ubar[i];",
+                       ["tests/test_oracle_limiter.py"]),
+    # eq:Roe: the u - c wave weighted by |u + c|
+    "roe_wave_speed": ("const double w1 = fabs(un - c) * al1,", "const double w1 = fabs(un + c) * al1,",
+                       ["tests/test_oracle_physics.py::test_roe_flux_matches_eigendecomposition"]),
     # CFL: dx_min as the element half-width instead of the smallest LGL node gap (R4)
     "cfl_dxmin": ("double h = 0.5 * m->dx[a] * (m->x[1] - m->x[0]);", "double h = 0.5 * m->dx[a];",
                   ["tests/test_oracle_scheme.py::test_cfl_dt_closed_form",
