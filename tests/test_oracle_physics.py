@@ -38,6 +38,21 @@ def test_c2p_round_trip_conditioned():
     assert np.all(np.abs(out[4] - prim[4])[well] / prim[4][well] <= 1e-12)
 
 
+def test_c2p_newton_converges_quadratically():
+    """Reading R7: Newton on f(p) with the exact f'(p).  From a guess 0.1 % off the
+    root, well-conditioned states (tau/(rho eps) < 10) stop within five
+    iterations (the error squares each step; the stopping rule adds one step);
+    a wrong derivative would converge only linearly."""
+    g = 4.0 / 3.0
+    prim = di.c2p_samples(12, 20000, gamma=g)
+    cons = oracle.prim2con(1, g, prim)
+    kappa = cons[4] / (prim[4] / (g - 1.0))
+    _, it, st = oracle.con2prim(g, cons, guess=prim[4] * (1.0 + 1e-3))
+    well = kappa < 10
+    assert np.all(st == 0) and well.sum() > 1000
+    assert it[well].max() <= 5 and np.median(it[well]) <= 4, np.bincount(it[well])
+
+
 def _c2p_zroot(g, D, S, tau):
     """Independent reference: 1D root in z = W v (Galeazzi-type formulation),
     with q = tau/D, r = |S|/D, eps(z) = W q - z r + z^2/(1+W), h = 1 + g eps."""

@@ -67,6 +67,18 @@ PLANTED = {
     # eq:Roe: the u - c wave weighted by |u + c|
     "roe_wave_speed": ("const double w1 = fabs(un - c) * al1,", "const double w1 = fabs(un + c) * al1,",
                        ["tests/test_oracle_physics.py::test_roe_flux_matches_eigendecomposition"]),
+    # the energy flux (tau + p) v_a without its pressure work
+    "energy_flux_work": ("F[4] = (u[4] + p) * va;", "F[4] = u[4] * va;",
+                         ["tests/test_oracle_physics.py::test_flux_consistency",
+                          "tests/test_oracle_sr_riemann.py::test_re_sod_st1_table_loose"]),
+    # the momentum flux's pressure on the wrong diagonal entry
+    "momentum_flux_pressure": ("F[1 + a] = F[1 + a] + p;", "F[1 + (a + 1) % 3] = F[1 + (a + 1) % 3] + p;",
+                               ["tests/test_oracle_physics.py::test_flux_consistency"]),
+    # con2prim's Newton derivative f'(p) = 1 - (g-1) v^2 (1 - D W / (E + p)) with the wrong sign
+    # inside: the bracket keeps the root, the iteration count gives it away
+    "c2p_derivative": ("r.df = 1.0 - (g - 1.0) * v2 * (1.0 - D * W / Ep);",
+                       "r.df = 1.0 - (g - 1.0) * v2 * (1.0 + D * W / Ep);",
+                       ["tests/test_oracle_physics.py::test_c2p_newton_converges_quadratically"]),
     # CFL: dx_min as the element half-width instead of the smallest LGL node gap (R4)
     "cfl_dxmin": ("double h = 0.5 * m->dx[a] * (m->x[1] - m->x[0]);", "double h = 0.5 * m->dx[a];",
                   ["tests/test_oracle_scheme.py::test_cfl_dt_closed_form",
