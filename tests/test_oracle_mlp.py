@@ -2,6 +2,7 @@
 against central finite differences, the Adam update against its definition on
 a quadratic, and the feature map against its defining formulas."""
 import numpy as np
+import pytest
 
 import dg_inputs as di
 import oracle
@@ -62,3 +63,33 @@ def test_features_and_guess_bracket():
     params = mlp.init_params(np.random.default_rng(1).random(mlp.N_PARAMS))
     pg = mlp.guess(params, cons, 4.0 / 3.0)
     assert np.all(pg >= np.maximum(0, s - tau - D)) and np.all(pg <= (4 / 3 - 1) * tau)
+
+
+def test_silu_identities():
+    """SiLU z sigma(z): silu(0) = 0, silu(z) - silu(-z) = z, silu(z) -> z for large
+    z, and its derivative matches central differences."""
+    z = np.linspace(-8.0, 8.0, 161)
+    assert mlp.silu(np.array([0.0]))[0] == 0.0
+    assert np.allclose(mlp.silu(z) - mlp.silu(-z), z, rtol=0, atol=1e-14)
+    assert abs(mlp.silu(np.array([40.0]))[0] - 40.0) < 1e-14
+    h = 1e-6
+    fd = (mlp.silu(z + h) - mlp.silu(z - h)) / (2 * h)
+    assert np.allclose(mlp.dsilu(z), fd, rtol=0, atol=1e-8)
+
+
+def test_planted_errors_in_the_mlp_are_caught(monkeypatch):
+    """A wrong SiLU derivative in backward, and a SiLU with the wrong sign in its
+    exponent, are rejected by the pins above: planted in the oracle on the CPU."""
+    good = mlp.dsilu
+
+    def bad_dsilu(z):
+        s = 1.0 / (1.0 + np.exp(-z))
+        return s * (1.0 + z * s)
+
+    monkeypatch.setattr(mlp, "dsilu", bad_dsilu)
+    with pytest.raises(AssertionError):
+        test_gradient_matches_central_differences()
+    monkeypatch.setattr(mlp, "dsilu", good)
+    monkeypatch.setattr(mlp, "silu", lambda z: z / (1.0 + np.exp(z)))
+    with pytest.raises(AssertionError):
+        test_silu_identities()
