@@ -306,9 +306,15 @@ dg_status dg_sync_status(dg_mesh *mesh, void *stream);
  * call's stream around every kernel it launches for `mesh` and accumulates the
  * elapsed time per kernel class:
  *   0 primitive recovery (incl. SR con2prim and the fused fix), 1 fused RHS +
- *   RK stage, 2 limiter, 3 SR fix pass, 4 CFL step, 5 other.
- * dg_profile_read synchronises the events, writes ms[c] (total milliseconds) and
- * launches[c] for c < min(nclass, 6) (host arrays) and resets the counters. */
+ *   RK stage, 2 limiter (decision passes of the Newtonian mixed step), 3 SR fix
+ *   pass, 4 CFL step, 5 other, 6 the last pass of the Newtonian mixed step
+ *   (limiter decisions and the write of U^{n+1}).
+ * Calls made while `stream` is being captured into a CUDA graph record their
+ * events as external event nodes of that graph; each replay records them again,
+ * and each dg_profile_read reports the replay before it (those events stay
+ * allocated until dg_mesh_destroy).  dg_profile_read synchronises the events,
+ * writes ms[c] (total milliseconds) and launches[c] for c < min(nclass, 7) (host
+ * arrays) and resets the counters of the eager launches. */
 dg_status dg_profile_enable(dg_mesh *mesh, int on);
 dg_status dg_profile_read(dg_mesh *mesh, double *ms, long long *launches, int nclass);
 

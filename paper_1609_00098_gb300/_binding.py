@@ -414,7 +414,7 @@ def dg_c2p_net_train(net, count, cons, p, epochs, batch, lr, loss_per_epoch=None
                                    _ptr(loss_per_epoch, epochs, torch.float32, "loss_per_epoch"), _stream(stream)))
 
 
-PROFILE_CLASSES = ("primitives", "stage", "limit", "fix", "dt", "other")
+PROFILE_CLASSES = ("primitives", "stage", "limit", "fix", "dt", "other", "final")
 
 
 def dg_profile_enable(mesh, on: bool = True):

@@ -29,15 +29,31 @@ dg_status fail(dg_status st, const char *fmt, ...)
         if (e_ != cudaSuccess) return fail(DG_ERR_CUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
     } while (0)
 
-// Per-kernel event log of dg_profile_enable.
+// Per-kernel event log of dg_profile_enable.  Launches recorded while the stream
+// is being captured into a CUDA graph get their events as external event nodes of
+// the graph: every replay records them again, and each dg_profile_read reports the
+// replay before it.  Those events live until the mesh is destroyed.
 struct ProfRec {
     int cls;
     cudaEvent_t a, b;
+    bool graph;
 };
 struct ProfLog {
     std::vector<cudaEvent_t> pool;
     std::vector<ProfRec> recs;
 };
+
+bool stream_capturing(cudaStream_t s)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    return cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive;
+}
+
+void prof_record(cudaEvent_t e, cudaStream_t s, bool graph)
+{
+    if (graph) cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+    else cudaEventRecord(e, s);
+}
 
 cudaEvent_t prof_event(ProfLog *L)
 {
@@ -56,19 +72,22 @@ cudaEvent_t prof_event(ProfLog *L)
     do {                                                                       \
         ProfLog *L_ = (m)->prof_on ? (ProfLog *)(m)->prof : nullptr;           \
         cudaEvent_t a_ = nullptr;                                              \
+        const bool g_ = L_ && stream_capturing(s);                             \
         if (L_) {                                                              \
             a_ = prof_event(L_);                                               \
-            cudaEventRecord(a_, (s));                                          \
+            prof_record(a_, (s), g_);                                          \
         }                                                                      \
         DG_CUDA(expr);                                                         \
         if (L_) {                                                              \
             cudaEvent_t b_ = prof_event(L_);                                   \
-            cudaEventRecord(b_, (s));                                          \
-            L_->recs.push_back(ProfRec{(cls), a_, b_});                        \
+            prof_record(b_, (s), g_);                                          \
+            L_->recs.push_back(ProfRec{(cls), a_, b_, g_});                    \
         }                                                                      \
     } while (0)
 
-enum { PROF_PRIM = 0, PROF_STAGE = 1, PROF_LIMIT = 2, PROF_FIX = 3, PROF_DT = 4, PROF_OTHER = 5 };
+// Timing classes of dg_profile_read (PROFILE_CLASSES in the binding); FINAL is the
+// last pass of the Newtonian delta-form step, which writes U^{n+1}.
+enum { PROF_PRIM = 0, PROF_STAGE = 1, PROF_LIMIT = 2, PROF_FIX = 3, PROF_DT = 4, PROF_OTHER = 5, PROF_FINAL = 6 };
 
 }  // namespace
 
@@ -251,7 +270,9 @@ cudaError_t launch_set(double *p, double v, cudaStream_t s);
 
 #define DG_DECL_MIXED(NP)                                                                               \
     cudaError_t launch_stage_mixed_n##NP(int, int, const MixedArgs &, cudaStream_t);                    \
-    cudaError_t launch_limit_mixed_n##NP(int, const LimitMixedArgs &, cudaStream_t);
+    cudaError_t launch_limit_mixed_n##NP(int, const LimitMixedArgs &, cudaStream_t);                    \
+    cudaError_t launch_ne_stage_n##NP(int, int, const NeArgs &, cudaStream_t);                          \
+    cudaError_t launch_ne_decide_n##NP(int, const NeDecideArgs &, cudaStream_t);
 DG_DECL_MIXED(2)
 DG_DECL_MIXED(3)
 DG_DECL_MIXED(4)
@@ -286,6 +307,136 @@ cudaError_t launch_limit_mixed(int n, int system, const LimitMixedArgs &a, cudaS
     case 8: return launch_limit_mixed_n8(system, a, s);
     }
     return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_ne_stage(int n, int flux, int stage, const NeArgs &a, cudaStream_t s)
+{
+    switch (n) {
+    case 2: return launch_ne_stage_n2(flux, stage, a, s);
+    case 3: return launch_ne_stage_n3(flux, stage, a, s);
+    case 4: return launch_ne_stage_n4(flux, stage, a, s);
+    case 5: return launch_ne_stage_n5(flux, stage, a, s);
+    case 6: return launch_ne_stage_n6(flux, stage, a, s);
+    case 7: return launch_ne_stage_n7(flux, stage, a, s);
+    case 8: return launch_ne_stage_n8(flux, stage, a, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_ne_decide(int n, int final_pass, const NeDecideArgs &a, cudaStream_t s)
+{
+    switch (n) {
+    case 2: return launch_ne_decide_n2(final_pass, a, s);
+    case 3: return launch_ne_decide_n3(final_pass, a, s);
+    case 4: return launch_ne_decide_n4(final_pass, a, s);
+    case 5: return launch_ne_decide_n5(final_pass, a, s);
+    case 6: return launch_ne_decide_n6(final_pass, a, s);
+    case 7: return launch_ne_decide_n7(final_pass, a, s);
+    case 8: return launch_ne_decide_n8(final_pass, a, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// Per-mesh slot of the Newtonian delta-form stage kernel (pointers filled in by
+// the caller) and the group-level arguments for meshes like m.
+NeSlot ne_slot(const dg_mesh *m)
+{
+    NeSlot sl;
+    std::memset(&sl, 0, sizeof(sl));
+    sl.gh = m->gh;
+    const int n = m->d.n;
+    for (int ax = 0; ax < 3; ++ax) {
+        sl.K[ax] = m->d.K[ax];
+        const double g = 2.0 / m->dx[ax];
+        sl.g[ax] = (float)g;
+        sl.lift0[ax] = (float)(g / m->T.w[0]);
+        sl.liftN[ax] = (float)(g / m->T.w[n - 1]);
+    }
+    return sl;
+}
+
+NeArgs ne_args(const dg_mesh *m)
+{
+    NeArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.one = ne_slot(m);
+    a.nslots = 1;
+    a.nelem = m->E;
+    a.gamma = (float)m->d.gamma;
+    for (int i = 0; i < MAXN * MAXN; ++i) a.D[i] = (float)m->T.D[i];
+    for (int i = 0; i < MAXN; ++i) {
+        a.x[i] = (float)m->T.x[i];
+        a.w[i] = (float)m->T.w[i];
+        a.row1[i] = (float)m->T.row1[i];
+        a.wh[i] = a.w[i];
+        a.wl[i] = (float)(m->T.w[i] - (double)a.wh[i]);
+    }
+    return a;
+}
+
+// Stage st (0, 1, 2) of the delta-form step on mesh m with state U: the FP32
+// stage differences live in W1 (D1, then D3) and W2 (D2); S holds S(U^n).
+NeArgs ne_stage_args(const dg_mesh *m, double *U, int st, bool lim, bool cflmode)
+{
+    float *D1 = reinterpret_cast<float *>(m->W1), *D2 = reinterpret_cast<float *>(m->W2);
+    static const float cb[3] = {1.0f, 0.25f, (float)(2.0 / 3.0)};
+    NeArgs a = ne_args(m);
+    a.one.Un = U;
+    a.one.dt_ptr = cflmode ? m->dt : nullptr;
+    a.one.Din = st == 1 ? D1 : st == 2 ? D2 : nullptr;
+    a.one.Dout = st == 1 ? D2 : D1;
+    a.cb = cb[st];
+    a.one.mask = (lim && st > 0) ? m->ne_mask : nullptr;
+    a.one.SH = m->ne_SH;
+    a.one.M0 = m->ne_M0;
+    a.one.SN = (lim && st == 0) ? m->S : nullptr;
+    a.one.SD = lim ? m->ne_SD : nullptr;
+    a.one.lam = (cflmode && st == 0) ? m->lam : nullptr;
+    return a;
+}
+
+NeDecideSlot ne_decide_slot(const dg_mesh *m)
+{
+    NeDecideSlot sl;
+    std::memset(&sl, 0, sizeof(sl));
+    sl.SN = m->S;
+    sl.SD = m->ne_SD;
+    sl.mask = m->ne_mask;
+    sl.M0 = m->ne_M0;
+    sl.SH = m->ne_SH;
+    for (int ax = 0; ax < 3; ++ax) {
+        sl.K[ax] = m->d.K[ax];
+        sl.tvb[ax] = m->d.tvb_M * m->dx[ax] * m->dx[ax];
+        sl.inv_dx[ax] = 1.0 / m->dx[ax];
+        sl.beta_dx[ax] = m->d.beta / m->dx[ax];
+        sl.hdx[ax] = 0.5 * m->dx[ax];
+    }
+    return sl;
+}
+
+// Decision pass after stage st (0, 1: limiter only; 2: also writes U^{n+1}).
+NeDecideSlot ne_decide_stage_slot(const dg_mesh *m, double *U, int st, bool cflmode, unsigned char *troubled)
+{
+    NeDecideSlot sl = ne_decide_slot(m);
+    sl.dt_ptr = cflmode ? m->dt : nullptr;
+    if (st == 2) {
+        sl.U = U;
+        sl.D3 = reinterpret_cast<const float *>(m->W1);
+        sl.troubled = troubled;
+    }
+    return sl;
+}
+
+NeDecideArgs ne_decide_args(const dg_mesh *m)
+{
+    NeDecideArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.one = ne_decide_slot(m);
+    a.nslots = 1;
+    a.nelem = m->E;
+    a.limiter = m->d.limiter;
+    for (int i = 0; i < MAXN; ++i) a.x[i] = (float)m->T.x[i];
+    return a;
 }
 
 // Per-mesh slot of a mixed stage launch (pointers filled in by the caller).
@@ -432,6 +583,10 @@ void free_scratch(dg_mesh *m)
     }
     cudaFree(m->W1);
     cudaFree(m->W2);
+    cudaFree(m->ne_SD);
+    cudaFree(m->ne_M0);
+    cudaFree(m->ne_SH);
+    cudaFree(m->ne_mask);
     cudaFree(m->pbuf[0]);
     cudaFree(m->pbuf[1]);
     cudaFree(m->pfull);
@@ -505,6 +660,12 @@ dg_status dg_mesh_create(const dg_mesh_desc *d, dg_mesh **out)
     cudaError_t st = cudaSuccess;
     st = st ? st : cudaMalloc(&m->W1, state);
     st = st ? st : cudaMalloc(&m->W2, state);
+    if (mixed && d->system == 0) {
+        st = st ? st : cudaMalloc(&m->ne_SD, sizeof(float) * (size_t)E * 50);
+        st = st ? st : cudaMalloc(&m->ne_M0, sizeof(double) * (size_t)E * 5);
+        st = st ? st : cudaMalloc(&m->ne_SH, sizeof(float4) * (size_t)E * 5);
+        st = st ? st : cudaMalloc(&m->ne_mask, (size_t)E);
+    }
     if (mixed && d->system == 1) {
         st = st ? st : cudaMalloc(&m->pbuf[0], sizeof(float) * (size_t)E * m->nn);
         st = st ? st : cudaMalloc(&m->pbuf[1], sizeof(float) * (size_t)E * m->nn);
@@ -605,6 +766,13 @@ dg_status dg_rhs(dg_mesh *m, const double *U, double *dUdt, void *stream)
     if (!U || !dUdt || U == dUdt) return fail(DG_ERR_ARG, "U and dUdt must be distinct, non-NULL");
     cudaStream_t s = (cudaStream_t)stream;
     if (m->gh.mask) DG_LAUNCH(m, s, PROF_OTHER, launch_exterior(m, 0.0, nullptr, 0.0, s));
+    if (m->d.precision == DG_PRECISION_MIXED && m->d.system == 0) {
+        NeArgs a = ne_args(m);
+        a.one.Un = U;
+        a.one.rhs = dUdt;
+        DG_LAUNCH(m, s, PROF_STAGE, launch_ne_stage(m->d.n, m->d.flux, 0, a, s));
+        return DG_OK;
+    }
     if (m->d.precision == DG_PRECISION_MIXED) {
         MixedArgs a = mixed_args(m);
         a.one.Us = U;
@@ -635,6 +803,43 @@ dg_status dg_compute_dt(dg_mesh *m, const double *U, double cfl, double *dt, voi
     DG_CUDA(cudaMemsetAsync(m->lam, 0, sizeof(unsigned long long), s));
     DG_CUDA(launch_primitives(m, U, m->P, 0, nullptr, m->lam, s));
     DG_CUDA(launch_dt(m, cfl, dt, s));
+    return DG_OK;
+}
+
+// Newtonian mixed-precision step in delta form (dg_ne_mixed.cuh): three stage
+// kernels on FP32 stage differences D1 (in W1), D2 (in W2), D3 (in W1), the
+// limiter's decision pass after stages 1 and 2, and a last pass that writes
+// U^{n+1} = U^n + D3 in place (replaced where the stage-3 limiter acts).  Stage 1
+// also takes the CFL maximum of U^n and S(U^n).
+static dg_status rk3_step_ne(dg_mesh *m, double *U, double dt, double cfl, double *dt_used, unsigned char *troubled,
+                             cudaStream_t s)
+{
+    const bool lim = m->d.limiter != 0;
+    const bool cflmode = cfl > 0.0;
+    const double *dtp = cflmode ? m->dt : nullptr;
+    if (cflmode) DG_CUDA(cudaMemsetAsync(m->lam, 0, sizeof(unsigned long long), s));
+    const double ct[3] = {0.0, 1.0, 0.5};  // stage times t + ct dt (analytic boundaries)
+    for (int st = 0; st < 3; ++st) {
+        if (m->gh.mask) DG_LAUNCH(m, s, PROF_OTHER, launch_exterior(m, ct[st], dtp, dt, s));
+        NeArgs a = ne_stage_args(m, U, st, lim, cflmode);
+        a.one.dt = dt;
+        DG_LAUNCH(m, s, PROF_STAGE, launch_ne_stage(m->d.n, m->d.flux, st + 1, a, s));
+        if (st == 0 && cflmode) DG_LAUNCH(m, s, PROF_DT, launch_dt(m, cfl, m->dt, s));
+        NeDecideArgs d = ne_decide_args(m);
+        d.one = ne_decide_stage_slot(m, U, st, cflmode, st == 2 ? troubled : nullptr);
+        d.one.dt = dt;
+        d.scale_dt = st == 0;
+        if (st < 2) {
+            if (lim) DG_LAUNCH(m, s, PROF_LIMIT, launch_ne_decide(m->d.n, 0, d, s));
+        } else {
+            DG_LAUNCH(m, s, PROF_FINAL, launch_ne_decide(m->d.n, 1, d, s));
+        }
+    }
+    if (m->gh.mask) DG_LAUNCH(m, s, PROF_OTHER, launch_time_add(m->t, dtp, dt, s));
+    if (dt_used) {
+        if (cflmode) DG_CUDA(cudaMemcpyAsync(dt_used, m->dt, sizeof(double), cudaMemcpyDeviceToDevice, s));
+        else DG_CUDA(launch_set(dt_used, dt, s));
+    }
     return DG_OK;
 }
 
@@ -721,6 +926,8 @@ dg_status dg_rk3_step(dg_mesh *m, double *U, double dt, double cfl, double *dt_u
     const bool cflmode = cfl > 0.0;
     if (!cflmode && !(dt > 0.0)) return fail(DG_ERR_ARG, "need dt > 0 or cfl > 0");
     cudaStream_t s = (cudaStream_t)stream;
+    if (m->d.precision == DG_PRECISION_MIXED && m->d.system == 0 && m->d.limiter != DG_LIMITER_MRS)
+        return rk3_step_ne(m, U, dt, cfl, dt_used, troubled, s);
     if (m->d.precision == DG_PRECISION_MIXED) return rk3_step_mixed(m, U, dt, cfl, dt_used, troubled, s);
     const bool sr = m->d.system == 1;
     const bool lim = m->d.limiter != 0;
@@ -927,7 +1134,16 @@ dg_status dg_sync_status(dg_mesh *m, void *stream)
 dg_status dg_profile_enable(dg_mesh *m, int on)
 {
     if (dg_status s = check_mesh(m)) return s;
-    if (!m->prof) m->prof = new ProfLog;
+    if (!m->prof) {
+        ProfLog *L = new ProfLog;
+        // events made up front: none is created while a stream is being captured
+        for (int i = 0; i < 256; ++i) {
+            cudaEvent_t e = nullptr;
+            if (cudaEventCreate(&e) != cudaSuccess) break;
+            L->pool.push_back(e);
+        }
+        m->prof = L;
+    }
     m->prof_on = on ? 1 : 0;
     return DG_OK;
 }
@@ -942,6 +1158,7 @@ dg_status dg_profile_read(dg_mesh *m, double *ms, long long *launches, int nclas
     }
     if (!m->prof) return DG_OK;
     ProfLog *L = (ProfLog *)m->prof;
+    std::vector<ProfRec> keep;
     for (auto &r : L->recs) {
         DG_CUDA(cudaEventSynchronize(r.b));
         float t = 0.0f;
@@ -950,10 +1167,14 @@ dg_status dg_profile_read(dg_mesh *m, double *ms, long long *launches, int nclas
             ms[r.cls] += t;
             launches[r.cls] += 1;
         }
-        L->pool.push_back(r.a);
-        L->pool.push_back(r.b);
+        if (r.graph) {
+            keep.push_back(r);
+        } else {
+            L->pool.push_back(r.a);
+            L->pool.push_back(r.b);
+        }
     }
-    L->recs.clear();
+    L->recs.swap(keep);
     return DG_OK;
 }
 

@@ -3,9 +3,11 @@
 //
 // Meshes that can share kernels (same n, system, flux, limiter, gamma, fix
 // bounds, options and learned-guess network) form a group.  A step launches,
-// per group, one CFL kernel, and per stage one stage kernel and (limiter on) one
-// limiter kernel over the concatenated element list of all its meshes; each CTA
-// finds its mesh by binary search over the group's element offsets.  With a few
+// per SR group, one CFL kernel, and per stage one stage kernel and (limiter on)
+// one limiter kernel over the concatenated element list of all its meshes; per
+// Newtonian group, the delta-form step's three stage kernels and decision passes
+// (dg_ne_mixed.cuh) over the same concatenation.  Each CTA finds its mesh by
+// binary search over the group's element offsets.  With a few
 // groups in place of hundreds of meshes, a step is a few dozen launches; they are
 // captured once into a CUDA graph and replayed.  dg_ensemble_tune picks, per
 // group, the elements per CTA and the volume contraction (tensor cores or FP32
@@ -71,6 +73,11 @@ struct EnsGroup {
     LimitSlot *d_limit[3] = {nullptr, nullptr, nullptr};
     CflSlot *d_cfl = nullptr, *d_cfl_first = nullptr;
     long long *d_elem0 = nullptr, *d_chunk0 = nullptr;
+    // Newtonian groups: the delta-form step's stage and decision slots per stage
+    NeArgs ne_proto[3];
+    NeDecideArgs ne_dproto[3];
+    NeSlot *d_ne[3] = {nullptr, nullptr, nullptr};
+    NeDecideSlot *d_ned[3] = {nullptr, nullptr, nullptr};
 };
 
 }  // namespace dg
@@ -118,6 +125,57 @@ void free_group(EnsGroup &g)
     cudaFree(g.d_cfl_first);
     cudaFree(g.d_elem0);
     cudaFree(g.d_chunk0);
+    for (int s = 0; s < 3; ++s) {
+        cudaFree(g.d_ne[s]);
+        cudaFree(g.d_ned[s]);
+    }
+}
+
+// Slot tables of a Newtonian group: the delta-form step of dg_rk3_step on each
+// member, its stage kernels and decision passes batched over the members.
+cudaError_t build_ne_group(dg_ensemble *en, EnsGroup &g)
+{
+    const dg_mesh *m0 = en->meshes[g.members[0]];
+    const bool lim = m0->d.limiter != 0;
+    std::vector<NeSlot> st[3];
+    std::vector<NeDecideSlot> de[3];
+    std::vector<long long> elem0;
+    long long e0 = 0;
+    for (int idx : g.members) {
+        dg_mesh *m = en->meshes[idx];
+        double *U = en->U[idx];
+        for (int s = 0; s < 3; ++s) {
+            st[s].push_back(ne_stage_args(m, U, s, lim, true).one);
+            de[s].push_back(ne_decide_stage_slot(m, U, s, true, nullptr));
+        }
+        elem0.push_back(e0);
+        e0 += m->E;
+    }
+    g.nelem = e0;
+    g.epb = ne_epb(g.n);
+    g.tc = 0;
+    cudaError_t e = upload(&g.d_elem0, elem0);
+    for (int s = 0; s < 3 && e == cudaSuccess; ++s) {
+        e = upload(&g.d_ne[s], st[s]);
+        if (e == cudaSuccess) e = upload(&g.d_ned[s], de[s]);
+    }
+    if (e != cudaSuccess) return e;
+    for (int s = 0; s < 3; ++s) {
+        NeArgs a = ne_stage_args(m0, en->U[g.members[0]], s, lim, true);
+        a.slots = g.d_ne[s];
+        a.elem0 = g.d_elem0;
+        a.nslots = (int)g.members.size();
+        a.nelem = g.nelem;
+        g.ne_proto[s] = a;
+        NeDecideArgs d = ne_decide_args(m0);
+        d.slots = g.d_ned[s];
+        d.elem0 = g.d_elem0;
+        d.nslots = (int)g.members.size();
+        d.nelem = g.nelem;
+        d.scale_dt = s == 0;
+        g.ne_dproto[s] = d;
+    }
+    return cudaSuccess;
 }
 
 // Slot tables of a group: the pointers of every member for each pass of a step.
@@ -225,6 +283,10 @@ MixedArgs stage_args_for(const EnsGroup &g, const MeshSlot *slots, int stage)
     return a;
 }
 
+// One step of the ensemble.  SR groups: CFL pass, then per stage the stage kernel
+// and the limiter.  Newtonian groups: the delta-form step, whose stage 1 takes the
+// CFL maximum itself, so their stage 1 runs before the batched dt; then per stage
+// the decision pass (the last one writes U^{n+1}).
 cudaError_t launch_step(dg_ensemble *en, double cfl, bool first, cudaStream_t s)
 {
     const int count = (int)en->meshes.size();
@@ -233,6 +295,10 @@ cudaError_t launch_step(dg_ensemble *en, double cfl, bool first, cudaStream_t s)
     cudaError_t e = cudaGetLastError();
     for (EnsGroup &g : en->groups) {
         if (e != cudaSuccess) return e;
+        if (g.system == 0) {
+            e = launch_ne_stage(g.n, g.flux, 1, g.ne_proto[0], s);
+            continue;
+        }
         CflArgs c = g.cproto;
         c.slots = first ? g.d_cfl_first : g.d_cfl;
         e = launch_cfl_batch(g.system, c, g.nchunks, s);
@@ -242,6 +308,13 @@ cudaError_t launch_step(dg_ensemble *en, double cfl, bool first, cudaStream_t s)
     e = cudaGetLastError();
     for (int st = 0; st < 3 && e == cudaSuccess; ++st) {
         for (EnsGroup &g : en->groups) {
+            if (g.system != 0) continue;
+            if (st > 0) e = launch_ne_stage(g.n, g.flux, st + 1, g.ne_proto[st], s);
+            if (e == cudaSuccess && (st == 2 || g.limiter)) e = launch_ne_decide(g.n, st == 2, g.ne_dproto[st], s);
+            if (e != cudaSuccess) return e;
+        }
+        for (EnsGroup &g : en->groups) {
+            if (g.system == 0) continue;
             MixedArgs a = stage_args_for(g, (first && st == 0) ? g.d_stage_first : g.d_stage[st], st);
             if (g.pgiven && st == 0) {  // stage 1 takes the CFL pass's primitives
                 a.netImg = nullptr;
@@ -250,7 +323,7 @@ cudaError_t launch_step(dg_ensemble *en, double cfl, bool first, cudaStream_t s)
             if (e != cudaSuccess) return e;
         }
         for (EnsGroup &g : en->groups) {
-            if (!g.limiter) continue;
+            if (!g.limiter || g.system == 0) continue;
             LimitMixedArgs l = g.lproto;
             l.slots = g.d_limit[st];
             e = launch_limit_mixed(g.n, g.system, l, s);
@@ -307,7 +380,7 @@ dg_status dg_ensemble_create(dg_mesh *const *meshes, double *const *U, int count
     }
     cudaError_t e = cudaSuccess;
     for (EnsGroup &g : en->groups)
-        if (e == cudaSuccess) e = build_group(en, g);
+        if (e == cudaSuccess) e = g.system == 0 ? build_ne_group(en, g) : build_group(en, g);
     std::vector<DtSlot> dts;
     for (dg_mesh *m : en->meshes) dts.push_back(DtSlot{m->lam, m->dt, m->dxmin});
     if (e == cudaSuccess) e = upload(&en->d_dt, dts);
@@ -337,6 +410,7 @@ dg_status dg_ensemble_tune(dg_ensemble *en, void *stream)
         return set_error(DG_ERR_CUDA, "event creation failed");
     dg_status st = DG_OK;
     for (EnsGroup &g : en->groups) {
+        if (g.system == 0) continue;  // the Newtonian step has no launch-shape options
         float best = 1e30f;
         int best_epb = g.epb, best_tc = g.tc;
         for (int tc = 1; tc >= 0; --tc)

@@ -128,6 +128,13 @@ struct dg_mesh {
     const dg_c2p_net *net;   // attached learned-guess network (mixed SR path), or nullptr
     int tc_contract;         // mixed volume contraction on the tensor cores (split-BF16x3)
     int epb;                 // mixed stage kernel: elements per CTA
+    // Newtonian mixed step in delta form (W1, W2 hold its FP32 stage differences;
+    // S holds S(U^n)): FP32 summaries of the differences, the limiter's per-element
+    // masks and replacement parameters
+    float *ne_SD;            // [e][5][10]
+    double *ne_M0;           // [e][5]
+    float4 *ne_SH;           // [e][5]
+    unsigned char *ne_mask;  // [e]
     // Adams-Bashforth state (dg_ab3_step): the last three right-hand sides (ring),
     // the steps taken since the last reset, and the fixed dt
     double *abL[3];
@@ -167,6 +174,22 @@ cudaError_t launch_con2prim(long long count, double gamma, const double *cons, d
 
 struct MixedArgs;
 struct LimitMixedArgs;
+struct NeArgs;
+struct NeDecideArgs;
+struct NeSlot;
+struct NeDecideSlot;
+// Newtonian mixed step in delta form: stage kernel (stage 0 = right-hand side
+// only) and the limiter's decision pass (final_pass: also writes U^{n+1}).
+cudaError_t launch_ne_stage(int n, int flux, int stage, const NeArgs &a, cudaStream_t s);
+cudaError_t launch_ne_decide(int n, int final_pass, const NeDecideArgs &a, cudaStream_t s);
+NeSlot ne_slot(const dg_mesh *m);
+NeArgs ne_args(const dg_mesh *m);
+// Stage st (0, 1, 2) of the delta-form step on mesh m with state U, and the
+// decision pass after it (st = 2: the last pass, which writes U^{n+1}).
+NeArgs ne_stage_args(const dg_mesh *m, double *U, int st, bool lim, bool cflmode);
+NeDecideSlot ne_decide_slot(const dg_mesh *m);
+NeDecideSlot ne_decide_stage_slot(const dg_mesh *m, double *U, int st, bool cflmode, unsigned char *troubled);
+NeDecideArgs ne_decide_args(const dg_mesh *m);
 cudaError_t launch_stage_mixed(int n, int system, int flux, const MixedArgs &a, cudaStream_t s);
 cudaError_t launch_limit_mixed(int n, int system, const LimitMixedArgs &a, cudaStream_t s);
 cudaError_t launch_cfl_mixed(const dg_mesh *m, const double *Un, const float *pin, float *pout, float *Pout,

@@ -991,6 +991,8 @@ inline int stage_max_epb(int n)
 
 // the limiter of the mixed path
 #include "dg_limit_mixed.cuh"
+// the Newtonian delta-form step
+#include "dg_ne_mixed.cuh"
 
 #define DG_INSTANTIATE_MIXED(NP)                                                                       \
     namespace dg {                                                                                     \
@@ -1001,5 +1003,13 @@ inline int stage_max_epb(int n)
     cudaError_t launch_limit_mixed_n##NP(int system, const LimitMixedArgs &a, cudaStream_t s)           \
     {                                                                                                  \
         return launch_limit_mixed_np<NP>(system, a, s);                                                \
+    }                                                                                                  \
+    cudaError_t launch_ne_stage_n##NP(int flux, int stage, const NeArgs &a, cudaStream_t s)             \
+    {                                                                                                  \
+        return launch_ne_stage_np<NP>(flux, stage, a, s);                                              \
+    }                                                                                                  \
+    cudaError_t launch_ne_decide_n##NP(int final_pass, const NeDecideArgs &a, cudaStream_t s)           \
+    {                                                                                                  \
+        return launch_ne_decide_np<NP>(final_pass, a, s);                                              \
     }                                                                                                  \
     }
