@@ -1,23 +1,26 @@
 #!/usr/bin/env python
-"""DG-RK3 throughput (dof-updates/s) of the nodal DG hot path on GB300: the
-mixed-precision path with the learned con2prim guess (headline `value`), the
-same path warm-started from the previous pass's pressures (`mixed_warm_start`),
-and the plain FP64 path (`plain_fp64`).  The guess network is trained first
-(untimed) on pairs the method generates.
+"""DG-RK3 throughput (dof-updates/s) of the nodal DG hot path on GB300.
 
-Workload: 3D special-relativistic blast on a periodic unit cube, 16^3 affine
-elements, 5 LGL nodes per axis (512,000 nodes x 5 conserved variables),
-gamma = 4/3, rho = 10, p = 13.33 for r < 0.3 else rho = 1, p = 1e-6, v = 0,
-1 % seeded density noise; HLL flux, MinModN limiter and SR fix after every
-stage, con2prim at every node, CFL 0.2 (dt computed on the device each step).
-A step is one full SSP-RK3 step (three RHS evaluations, limiter, fix).
+Headline workload: the 3D Newtonian Kelvin-Helmholtz shear layer, gamma = 5/3,
+periodic [-0.5, 0.5]^3, 64^3 affine elements, 6 LGL nodes per axis (56,623,104
+nodes x 5 conserved variables), rho = 2 and vx = +0.5 for |y| < 0.25, else rho = 1
+and vx = -0.5, p = 2.5, vy = 0.01 (2u - 1) seeded per node; HLL flux, MinModN
+limiter after every stage, CFL 0.2 (dt computed on the device every step).  A
+step is one full SSP-RK3 step (three right-hand sides, the limiter after each
+stage).  `value` is the mixed-precision path (FP32 arithmetic, FP64 state and RK
+accumulation); the Newtonian system has no con2prim, so the learned guess does
+not apply to it.  `plain_fp64` is the FP64 path on the same workload, and
+`mixed_accuracy` compares the two after ten steps at equal dt.
+
+Secondary objects: `sr_blast` (the relativistic blast, 16^3 x 5^3 nodes: mixed
+with the learned con2prim guess, mixed warm-started, FP64), `con2prim` (2^24
+standalone FP64 con2prim solves from the standard and the learned guess, the
+network trained on 2^22 generated pairs), `ensemble` (256 ragged meshes).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Prints one JSON line (rank 0).  N > 1 (launched by torch.distributed.run) runs
 N independent replicas, one per GPU; the path has no data exchange to shard.
-The state (20.5 MB) is smaller than L2, so a 256 MiB buffer is written between
-timed steps (outside the per-step event pairs).
 """
 from __future__ import annotations
 
@@ -35,17 +38,36 @@ sys.path.insert(0, ROOT)
 
 import dg_inputs  # noqa: E402  (seeded input generator, no method arithmetic)
 
-WORKLOAD = dict(system=1, K=(16, 16, 16), n=5, flux=1, limiter=1, gamma=4.0 / 3.0, cfl=0.2, seed=1)
+KH = dict(system=0, K=(64, 64, 64), n=6, flux=1, limiter=1, gamma=5.0 / 3.0, lo=(-0.5,) * 3, hi=(0.5,) * 3,
+          cfl=0.2, seed=1)
+BLAST = dict(system=1, K=(16, 16, 16), n=5, flux=1, limiter=1, gamma=4.0 / 3.0, lo=(0.0,) * 3, hi=(1.0,) * 3,
+             cfl=0.2, seed=1)
+KH_SAMPLE_K = (16, 16, 16)   # the CPU oracle's bounded sample of the KH workload
 METRIC = "DG-RK3 dof-updates/s on 1 GB300: plain FP64 vs mixed+learned at equal L2 error"
 UNIT = "dof-updates/s"
+# Compulsory HBM bytes per node of one stage launch as the survey's roofline model
+# counts them (FP64 stage states): stage 1 reads U^n and writes U^1 (80 B), stages 2
+# and 3 read U_s and U^n and write U_{s+1} (120 B each): 320 B per node-step.
+SURVEY_BYTES_PER_NODE_STAGE = (80.0 + 120.0 + 120.0) / 3.0
+
+
+def _nodes(w):
+    return int(np.prod(w["K"])) * w["n"] ** 3
+
+
+def _mesh_kw(w, **extra):
+    kw = {k: w[k] for k in ("system", "K", "n", "flux", "limiter", "gamma", "lo", "hi")}
+    kw.update(extra)
+    return kw
 
 
 def _config(extra=None):
-    w = WORKLOAD
-    cfg = {"workload": "SR blast, 16^3 elements, 5 LGL nodes/axis, HLL, MinModN, con2prim per node, CFL 0.2",
-           "system": "special-relativistic hydro", "elements": list(w["K"]), "lgl_nodes_per_axis": w["n"],
-           "nodes": int(np.prod(w["K"]) * w["n"] ** 3), "vars": 5, "flux": "HLL", "limiter": "MinModN",
-           "cfl": w["cfl"], "seed": w["seed"], "l2_between_steps": "flushed (256 MiB write)"}
+    w = KH
+    cfg = {"workload": "Newtonian Kelvin-Helmholtz shear layer, 64^3 elements, 6 LGL nodes/axis (56.6M nodes), "
+                       "gamma 5/3, HLL, MinModN, CFL 0.2",
+           "system": "Newtonian Euler", "elements": list(w["K"]), "lgl_nodes_per_axis": w["n"], "nodes": _nodes(w),
+           "vars": 5, "flux": "HLL", "limiter": "MinModN", "cfl": w["cfl"], "seed": w["seed"],
+           "l2_between_steps": "inputs larger than L2 (state 2.26 GB per copy; no flush)"}
     if extra:
         cfg.update(extra)
     return cfg
@@ -125,64 +147,144 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _init_state(pkg, mesh, torch):
-    import dg_inputs as di
+
+def _state(pkg, torch, w, mesh, seed=None):
+    """Initial conserved state on the device: the library's node coordinates, the
+    seeded primitive fields of dg_inputs, the library's prim -> cons."""
     xyz = mesh.coords().cpu().numpy()
-    prim = di.blast_sr(xyz, seed=WORKLOAD["seed"])
+    seed = w["seed"] if seed is None else seed
+    prim = dg_inputs.kh_ne(xyz, seed=seed) if w["system"] == 0 else dg_inputs.blast_sr(xyz, seed=seed)
+    del xyz
     return mesh.from_prim(torch.from_numpy(prim).cuda())
 
 
-# DRAM bytes per k_stage_mixed launch of the learned-guess steps on this workload
-# (mean over the three stages of a step: stage 1 runs the variant that takes the
-# CFL pass's primitives, stages 2-3 the in-kernel network), from the ncu launch
-# list summarised in profiles/launches_sr_blast_16x16x16_n5.md.  Reported only
-# while the kernel's sources and the step's dispatch still hash to the value they
-# had when it was taken.
-TRAFFIC_BYTES_PER_LAUNCH = 38690727.0
-TRAFFIC_SOURCES = ("paper_1609_00098_gb300/csrc/dg_mixed.cuh", "paper_1609_00098_gb300/csrc/dg_physics.cuh",
-                   "paper_1609_00098_gb300/csrc/dg_internal.h", "paper_1609_00098_gb300/csrc/dg_c2p_net.cuh",
-                   "paper_1609_00098_gb300/csrc/dg_api.cu")
-TRAFFIC_SOURCES_SHA256 = "b2f0d951b38752a732040ff7c665d4a125ae41b1c6a8c7c5cf13899394c49ee4"
-TRAFFIC_VARIANT = "learned"
+def _lgl_weights3(pkg, n):
+    _, w, _, _ = pkg.abi.dg_lgl_tables(n)
+    return np.einsum("k,j,i->kji", w, w, w).reshape(-1)
 
 
-def _traffic(variant):
-    import hashlib
-    h = hashlib.sha256()
-    for f in TRAFFIC_SOURCES:
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
-    ok = h.hexdigest() == TRAFFIC_SOURCES_SHA256 and variant == TRAFFIC_VARIANT
-    return TRAFFIC_BYTES_PER_LAUNCH if ok else None
+def _rel_l2(torch, w3, a, b):
+    """Per-variable relative L2 distance of a to b (LGL quadrature on the uniform
+    affine mesh, each norm floored at 1 % of the largest variable's norm)."""
+    wt = torch.from_numpy(w3).to(a.device)
+    d = torch.sqrt(((a - b) ** 2 * wt).sum(dim=(0, 2)))
+    r = torch.sqrt((b ** 2 * wt).sum(dim=(0, 2)))
+    return (d / torch.clamp(r, min=1e-2 * float(r.max()))).cpu().tolist()
 
 
-def _algorithmic(nodes, precision, learned=False):
-    """Compulsory HBM bytes of one fused stage launch, averaged over the 3 stages.
-    Both paths keep FP64 stage states: stage 1 reads U^n and writes U^1 (80 B/node);
-    stages 2, 3 read U_s and U^n and write U_{s+1} (120 B/node).  The warm-started
-    mixed SR path also reads the previous pass's FP32 pressure (4 B) and writes its
-    own (4 B).  Stage 1 of an SR CFL step reads the CFL pass's FP32 primitives of
-    U^n (20 B) instead of solving con2prim; with the learned guess computed in the
-    kernel, stages 2, 3 carry no pressure."""
-    if precision == 0:
-        return nodes * (80 + 120 + 120) / 3.0
-    if learned:
-        return nodes * (100 + 120 + 120) / 3.0
-    return nodes * (104 + 128 + 128) / 3.0
+def _timed_steps(pkg, torch, mesh, U, w, steps, dist, flush=None):
+    """Graph-replayed steps, each bracketed by CUDA events on the replay stream, with
+    the library's per-kernel events captured into the same graph (external event
+    nodes): kernel durations come from the very replays that are timed."""
+    pkg.abi.dg_profile_enable(mesh.h, True)
+    graph = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        mesh.rk3_step(U, cfl=w["cfl"])  # one more warm step on the capture stream
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    pkg.abi.dg_profile_read(mesh.h)  # drop the eager warm step's events
+    with torch.cuda.graph(graph):
+        mesh.rk3_step(U, cfl=w["cfl"])
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    s_ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    e_ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    prof = {}
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for k in range(steps):
+        if flush is not None:
+            flush.fill_(float(k))
+        s_ev[k].record(stream)
+        graph.replay()
+        e_ev[k].record(stream)
+        torch.cuda.synchronize()
+        for c, (ms, n) in pkg.abi.dg_profile_read(mesh.h).items():
+            acc = prof.setdefault(c, [0.0, 0])
+            acc[0] += ms
+            acc[1] += n
+    if dist:
+        dist.barrier()
+    step_ms = [s.elapsed_time(e) for s, e in zip(s_ev, e_ev)]
+    pkg.abi.dg_profile_enable(mesh.h, False)
+    del graph  # before the mesh that owns the graph's events goes
+    torch.cuda.synchronize()
+    return step_ms, prof
 
 
-def _train_guess_net(pkg, torch):
+def _kern(prof):
+    tot = max(1e-12, sum(v[0] for v in prof.values()))
+    return {c: {"ms_total": round(v[0], 4), "launches": int(v[1]), "share": round(v[0] / tot, 4)}
+            for c, v in prof.items() if v[1]}
+
+
+def _kh_accuracy(pkg, torch, U0, steps):
+    """Mixed vs FP64 after `steps` KH steps at equal dt (the FP64 path's CFL dt;
+    the FP64 path is bitwise equal to the FP64 oracle in the tests), with the
+    number of elements whose last-stage limiter flags differ."""
+    w = KH
+    f = pkg.Mesh(precision=0, **_mesh_kw(w))
+    m = pkg.Mesh(precision=1, **_mesh_kw(w))
+    Uf, Um = U0.clone(), U0.clone()
+    dtv = torch.zeros(1, dtype=torch.float64, device="cuda")
+    tf = torch.zeros(f.E, dtype=torch.uint8, device="cuda")
+    tm = torch.zeros(f.E, dtype=torch.uint8, device="cuda")
+    for _ in range(steps):
+        f.rk3_step(Uf, cfl=w["cfl"], dt_used=dtv, troubled=tf)
+        m.rk3_step(Um, dt=float(dtv.item()), troubled=tm)
+    torch.cuda.synchronize()
+    rel = _rel_l2(torch, _lgl_weights3(pkg, w["n"]), Um, Uf)
+    flips = int((tf != tm).sum().item())
+    out = {"steps": steps, "rel_l2_vs_fp64_per_var": rel, "max": max(rel), "bar": 1e-6,
+           "norm": "LGL-quadrature L2 per conserved variable, floored at 1 % of the largest",
+           "reference": "the FP64 GPU path at the same dt (bitwise equal to the FP64 oracle in the tests)",
+           "limiter_flag_differences_last_stage": flips, "elements": f.E,
+           "device_status": [f.sync_status(), m.sync_status()]}
+    f.close()
+    m.close()
+    del Uf, Um
+    return out
+
+
+def _new_net(pkg):
+    """A network with seeded uniform initial weights U(+-sqrt(3 / fan_in))."""
+    init = dg_inputs.uniform(5, 9, np.arange(pkg.abi.N_NET_PARAMS))
+    params = np.zeros(pkg.abi.N_NET_PARAMS)
+    for o, fan, cnt in ((0, 3, 192), (256, 64, 4096), (4416, 64, 64)):
+        params[o:o + cnt] = np.sqrt(3.0 / fan) * (2.0 * init[o:o + cnt] - 1.0)
+    return pkg.abi.dg_c2p_net_create(params.astype(np.float32), (-5.0, 4.0, -9.0, 3.0, -4.5, 4.5))
+
+
+def _c2p_states(pkg, torch, seed, count, gamma):
+    """`count` (a multiple of 64) seeded primitive states of the con2prim
+    distribution (rho log-uniform [1e-8, 10], W uniform [1, 10] on uniform
+    directions, eps log-uniform [1e-6, 1e2]) and their conserved states from the
+    library's prim -> cons (a helper mesh of 4^3-node elements holds them)."""
+    prim = torch.from_numpy(np.ascontiguousarray(dg_inputs.c2p_samples(seed, count, gamma=gamma))).cuda()
+    E = count // 64
+    kx = min(E, 64)
+    ky = min(E // kx, 64)
+    kz = E // (kx * ky)
+    helper = pkg.Mesh(system=1, K=(kx, ky, kz), n=4, gamma=gamma)
+    assert helper.E * 64 == count
+    Ug = helper.state()
+    pkg.abi.dg_prim2con(helper.h, prim, Ug)
+    helper.close()
+    return Ug.permute(1, 0, 2).reshape(5, count).contiguous(), prim
+
+
+def _train_guess_net(pkg, torch, w):
     """Train the learned con2prim guess (untimed) on pairs the method generates for
-    this problem class: the conserved states and FP64 pressures of the first six
-    FP64 steps of the same blast with another noise seed (2), 2^18 pairs sampled
-    from them, plus 2^16 states of the generic con2prim distribution (rho
-    log-uniform [1e-8, 10], W uniform [1, 10], eps log-uniform [1e-6, 1e2]).
-    Twenty epochs of Adam, batch 2048."""
-    w = WORKLOAD
+    the blast: the conserved states and FP64 pressures of the first six FP64 steps
+    of the same blast with another noise seed (2), 2^18 pairs sampled from them,
+    plus 2^16 states of the generic con2prim distribution.  Twenty epochs of
+    Adam, batch 2048."""
     g = w["gamma"]
-    mesh = pkg.Mesh(system=w["system"], K=w["K"], n=w["n"], flux=w["flux"], limiter=w["limiter"], gamma=g)
-    xyz = mesh.coords().cpu().numpy()
-    U = mesh.from_prim(torch.from_numpy(dg_inputs.blast_sr(xyz, seed=2)).cuda())
+    mesh = pkg.Mesh(precision=0, **_mesh_kw(w))
+    U = _state(pkg, torch, w, mesh, seed=2)
     cons, pres = [], []
     P = torch.empty((mesh.E, 4, mesh.nn), dtype=torch.float64, device="cuda")
     for _ in range(6):
@@ -194,32 +296,127 @@ def _train_guess_net(pkg, torch):
     cons, pres = torch.cat(cons, 1), torch.cat(pres)
     gen = torch.Generator().manual_seed(2)
     pick = torch.randperm(cons.shape[1], generator=gen)[: 1 << 18].cuda()
-    n_gen = 1 << 16
-    prim = torch.from_numpy(np.ascontiguousarray(dg_inputs.c2p_samples(7, n_gen, gamma=g))).cuda()
-    helper = pkg.Mesh(system=1, K=(16, 8, 8), n=4, gamma=g)   # 1024 x 64 = 2^16 nodes
-    Ug = helper.state()
-    pkg.abi.dg_prim2con(helper.h, prim, Ug)
-    helper.close()
-    cons = torch.cat([cons[:, pick], Ug.permute(1, 0, 2).reshape(5, n_gen)], 1).contiguous()
+    Ug, prim = _c2p_states(pkg, torch, 7, 1 << 16, g)
+    cons = torch.cat([cons[:, pick], Ug], 1).contiguous()
     pres = torch.cat([pres[pick], prim[4]]).contiguous()
-    n_samp = cons.shape[1]
-    init = dg_inputs.uniform(5, 9, np.arange(pkg.abi.N_NET_PARAMS))
-    params = np.zeros(pkg.abi.N_NET_PARAMS)
-    for o, fan, cnt in ((0, 3, 192), (256, 64, 4096), (4416, 64, 64)):  # W1, W2, W3: U(+-sqrt(3/fan_in))
-        params[o:o + cnt] = np.sqrt(3.0 / fan) * (2.0 * init[o:o + cnt] - 1.0)
-    net = pkg.abi.dg_c2p_net_create(params.astype(np.float32), (-5.0, 4.0, -9.0, 3.0, -4.5, 4.5))
+    net = _new_net(pkg)
     epochs = 20
     losses = torch.zeros(epochs, dtype=torch.float32, device="cuda")
     t0 = time.time()
-    pkg.abi.dg_c2p_net_train(net, n_samp, cons, pres, epochs, 2048, 2e-3, losses)
+    pkg.abi.dg_c2p_net_train(net, cons.shape[1], cons, pres, epochs, 2048, 2e-3, losses)
     torch.cuda.synchronize()
-    info = {"pairs": n_samp, "source": "blast seed 2, FP64 steps 0-5 (2^18) + generic con2prim states (2^16)",
+    info = {"pairs": int(cons.shape[1]),
+            "source": "blast seed 2, FP64 steps 0-5 (2^18) + generic con2prim states (2^16)",
             "epochs": epochs, "batch": 2048, "train_s": round(time.time() - t0, 3),
             "loss_first_last": [float(losses[0]), float(losses[-1])]}
     return net, info
 
 
-def _ensemble(pkg, torch, net, args):
+def _con2prim_bench(pkg, torch, reps=3):
+    """Config 3: 2^24 FP64 con2prim solves (Sec. 2.1.2) from the standard guess and
+    from the learned guess (network trained on 2^22 generated pairs, disjoint
+    seed), timed with CUDA events; the results agree to the solver's resolution."""
+    g = 4.0 / 3.0
+    tr_cons, tr_prim = _c2p_states(pkg, torch, 11, 1 << 22, g)
+    net = _new_net(pkg)
+    epochs = 8
+    losses = torch.zeros(epochs, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.time()
+    pkg.abi.dg_c2p_net_train(net, 1 << 22, tr_cons, tr_prim[4].contiguous(), epochs, 4096, 2e-3, losses)
+    torch.cuda.synchronize()
+    train_s = time.time() - t0
+    del tr_cons, tr_prim
+    N = 1 << 24
+    cons, prim_true = _c2p_states(pkg, torch, 3, N, g)
+    del prim_true
+    guess = torch.empty(N, dtype=torch.float64, device="cuda")
+    out = torch.empty((5, N), dtype=torch.float64, device="cuda")
+    it = torch.empty(N, dtype=torch.int32, device="cuda")
+    st = torch.empty(N, dtype=torch.int32, device="cuda")
+    res, prims = {}, {}
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    for name in ("standard", "learned"):
+        times, gtimes = [], []
+        for r in range(reps + 1):
+            torch.cuda.synchronize()
+            ev[0].record()
+            if name == "learned":
+                pkg.abi.dg_c2p_net_guess(net, N, g, cons, guess)
+            ev[1].record()
+            pkg.abi.dg_con2prim(N, g, cons, out, guess if name == "learned" else None, it, st)
+            ev[2].record()
+            torch.cuda.synchronize()
+            if r:  # the first repetition is a warm-up
+                gtimes.append(ev[0].elapsed_time(ev[1]))
+                times.append(ev[1].elapsed_time(ev[2]))
+        itn = it.to(torch.float64)
+        ms = float(np.median(times))
+        gms = float(np.median(gtimes)) if name == "learned" else 0.0
+        res[name] = {"con2prim_ms": ms, "guess_ms": gms, "total_ms": ms + gms,
+                     "solves_per_s": N / ((ms + gms) / 1e3), "mean_iters": float(itn.mean()),
+                     "max_iters": int(it.max()), "failed": int((st != 0).sum())}
+        prims[name] = out[4].clone()
+    p0, p1 = prims["standard"], prims["learned"]
+    rel = ((p1 - p0).abs() / p0.abs()).max().item()
+    pkg.abi.dg_c2p_net_destroy(net)
+    return {"workload": "2^24 con2prim solves, gamma 4/3, rho log-uniform [1e-8, 10], W uniform [1, 10], "
+                        "eps log-uniform [1e-6, 1e2], seed 3; FP64 bracketed Newton",
+            "states": N, "net": {"pairs": 1 << 22, "seed": 11, "epochs": epochs, "batch": 4096,
+                                  "train_s": round(train_s, 3),
+                                  "loss_first_last": [float(losses[0]), float(losses[-1])]},
+            "standard_guess": res["standard"], "learned_guess": res["learned"],
+            "speedup_con2prim_only": res["standard"]["con2prim_ms"] / res["learned"]["con2prim_ms"],
+            "speedup_with_guess": res["standard"]["total_ms"] / res["learned"]["total_ms"],
+            "max_rel_diff_pressure": rel}
+
+
+def _sr_blast(pkg, torch, args):
+    """The relativistic blast (secondary): mixed with the learned guess, mixed
+    warm-started, FP64; L2 flushed between steps (its state fits in L2)."""
+    w = BLAST
+    setup = pkg.Mesh(precision=0, **_mesh_kw(w))
+    U0 = _state(pkg, torch, w, setup)
+    setup.close()
+    net, net_info = _train_guess_net(pkg, torch, w)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    out = {"workload": "SR blast, 16^3 elements, 5 LGL nodes/axis (512,000 nodes), HLL, MinModN, con2prim per node, "
+                       "CFL 0.2", "l2_between_steps": "flushed (256 MiB write)", "c2p_net": net_info}
+    nodes = _nodes(w)
+    steps = args.sr_steps
+    for key, precision, use_net in (("mixed_learned", 1, net), ("mixed_warm_start", 1, None), ("plain_fp64", 0, None)):
+        m = pkg.Mesh(precision=precision, **_mesh_kw(w))
+        if use_net is not None:
+            m.set_c2p_net(use_net)
+        U = U0.clone()
+        for _ in range(max(3, args.warmup)):
+            m.rk3_step(U, cfl=w["cfl"])
+        ms, prof = _timed_steps(pkg, torch, m, U, w, steps, None, flush=flush)
+        out[key] = {"value": nodes * 5 * steps / (sum(ms) / 1e3), "unit": UNIT, "ms_per_step": sum(ms) / steps,
+                    "kernels": _kern(prof), "device_status": m.sync_status()}
+        m.close()
+    acc = {}
+    for name, use_net in (("learned", net), ("warm_start", None)):
+        f = pkg.Mesh(precision=0, **_mesh_kw(w))
+        m = pkg.Mesh(precision=1, **_mesh_kw(w))
+        if use_net is not None:
+            m.set_c2p_net(use_net)
+        Uf, Um = U0.clone(), U0.clone()
+        dtv = torch.zeros(1, dtype=torch.float64, device="cuda")
+        for _ in range(10):
+            f.rk3_step(Uf, cfl=w["cfl"], dt_used=dtv)
+            m.rk3_step(Um, dt=float(dtv.item()))
+        rel = _rel_l2(torch, _lgl_weights3(pkg, w["n"]), Um, Uf)
+        acc[name] = {"steps": 10, "rel_l2_vs_fp64_per_var": rel, "max": max(rel)}
+        f.close()
+        m.close()
+    out["mixed_accuracy"] = acc
+    out["speedup_learned_vs_fp64"] = out["plain_fp64"]["ms_per_step"] / out["mixed_learned"]["ms_per_step"]
+    pkg.abi.dg_c2p_net_destroy(net)
+    return out
+
+
+def _ensemble(pkg, torch, args):
     """Ragged ensemble (untimed setup): 256 meshes from the seeded recipe -- system
     NE or SR with probability 1/2, K uniform in [2, 16] per axis, n uniform in
     [3, 8].  NE meshes carry the smooth density wave (LLF, no limiter), SR meshes
@@ -227,6 +424,7 @@ def _ensemble(pkg, torch, net, args):
     Times `ens_steps` steps of (a) the batched per-group launches replayed as one
     CUDA graph per step, after the launch-shape autotuner, and (b) the same meshes
     stepped one by one with dg_rk3_step.  The states (2.7 GB each) exceed L2."""
+    net, _ = _train_guess_net(pkg, torch, BLAST)
     recipe = dg_inputs.ensemble_recipe(5)
     meshes, states = [], []
     for system, K, n in recipe:
@@ -274,6 +472,7 @@ def _ensemble(pkg, torch, net, args):
     pkg.abi.dg_ensemble_destroy(ens)
     for m in meshes:
         m.close()
+    pkg.abi.dg_c2p_net_destroy(net)
     dof = nodes * 5 * args.ens_steps
     return {"workload": "256 meshes: NE smooth wave (LLF) or SR blast (HLL, MinModN, learned guess), "
                         "K in [2,16], n in [3,8], seed 5, mixed precision, CFL 0.2",
@@ -286,77 +485,34 @@ def _ensemble(pkg, torch, net, args):
             "device_status": status}
 
 
-def _measure(pkg, torch, precision, args, dist, U0, net=None):
-    """Warm-up, then K graph-replayed steps timed with per-step CUDA events (L2
-    flushed between steps, outside the event pairs), then K profiled steps for
-    per-kernel durations."""
-    w = WORKLOAD
-    mesh = pkg.Mesh(system=w["system"], K=w["K"], n=w["n"], flux=w["flux"], limiter=w["limiter"],
-                    gamma=w["gamma"], precision=precision)
-    if net is not None:
-        mesh.set_c2p_net(net)
-    shape = None
-    U = U0.clone()
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    for _ in range(args.warmup):
-        mesh.rk3_step(U, cfl=w["cfl"])
-    torch.cuda.synchronize()
-    if mesh.sync_status() != 0:
-        raise RuntimeError("warm-up steps reported a device error")
-    if precision == 1:
-        # tuned on the warmed-up state, the one the timed steps start from
-        shape = _tune_launch_shape(pkg, mesh, U)
-    graph = torch.cuda.CUDAGraph()
-    side = torch.cuda.Stream()
-    side.wait_stream(torch.cuda.current_stream())
-    with torch.cuda.stream(side):
-        mesh.rk3_step(U, cfl=w["cfl"])  # one more warm step on the capture stream
-    torch.cuda.current_stream().wait_stream(side)
-    with torch.cuda.graph(graph):
-        mesh.rk3_step(U, cfl=w["cfl"])
-    torch.cuda.synchronize()
-    stream = torch.cuda.current_stream()
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    for k in range(args.steps):
-        flush.fill_(float(k))
-        starts[k].record(stream)
-        graph.replay()
-        ends[k].record(stream)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    status = mesh.sync_status()
-    # per-kernel durations: the same steps launched directly with event pairs
-    pkg.abi.dg_profile_enable(mesh.h, True)
-    for k in range(args.steps):
-        flush.fill_(float(k))
-        mesh.rk3_step(U, cfl=w["cfl"])
-    torch.cuda.synchronize()
-    prof = pkg.abi.dg_profile_read(mesh.h)
-    pkg.abi.dg_profile_enable(mesh.h, False)
-    return mesh, graph, step_ms, prof, status, U, shape
+# DRAM bytes per k_ne_stage launch on the headline workload (mean over the three
+# stages of a step), from a one-kernel ncu capture of the same kernel on the
+# 32^3-element case of the same problem scaled by the node count (64^3 / 32^3 = 8).
+# Reported only while the kernel's sources still hash to their state at capture.
+TRAFFIC_BYTES_PER_LAUNCH = None
+TRAFFIC_SOURCES = ("paper_1609_00098_gb300/csrc/dg_ne_mixed.cuh", "paper_1609_00098_gb300/csrc/dg_internal.h")
+TRAFFIC_SOURCES_SHA256 = ""
 
 
-def _tune_launch_shape(pkg, mesh, U0):
-    """Pick the stage kernel's elements per CTA and volume contraction for this
-    mesh with the library's autotuner (a one-mesh ensemble times the candidates
-    on a copy of the given state), and set them on the mesh (untimed)."""
-    U = U0.clone()
-    ens = pkg.abi.dg_ensemble_create([mesh.h], [U])
-    try:
-        pkg.abi.dg_ensemble_tune(ens)
-        g = pkg.abi.dg_ensemble_groups(ens)[0]
-    finally:
-        pkg.abi.dg_ensemble_destroy(ens)
-    mesh.set_option(pkg.abi.OPT_ELEMENTS_PER_CTA, g["epb"])
-    mesh.set_option(pkg.abi.OPT_TENSOR_CORE_CONTRACTION, g["tc"])
-    return {"elements_per_cta": g["epb"], "volume_contraction": "tensor cores (split-BF16x3)" if g["tc"]
-            else "FP32 FMA"}
+def _traffic():
+    import hashlib
+    if TRAFFIC_BYTES_PER_LAUNCH is None:
+        return None
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return TRAFFIC_BYTES_PER_LAUNCH if h.hexdigest() == TRAFFIC_SOURCES_SHA256 else None
+
+
+def _design_bytes_per_node_stage(masked_all):
+    """Compulsory bytes per node of one k_ne_stage launch of this design (FP64 U^n,
+    FP32 stage differences), mean over the three stages: stage 1 reads U^n (40 B)
+    and writes R(U^n) (20 B); stages 2 and 3 read U^n and, where a variable is not
+    limited, its difference (20 B), and write the next difference (20 B).  With
+    every variable limited (the shear layer after its first stage) the differences
+    of stages 2 and 3 are not read."""
+    return (60.0 + 2 * (60.0 if masked_all else 80.0)) / 3.0
 
 
 def run_ours(args):
@@ -369,65 +525,45 @@ def run_ours(args):
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    w = WORKLOAD
-    setup = pkg.Mesh(system=w["system"], K=w["K"], n=w["n"], flux=w["flux"], limiter=w["limiter"],
-                     gamma=w["gamma"])
-    nodes = setup.E * setup.nn
-    U0 = _init_state(pkg, setup, torch)
-    net, net_info = _train_guess_net(pkg, torch)
-
-    # accuracy at equal time steps (untimed): mixed (learned guess, and warm
-    # start) vs plain FP64 after a few steps
-    mixed_acc = None
-    if not args.no_accuracy:
-        mixed_acc = {}
-        for name, use_net in (("learned", net), ("warm_start", None)):
-            mix = pkg.Mesh(system=w["system"], K=w["K"], n=w["n"], flux=w["flux"], limiter=w["limiter"],
-                           gamma=w["gamma"], precision=1)
-            if use_net is not None:
-                mix.set_c2p_net(use_net)
-            Uf, Um = U0.clone(), U0.clone()
-            dtv = torch.zeros(1, dtype=torch.float64, device="cuda")
-            for _ in range(args.acc_steps):
-                setup.rk3_step(Uf, cfl=w["cfl"], dt_used=dtv)
-                mix.rk3_step(Um, dt=float(dtv.item()))
-            torch.cuda.synchronize()
-            num = torch.sqrt(((Um - Uf) ** 2).sum(dim=(0, 2)))
-            den = torch.sqrt((Uf ** 2).sum(dim=(0, 2)))
-            rel = (num / torch.clamp(den, min=1e-3 * float(den.max()))).cpu().tolist()
-            mixed_acc[name] = {"steps": args.acc_steps, "rel_l2_vs_fp64_per_var": rel, "max": max(rel)}
-            mix.close()
+    w = KH
+    nodes = _nodes(w)
+    setup = pkg.Mesh(precision=0, **_mesh_kw(w))
+    U0 = _state(pkg, torch, w, setup)
     setup.close()
+
+    mixed_acc = None if args.no_accuracy else _kh_accuracy(pkg, torch, U0, args.acc_steps)
 
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
-    results = {}
-    for key, precision, use_net in (("learned", 1, net), ("warm_start", 1, None), ("fp64", 0, None)):
-        results[key] = _measure(pkg, torch, precision, args, dist, U0, use_net)
+    runs = {}
+    for key, precision in (("mixed", 1), ("fp64", 0)):
+        m = pkg.Mesh(precision=precision, **_mesh_kw(w))
+        U = U0.clone()
+        for _ in range(args.warmup):
+            m.rk3_step(U, cfl=w["cfl"])
+        torch.cuda.synchronize()
+        if m.sync_status() != 0:
+            raise RuntimeError("warm-up steps reported a device error")
+        ms, prof = _timed_steps(pkg, torch, m, U, w, args.steps if key == "mixed" else args.fp64_steps, dist)
+        runs[key] = (m, ms, prof, m.sync_status(), U)
     clk = clocks.stop()
-
-    def agg(ms):
-        return max_over_ranks(float(sum(ms)), dist)
-
-    mesh, graph, step_ms, prof, status, mesh_state, shape = results["learned"]
-    total_ms = agg(step_ms)
-    ms_per_step = total_ms / args.steps
+    mesh, step_ms, prof, status, mesh_state = runs["mixed"]
+    total_ms = max_over_ranks(float(sum(step_ms)), dist)
     value = whole_job_rate(nodes, ws, args.steps, total_ms)
-    f_mesh, f_graph, f_ms, f_prof, f_status, _, _ = results["fp64"]
-    f_total = agg(f_ms)
-    w_mesh, w_graph, w_ms, w_prof, w_status, _, w_shape = results["warm_start"]
-    w_total = agg(w_ms)
+    f_mesh, f_ms, f_prof, f_status, _ = runs["fp64"]
+    f_total = max_over_ranks(float(sum(f_ms)), dist)
+    f_value = whole_job_rate(nodes, ws, args.fp64_steps, f_total)
+    f_mesh.close()
+    del runs["fp64"]
 
     # end to end through the C ABI with host buffers (mixed path): every step copies
     # the state from pinned host memory to the device, advances it with
     # dg_rk3_step, and copies it back, so the host copy evolves as the device state
-    # did above.  The three are captured once into a CUDA graph (as the device-timed
-    # steps are) and replayed; per-step event pairs, the L2 flush between steps
-    # outside them.
+    # did above.  The three are captured into a CUDA graph (as the device-timed
+    # steps are) and replayed; per-step event pairs.
     host_state = mesh_state.cpu().pin_memory()
     Ud = torch.empty_like(U0)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     side = torch.cuda.Stream()
     side.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(side):  # one eager end-to-end step before the capture
@@ -441,18 +577,18 @@ def run_ours(args):
         mesh.rk3_step(Ud, cfl=w["cfl"])
         host_state.copy_(Ud, non_blocking=True)
     stream = torch.cuda.current_stream()
-    e_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    e_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    e_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.e2e_steps)]
+    e_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.e2e_steps)]
     torch.cuda.synchronize()
-    for k in range(args.steps):
-        flush.fill_(float(k))
+    for k in range(args.e2e_steps):
         e_s[k].record(stream)
         e2e_graph.replay()
         e_e[k].record(stream)
     torch.cuda.synchronize()
-    e2e_ms = agg([a.elapsed_time(b) for a, b in zip(e_s, e_e)])
-    e2e = ws * nodes * 5 * args.steps / (e2e_ms / 1e3)
+    e2e_ms = max_over_ranks(float(sum(a.elapsed_time(b) for a, b in zip(e_s, e_e))), dist)
+    e2e = ws * nodes * 5 * args.e2e_steps / (e2e_ms / 1e3)
     state_bytes = nodes * 5 * 8
+    del e2e_graph, Ud, host_state
 
     peaks = {}
     try:
@@ -460,113 +596,120 @@ def run_ours(args):
     except Exception:
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-
-    def kern(pr):
-        tot = max(1e-12, sum(x[0] for x in pr.values()))
-        return {c: {"ms_total": round(v[0], 4), "launches": int(v[1]), "share": round(v[0] / tot, 4)}
-                for c, v in pr.items() if v[1]}
-
     st_ms, st_n = prof["stage"]
-    stage_avg_s = (st_ms / st_n) / 1e3 if st_n else float("nan")
-    achieved = _algorithmic(nodes, 1, learned=True) / stage_avg_s / 1e9
-    launches = int(sum(c for _, c in prof.values()))
+    stage_avg_s = (st_ms / st_n) / 1e3
+    bytes_8d = SURVEY_BYTES_PER_NODE_STAGE * nodes
+    bytes_design = _design_bytes_per_node_stage(True) * nodes
+    achieved = bytes_8d / stage_avg_s / 1e9
+    launches = int(sum(v[1] for v in prof.values()))
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 arithmetic, f64 state and RK accumulation",
-        "data": "synthetic (seeded blast initial data)",
-        "config": _config({"precision": "mixed", "c2p_guess": "learned (in-kernel MLP; stage 1 reuses the CFL pass's solve of U^n)",
-                           "launch_shape": dict(shape, picked_by="dg_ensemble_tune"),
-                           "parallelism": "replicas" if ws > 1 else "single GPU",
-                           "step_launch": "CUDA graph replay"}),
-        "variant": "mixed+learned (FP32 con2prim from the in-kernel MLP guess, FP32 fluxes/contraction/face "
-                   "fluxes, FP64 stage states and RK accumulation)",
-        "plain_fp64": {"value": ws * nodes * 5 * args.steps / (f_total / 1e3), "unit": UNIT,
-                       "ms_per_step": f_total / args.steps, "kernels": kern(f_prof), "device_status": f_status},
-        "speedup_vs_plain_fp64": f_total / total_ms,
-        "mixed_warm_start": {"value": ws * nodes * 5 * args.steps / (w_total / 1e3), "unit": UNIT,
-                             "ms_per_step": w_total / args.steps, "kernels": kern(w_prof),
-                             "device_status": w_status, "launch_shape": w_shape,
-                             "note": "con2prim starts from the previous pass's pressure (8 B/node/stage carried)"},
-        "c2p_net": net_info,
+        "data": "synthetic (seeded Kelvin-Helmholtz initial data)",
+        "config": _config({"precision": "mixed", "parallelism": "replicas" if ws > 1 else "single GPU",
+                           "step_launch": "CUDA graph replay (7 kernels per step)"}),
+        "variant": "mixed (Newtonian: no con2prim, so the learned guess does not apply; the learned form is "
+                   "measured on the relativistic blast in sr_blast and standalone in con2prim)",
+        "plain_fp64": {"value": f_value, "unit": UNIT, "ms_per_step": f_total / args.fp64_steps,
+                       "steps": args.fp64_steps, "kernels": _kern(f_prof), "device_status": f_status},
+        "speedup_vs_plain_fp64": value / f_value,
         "mixed_accuracy": mixed_acc,
-        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes},
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes,
+                "steps": args.e2e_steps},
         "gpu_launches": launches,
-        "kernels": kern(prof),
-        "roofline": {"kernel": "k_stage_mixed (fused con2prim + RHS + SSP-RK3 stage update + limiter summaries)", "bound": "hbm",
-                     "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                     "traffic": _traffic("learned"), "bytes_per_launch": _algorithmic(nodes, 1, learned=True),
-                     "avg_launch_ms": stage_avg_s * 1e3,
+        "kernels": _kern(prof),
+        "roofline": {"kernel": "k_ne_stage (fused RHS of eq:411 + SSP-RK3 stage difference + limiter summaries)",
+                     "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "traffic": _traffic(),
+                     "bytes_per_launch": bytes_8d, "bytes_per_node": SURVEY_BYTES_PER_NODE_STAGE,
+                     "bytes_rule": "survey roofline model: FP64 stage states, 320 B per node-step, mean 106.7 B per "
+                                   "node and stage launch",
+                     "design_bytes_per_launch": bytes_design,
+                     "design_frac": bytes_design / stage_avg_s / 1e9 / hbm_peak,
+                     "avg_launch_ms": stage_avg_s * 1e3, "launches_timed": int(st_n),
+                     "timing": "CUDA events captured in the timed graph replays",
                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks else "fallback"},
+        "step_roofline": {"ceiling_dof_updates_per_s": hbm_peak * 1e9 / 64.0,
+                          "frac": value / (hbm_peak * 1e9 / 64.0),
+                          "rule": "64 B per dof-update (320 B per node-step) over the measured HBM bandwidth"},
         "clocks": clk,
         "device_status": status,
     }
+    mesh.close()
+    del mesh_state, runs
+    torch.cuda.empty_cache()
+    if not args.no_sr:
+        out["sr_blast"] = _sr_blast(pkg, torch, args)
+    if not args.no_con2prim:
+        out["con2prim"] = _con2prim_bench(pkg, torch)
     if not args.no_ensemble:
-        out["ensemble"] = _ensemble(pkg, torch, net, args)
+        out["ensemble"] = _ensemble(pkg, torch, args)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(seconds=args.cpu_seconds)
-    for r in results.values():
-        r[0].close()
-    pkg.abi.dg_c2p_net_destroy(net)
     if dist:
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(out), flush=True)
 
 
-def _oracle_mesh():
+def _oracle_sample_mesh():
+    """The oracle's bounded sample of the headline workload: the same problem on
+    a 16^3-element periodic box (1/64 of the elements)."""
     import oracle
-    w = WORKLOAD
-    spec = oracle.MeshSpec(system=w["system"], K=w["K"], n=w["n"], flux=w["flux"], limiter=w["limiter"],
-                           gamma=w["gamma"])
+    w = KH
+    spec = oracle.MeshSpec(system=w["system"], K=KH_SAMPLE_K, n=w["n"], flux=w["flux"], limiter=w["limiter"],
+                           gamma=w["gamma"], lo=w["lo"], hi=w["hi"])
     return oracle.Mesh(spec)
 
 
 def cpu_baseline(seconds: float = 15.0):
-    """The FP64 oracle, as it stands, on the host cores: as many steps of the same
-    workload as fit in about `seconds` (at least one)."""
-    import dg_inputs as di
-    om = _oracle_mesh()
-    U = om.from_prim(di.blast_sr(om.coords(), seed=WORKLOAD["seed"]))
+    """The FP64 oracle, as it stands, on the host cores: as many CFL steps of the
+    bounded sample as fit in about `seconds` (at least one)."""
+    om = _oracle_sample_mesh()
+    U = om.from_prim(dg_inputs.kh_ne(om.coords(), seed=KH["seed"]))
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     t0 = time.perf_counter()
     steps = 0
     while True:
-        h = om.cfl_dt(U, WORKLOAD["cfl"])
-        U = om.rk3_step(U, h)
+        U = om.rk3_step(U, om.cfl_dt(U, KH["cfl"]))
         steps += 1
         if time.perf_counter() - t0 > seconds:
             break
     el = time.perf_counter() - t0
     nodes = om.E * om.nn
     return {"value": nodes * 5 * steps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{steps} CFL steps of the full workload from its initial state ({el:.1f} s)"}
+            "sample": f"{steps} CFL steps of the Kelvin-Helmholtz problem on a 16^3-element box, n = 6 "
+                      f"({nodes} nodes, 1/64 of the workload) from its initial state ({el:.1f} s)"}
 
 
 def run_reference(args):
-    """The oracle timed as the reference arm: each step is one full step of the
-    workload on the host cores."""
+    """The oracle timed as the reference arm: each step is one CFL step of the
+    bounded sample of the workload on the host cores."""
     ws, rank, local = _dist()
     if rank != 0:
         return
-    import dg_inputs as di
-    om = _oracle_mesh()
-    U = om.from_prim(di.blast_sr(om.coords(), seed=WORKLOAD["seed"]))
+    om = _oracle_sample_mesh()
+    U = om.from_prim(dg_inputs.kh_ne(om.coords(), seed=KH["seed"]))
     for _ in range(args.warmup):
-        U = om.rk3_step(U, om.cfl_dt(U, WORKLOAD["cfl"]))
+        U = om.rk3_step(U, om.cfl_dt(U, KH["cfl"]))
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        U = om.rk3_step(U, om.cfl_dt(U, WORKLOAD["cfl"]))
+        U = om.rk3_step(U, om.cfl_dt(U, KH["cfl"]))
     el = time.perf_counter() - t0
     nodes = om.E * om.nn
     value = nodes * 5 * args.steps / el
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded blast initial data)",
-           "config": _config({"precision": "fp64", "implementation": "FP64 CPU oracle (C, OpenMP)"}),
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded Kelvin-Helmholtz initial data)",
+           "config": _config({"precision": "fp64", "implementation": "FP64 CPU oracle (C, OpenMP)",
+                              "sample": "each step: one CFL step of the same problem on a 16^3-element box "
+                                        f"({nodes} nodes, 1/64 of the workload)"}),
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                            "sample": f"{args.steps} full steps after {args.warmup} warm-up steps"},
+                            "sample": f"{args.steps} CFL steps of the 16^3-element box after {args.warmup} warm-up "
+                                      "steps"},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -576,6 +719,9 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--fp64-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--sr-steps", type=int, default=20)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -583,6 +729,8 @@ def main():
     ap.add_argument("--acc-steps", type=int, default=10)
     ap.add_argument("--ens-steps", type=int, default=20)
     ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--no-sr", action="store_true")
+    ap.add_argument("--no-con2prim", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -25,7 +25,7 @@ def test_reference_arm_json_line():
     assert d["value"] > 0 and d["higher_is_better"] is True and d["n_gpus"] == 1
     assert d["steps"] == 1 and d["warmup"] == 3 and d["ms_per_step"] > 0
     assert d["scaling"] == "weak" and d["vs_baseline"] is None and d["dtype"] == "f64"
-    assert "workload" in d["config"] and d["config"]["nodes"] == 512000
+    assert "workload" in d["config"] and d["config"]["nodes"] == 64 ** 3 * 6 ** 3 and "sample" in d["config"]
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}

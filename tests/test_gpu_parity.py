@@ -245,23 +245,51 @@ def test_unphysical_state_reports_status(pkg):
     assert gm.sync_status() == 0  # cleared
 
 
-def test_full_size_blast_one_step(pkg):
-    """The bench workload (SR blast, 16^3 elements, n=5, HLL, MinModN) at full size,
-    in the launch configuration the bench times: one CFL step on both sides."""
+def _full_size_ten_steps(pkg, kw, kind):
+    """Ten CFL steps at full size on both sides, in the launch configuration the
+    bench times: the FP64 path bitwise equal to the oracle (dt of every step, the
+    last step's troubled flags, the state); the mixed path, stepped on the
+    oracle's dt sequence, within the mixed bar of 1e-6 relative L2 per conserved
+    variable (LGL quadrature, each norm floored at 1 % of the largest; Sec. 3.4,
+    SSP-RK3 with the limiter after every stage)."""
     import torch
-    om, gm = _pair(pkg, system=1, K=(16, 16, 16), n=5, flux=1, limiter=1)
-    U = _init(om, "blast", seed=1)
-    h = om.cfl_dt(U, 0.2)
-    to = np.zeros(om.E, dtype=np.uint8)
-    Uo = om.rk3_step(U, h, to)
-    Ug = _gpu(U)
+    om, gm = _pair(pkg, **kw)
+    U0 = _init(om, kind, seed=1)
+    Ug = _gpu(U0)
     dt = torch.zeros(1, dtype=torch.float64, device="cuda")
     tg = torch.zeros(om.E, dtype=torch.uint8, device="cuda")
-    gm.rk3_step(Ug, cfl=0.2, dt_used=dt, troubled=tg)
+    U, hs = U0, []
+    for _ in range(10):
+        h = om.cfl_dt(U, 0.2)
+        to = np.zeros(om.E, dtype=np.uint8)
+        U = om.rk3_step(U, h, to)
+        hs.append(h)
+        gm.rk3_step(Ug, cfl=0.2, dt_used=dt, troubled=tg)
+        assert dt.item() == h
     assert gm.sync_status() == 0
-    assert abs(dt.item() - h) <= 4e-16 * h
     assert np.array_equal(tg.cpu().numpy(), to)
-    assert _rel(Ug.cpu().numpy(), Uo).max() <= TOL
+    assert np.array_equal(Ug.cpu().numpy(), U)
+    del gm, Ug
+    mm = pkg.Mesh(precision=1, **kw)
+    Um = _gpu(U0)
+    tm = torch.zeros(om.E, dtype=torch.uint8, device="cuda")
+    for h in hs:
+        mm.rk3_step(Um, dt=h, troubled=tm)
+    assert mm.sync_status() == 0
+    got = Um.cpu().numpy()
+    _, d = om.norms(got, U)
+    _, ref = om.norms(U, np.zeros_like(U))
+    rel = d / np.maximum(ref, 1e-2 * ref.max())
+    assert np.all(rel <= 1e-6), rel
+    # the limiter decides the same way on all but a few elements (its 1e-8 face
+    # test sits at the FP32 level of the mixed right-hand side)
+    flips = np.count_nonzero(tm.cpu().numpy() != to)
+    assert flips <= 1e-3 * om.E, flips
+
+
+def test_full_size_blast_ten_steps(pkg):
+    """The SR blast at full size (16^3 elements, n = 5, HLL, MinModN)."""
+    _full_size_ten_steps(pkg, dict(system=1, K=(16, 16, 16), n=5, flux=1, limiter=1), "blast")
 
 
 def test_full_size_con2prim_2p24(pkg):
@@ -283,35 +311,11 @@ def test_full_size_con2prim_2p24(pkg):
     assert np.array_equal(it.cpu().numpy(), ito)
 
 
-def test_full_size_kh_one_step(pkg):
+def test_full_size_kh_ten_steps(pkg):
     """The Kelvin-Helmholtz workload at full size (64^3 elements, n = 6, HLL,
-    MinModN; 56.6 M nodes): one CFL step, FP64 path bitwise equal to the oracle
-    (state, troubled flags, dt); the mixed path within FP32 rounding of it."""
-    import torch
-    kw = dict(system=0, K=(64, 64, 64), n=6, flux=1, limiter=1, gamma=5.0 / 3.0, lo=(-0.5,) * 3, hi=(0.5,) * 3)
-    om, gm = _pair(pkg, **kw)
-    U = _init(om, "kh", seed=1)
-    h = om.cfl_dt(U, 0.2)
-    to = np.zeros(om.E, dtype=np.uint8)
-    Uo = om.rk3_step(U, h, to)
-    Ug = _gpu(U)
-    dt = torch.zeros(1, dtype=torch.float64, device="cuda")
-    tg = torch.zeros(om.E, dtype=torch.uint8, device="cuda")
-    gm.rk3_step(Ug, cfl=0.2, dt_used=dt, troubled=tg)
-    assert gm.sync_status() == 0
-    assert dt.item() == h
-    assert np.array_equal(tg.cpu().numpy(), to)
-    assert np.array_equal(Ug.cpu().numpy(), Uo)
-    del gm, Ug, tg
-    mm = pkg.Mesh(precision=1, **kw)
-    Um = _gpu(U)
-    mm.rk3_step(Um, dt=h)
-    assert mm.sync_status() == 0
-    # max-norm error against the largest variable's scale (S_z of the shear layer
-    # is zero up to rounding and has no scale of its own): FP32 rounding level
-    sc = np.abs(Uo).max()
-    d = np.abs(Um.cpu().numpy() - Uo).max(axis=(0, 2)) / sc
-    assert d.max() < 2e-6, d
+    MinModN; 56.6 M nodes)."""
+    _full_size_ten_steps(pkg, dict(system=0, K=(64, 64, 64), n=6, flux=1, limiter=1, gamma=5.0 / 3.0,
+                                   lo=(-0.5,) * 3, hi=(0.5,) * 3), "kh")
 
 
 @pytest.mark.parametrize("n,limiter", [(2, 2), (4, 1), (6, 0)])
