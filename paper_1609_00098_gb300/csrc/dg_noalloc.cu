@@ -62,7 +62,8 @@ extern "C" dg_status dg_rhs_static(const dg_mesh_desc *d, const double *U, doubl
     if (!d || !U || !dUdt || U == dUdt) return set_error(DG_ERR_ARG, "desc, U and dUdt must be non-NULL and distinct");
     if (d->system != 0 && d->system != 1) return set_error(DG_ERR_ARG, "system must be 0 or 1");
     if (d->n < 2 || d->n > MAXN) return set_error(DG_ERR_ARG, "n must be in 2..8");
-    if (d->flux != 0 && d->flux != 1) return set_error(DG_ERR_ARG, "flux must be 0 (LLF) or 1 (HLL)");
+    if (d->flux != 0 && d->flux != 1 && !(d->flux == 2 && d->system == 0))
+        return set_error(DG_ERR_ARG, "flux must be 0 (LLF), 1 (HLL) or, for the Newtonian system, 2 (Roe)");
     if (d->precision != DG_PRECISION_FP64) return set_error(DG_ERR_ARG, "dg_rhs_static computes the FP64 path only");
     if (d->bc[0] || d->bc[1] || d->bc[2]) return set_error(DG_ERR_ARG, "dg_rhs_static takes periodic meshes only");
     if (!(d->gamma > 1.0)) return set_error(DG_ERR_ARG, "gamma must be > 1");

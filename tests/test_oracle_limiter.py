@@ -194,7 +194,7 @@ def test_mrs_keeps_smooth_extrema_only_with_alpha():
 
 
 def test_mrs_theta_closed_form_for_an_isolated_bump():
-    """eq:MRSSol (R16) on a density bump in one element of a uniform flow at rest:
+    """eq:MRSSol (Sec. 3.3.3) on a density bump in one element of a uniform flow at rest:
     velocity and pressure are constant, so only the density bounds act, the
     neighbours' means lie below the bump's, and Theta = alpha h^{3/2} /
     (rho_max - rho_0), h the element width.  The bump element becomes U0 +

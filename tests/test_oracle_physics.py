@@ -39,7 +39,7 @@ def test_c2p_round_trip_conditioned():
 
 
 def test_c2p_newton_converges_quadratically():
-    """Reading R7: Newton on f(p) with the exact f'(p).  From a guess 0.1 % off the
+    """Sec. 2.1.2 con2prim: Newton on f(p) with the exact f'(p).  From a guess 0.1 % off the
     root, well-conditioned states (tau/(rho eps) < 10) stop within five
     iterations (the error squares each step; the stopping rule adds one step);
     a wrong derivative would converge only linearly."""

@@ -60,7 +60,7 @@ PLANTED = {
     # limiter summaries: the upper face mean taken one node line inside the element
     "summary_face_index": ("S[2 + 2 * a] = ubar[n - 1];", "S[2 + 2 * a] = ubar[n - 2];",
                            ["tests/test_oracle_limiter.py::test_linear_data_not_limited"]),
-    # limiter summaries: the element slope from the P2 instead of the P1 Legendre coefficient (R5)
+    # limiter summaries: the element slope from the P2 instead of the P1 Legendre coefficient (Sec. 3.3.2)
     "summary_p1_row": ("for (int i = 0; i < n; ++i) c1 = c1 + m->Vinv[1 * n + i] * ubar[i];",
                        "for (int i = 0; i < n; ++i) c1 = c1 + m->Vinv[2 * n + i] * ubar[i];",
                        ["tests/test_oracle_limiter.py"]),
@@ -79,7 +79,7 @@ PLANTED = {
     "c2p_derivative": ("r.df = 1.0 - (g - 1.0) * v2 * (1.0 - D * W / Ep);",
                        "r.df = 1.0 - (g - 1.0) * v2 * (1.0 + D * W / Ep);",
                        ["tests/test_oracle_physics.py::test_c2p_newton_converges_quadratically"]),
-    # CFL: dx_min as the element half-width instead of the smallest LGL node gap (R4)
+    # CFL: dx_min as the element half-width instead of the smallest LGL node gap (Sec. 3.4)
     "cfl_dxmin": ("double h = 0.5 * m->dx[a] * (m->x[1] - m->x[0]);", "double h = 0.5 * m->dx[a];",
                   ["tests/test_oracle_scheme.py::test_cfl_dt_closed_form",
                    "tests/test_oracle_scheme.py::test_ne_smooth_wave_exact_and_order"]),
@@ -93,7 +93,7 @@ PLANTED = {
                               ["tests/test_oracle_physics.py"]),
     # the differentiation matrix's diagonal with the wrong sign (negative-sum trick)
     "dmat_diagonal_sign": ("D[i * n + i] = -s;", "D[i * n + i] = s;", ["tests/test_oracle_lgl.py"]),
-    # MRS bound widening alpha h instead of alpha h^{3/2} (eq:MRSSol, R16)
+    # MRS bound widening alpha h instead of alpha h^{3/2} (eq:MRSSol, Sec. 3.3.3)
     "mrs_width_exponent": ("const double wid = m->d.mrs_alpha * h * sqrt(h);", "const double wid = m->d.mrs_alpha * h;",
                            ["tests/test_oracle_limiter.py::test_mrs_theta_closed_form_for_an_isolated_bump"]),
     # the fix's momentum bound tau (tau + 2 D) with the factor 2 dropped

@@ -92,7 +92,7 @@ def test_ne_smooth_wave_exact_and_order():
 
 
 def test_cfl_dt_closed_form():
-    """Sec. 3.4 with reading R4: dt = C dx_min / lambda_max, dx_min the smallest
+    """Sec. 3.4 time step: dt = C dx_min / lambda_max, dx_min the smallest
     gap between neighbouring LGL nodes on the physical grid, min_a (dx_a/2)(1 -
     1/sqrt(5)) for n = 4 (nodes -1, -1/sqrt 5, 1/sqrt 5, 1), and lambda_max = |v| + c
     for a uniform Newtonian state (c^2 = gamma p / rho)."""
