@@ -377,10 +377,13 @@ __global__ void __launch_bounds__(NeShape<NP>::THREADS, 3) k_ne_stage(const __gr
     const long long ge = e0 + sub;
     const bool live = sub_raw < EPB && ge < a.nelem;
     if (BATCH) {
-        if (live && ln == 0) {
-            const int m = ne_find_slot(a.elem0, a.nslots, ge);
+        // every element slot of the CTA holds a valid mesh slot (past the last
+        // element: the first mesh's), so that per-slot settings, which are the same
+        // for all meshes of a launch, are read consistently by every thread
+        if (sub_raw < EPB && ln == 0) {
+            const int m = live ? ne_find_slot(a.elem0, a.nslots, ge) : 0;
             sSlot[sub] = a.slots[m];
-            sLoc[sub] = ge - a.elem0[m];
+            sLoc[sub] = live ? ge - a.elem0[m] : 0;
         }
         __syncthreads();
     }
@@ -394,7 +397,7 @@ __global__ void __launch_bounds__(NeShape<NP>::THREADS, 3) k_ne_stage(const __gr
     float *const sL = eb + SH::F_L;
     const bool lim_in = ST >= 2 && sl.mask != nullptr;
     const bool do_sn = ST == 1 && sl.SN != nullptr;
-    const float dtf = ST >= 2 ? (float)(sl.dt_ptr ? *sl.dt_ptr : sl.dt) : 0.0f;
+    const float dtf = (ST >= 2 && live) ? (float)(sl.dt_ptr ? *sl.dt_ptr : sl.dt) : 0.0f;
     const float xj = a.x[j], xk = a.x[k];
 
     if (t < EPB) sLamE[t] = 0u;
@@ -894,7 +897,7 @@ __global__ void __launch_bounds__(128) k_ne_decide(const __grid_constant__ NeDec
         const int v = h / 3, ax = h % 3;
         auto S = [&](long long el, int kind) {
             const long long ix = (el * 5 + v) * 10 + kind;
-            return sl.SN[ix] + c * (double)sl.SD[ix];
+            return fma(c, ne_f32_to_f64(sl.SD[ix]), sl.SN[ix]);
         };
         U0 = S(e, 0);
         const double U0m = S(elem_neighbour(e, sl.K, ax, -1), 0);
@@ -915,7 +918,7 @@ __global__ void __launch_bounds__(128) k_ne_decide(const __grid_constant__ NeDec
     for (int v = 0; v < 5; ++v)
         if ((fb >> (3 * v)) & 7u) mask |= 1u << v;
     // replacement parameters: lane 3 v of the half gathers the slopes of v
-    const float shl = (float)(slope * sl.hdx[h % 3]);
+    const float shl = ne_hi(slope * sl.hdx[h % 3]);
     const float s1v = __shfl_down_sync(0xffffffffu, shl, 1);
     const float s2v = __shfl_down_sync(0xffffffffu, shl, 2);
     if (live && a.limiter) {
@@ -926,7 +929,7 @@ __global__ void __launch_bounds__(128) k_ne_decide(const __grid_constant__ NeDec
         if (h < 15 && h % 3 == 0 && ((mask >> (h / 3)) & 1u)) {
             const int v = h / 3;
             sl.M0[e * 5 + v] = U0;
-            sl.SH[e * 5 + v] = make_float4((float)U0, shl, s1v, s2v);
+            sl.SH[e * 5 + v] = make_float4(ne_hi(U0), shl, s1v, s2v);
         }
     } else if (live && h == 0 && sl.troubled) {
         sl.troubled[e] = 0;
