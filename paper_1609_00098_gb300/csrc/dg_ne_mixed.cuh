@@ -358,7 +358,7 @@ __device__ __forceinline__ float ne_final_sum(const NeArgs &a, int kind, Q q)
 // terms with each face taken along +e_a, the lower element lifting
 // -(2/dx_a)(F* - F_L)/w_N, the upper +(2/dx_a)(F* - F_R)/w_0); eq:LLF, eq:HLL,
 // eq:Roe; Sec. 3.4 (SSP-RK3 in the difference form above, CFL maximum).
-template <int NP, int FLX, int ST, int BATCH>
+template <int NP, int FLX, int ST>
 __global__ void __launch_bounds__(NeShape<NP>::THREADS, 3) k_ne_stage(const __grid_constant__ NeArgs a)
 {
     using SH = NeShape<NP>;
@@ -367,8 +367,8 @@ __global__ void __launch_bounds__(NeShape<NP>::THREADS, 3) k_ne_stage(const __gr
     __shared__ long long sNb[EPB][6];
     __shared__ unsigned sMask[EPB][7];  // own (0) and neighbours' (1 + 2 ax + side) limited variables
     __shared__ unsigned sLamE[EPB];  // per element: max wave speed (bits of a non-negative float)
-    __shared__ NeSlot sSlot[BATCH ? EPB : 1];
-    __shared__ long long sLoc[BATCH ? EPB : 1];
+    __shared__ NeSlot sSlot[EPB];
+    __shared__ long long sLoc[EPB];
 
     const int t = threadIdx.x;
     const int sub_raw = t / L, ln = t % L, j = ln % NP, k = ln / NP;
@@ -376,19 +376,18 @@ __global__ void __launch_bounds__(NeShape<NP>::THREADS, 3) k_ne_stage(const __gr
     const long long e0 = (long long)blockIdx.x * EPB;  // first element of the CTA (launch numbering)
     const long long ge = e0 + sub;
     const bool live = sub_raw < EPB && ge < a.nelem;
-    if (BATCH) {
-        // every element slot of the CTA holds a valid mesh slot (past the last
-        // element: the first mesh's), so that per-slot settings, which are the same
-        // for all meshes of a launch, are read consistently by every thread
-        if (sub_raw < EPB && ln == 0) {
-            const int m = live ? ne_find_slot(a.elem0, a.nslots, ge) : 0;
-            sSlot[sub] = a.slots[m];
-            sLoc[sub] = live ? ge - a.elem0[m] : 0;
-        }
-        __syncthreads();
+    // Every element of the CTA gets its mesh's slot in shared memory (past the last
+    // element: the first mesh's, so that per-slot settings, the same for all meshes
+    // of a launch, are read consistently by every thread).  Single-mesh and batch
+    // launches run this one code path, so they give the same bits.
+    if (sub_raw < EPB && ln == 0) {
+        const int m = (a.slots && live) ? ne_find_slot(a.elem0, a.nslots, ge) : 0;
+        sSlot[sub] = a.slots ? a.slots[m] : a.one;
+        sLoc[sub] = live ? (a.slots ? ge - a.elem0[m] : ge) : 0;
     }
-    const NeSlot &sl = BATCH ? sSlot[sub] : a.one;
-    const long long e = BATCH ? (live ? sLoc[sub] : 0) : ge;  // element index within its mesh
+    __syncthreads();
+    const NeSlot &sl = sSlot[sub];
+    const long long e = sLoc[sub];                              // element index within its mesh
     const long long gofs = ge - e;                              // launch index of the mesh's element 0
     float *const eb = ne_smem + SH::ELEM_FLOATS * sub;
     float *const sU = eb + SH::F_U;
@@ -540,7 +539,7 @@ __global__ void __launch_bounds__(NeShape<NP>::THREADS, 3) k_ne_stage(const __gr
         unsigned long long *cur = nullptr;
         float mx = 0.0f;
         for (int s0 = 0; s0 < EPB && e0 + s0 < a.nelem; ++s0) {
-            const NeSlot &m = BATCH ? sSlot[s0] : a.one;
+            const NeSlot &m = sSlot[s0];
             if (m.lam != cur) {
                 if (cur) atomicMax(cur, (unsigned long long)__double_as_longlong(ne_f32_to_f64(mx)));
                 cur = m.lam;
@@ -879,17 +878,17 @@ __global__ void __launch_bounds__(NeShape<NP>::THREADS, 3) k_ne_stage(const __gr
 // m_B slope (eq:MinModB).  Limited variables get the replacement parameters of
 // eq:MinModSol.  FINAL: the last pass of a step also writes U^{n+1} in place,
 // U^n + D3 where not limited, else the replacement, in FP64.
-template <int NP, int FINAL, int BATCH>
+template <int NP, int FINAL>
 __global__ void __launch_bounds__(128) k_ne_decide(const __grid_constant__ NeDecideArgs a)
 {
     constexpr int NN = NP * NP * NP;
     const int lane = threadIdx.x & 31, half = lane >> 4, h = lane & 15;
     const long long ge = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 4;
     const bool live = ge < a.nelem;
-    int slot = 0;
-    if (BATCH && live) slot = ne_find_slot(a.elem0, a.nslots, ge);
-    const NeDecideSlot &sl = BATCH ? a.slots[slot] : a.one;
-    const long long e = BATCH ? (live ? ge - a.elem0[slot] : 0) : ge;
+    // one code path for single-mesh and batch launches (the same bits either way)
+    const int slot = (a.slots && live) ? ne_find_slot(a.elem0, a.nslots, ge) : 0;
+    const NeDecideSlot &sl = a.slots ? a.slots[slot] : a.one;
+    const long long e = live ? (a.slots ? ge - a.elem0[slot] : ge) : 0;
     const double c = a.scale_dt ? (sl.dt_ptr ? *sl.dt_ptr : sl.dt) : 1.0;
     int flag = 0;
     double slope = 0.0, U0 = 0.0;
@@ -969,18 +968,12 @@ cudaError_t launch_ne_stage_np(int flux, int stage, const NeArgs &a, cudaStream_
     if (a.nelem <= 0) return cudaSuccess;
     const unsigned grid = (unsigned)((a.nelem + SH::EPB - 1) / SH::EPB);
     void (*kern)(const NeArgs) = nullptr;
-#define DG_NE_PICK(F, B)                                                                              \
-    kern = stage == 0 ? k_ne_stage<NP, F, 0, B> : stage == 1 ? k_ne_stage<NP, F, 1, B>                  \
-         : stage == 2 ? k_ne_stage<NP, F, 2, B> : k_ne_stage<NP, F, 3, B>
-    if (a.slots) {
-        if (flux == 0) DG_NE_PICK(0, 1);
-        else if (flux == 1) DG_NE_PICK(1, 1);
-        else DG_NE_PICK(2, 1);
-    } else {
-        if (flux == 0) DG_NE_PICK(0, 0);
-        else if (flux == 1) DG_NE_PICK(1, 0);
-        else DG_NE_PICK(2, 0);
-    }
+#define DG_NE_PICK(F)                                                                                 \
+    kern = stage == 0 ? k_ne_stage<NP, F, 0> : stage == 1 ? k_ne_stage<NP, F, 1>                        \
+         : stage == 2 ? k_ne_stage<NP, F, 2> : k_ne_stage<NP, F, 3>
+    if (flux == 0) DG_NE_PICK(0);
+    else if (flux == 1) DG_NE_PICK(1);
+    else DG_NE_PICK(2);
 #undef DG_NE_PICK
     if (SH::SMEM > 48 * 1024) {
         const cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SH::SMEM);
@@ -995,13 +988,8 @@ cudaError_t launch_ne_decide_np(int final_pass, const NeDecideArgs &a, cudaStrea
 {
     if (a.nelem <= 0) return cudaSuccess;
     const unsigned grid = (unsigned)((a.nelem + 7) / 8);  // 8 elements per 128-thread CTA
-    if (a.slots) {
-        if (final_pass) k_ne_decide<NP, 1, 1><<<grid, 128, 0, s>>>(a);
-        else k_ne_decide<NP, 0, 1><<<grid, 128, 0, s>>>(a);
-    } else {
-        if (final_pass) k_ne_decide<NP, 1, 0><<<grid, 128, 0, s>>>(a);
-        else k_ne_decide<NP, 0, 0><<<grid, 128, 0, s>>>(a);
-    }
+    if (final_pass) k_ne_decide<NP, 1><<<grid, 128, 0, s>>>(a);
+    else k_ne_decide<NP, 0><<<grid, 128, 0, s>>>(a);
     return cudaGetLastError();
 }
 
