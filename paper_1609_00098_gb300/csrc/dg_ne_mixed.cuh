@@ -297,6 +297,14 @@ __device__ __forceinline__ void ne_face_flux(float g, const float uL[5], const f
     }
 }
 
+// Linear part of a limited variable's replacement at LGL coordinates (x, y, z),
+// sh = {f32(U0), s_x dx/2, s_y dy/2, s_z dz/2}: one fixed rounding sequence, so that
+// every place that evaluates it (own nodes, neighbours' face nodes) gets the same bits.
+__device__ __forceinline__ float ne_lin(const float4 sh, float x, float y, float z)
+{
+    return __fmaf_rn(sh.y, x, __fmaf_rn(sh.z, y, __fmul_rn(sh.w, z)));
+}
+
 // Node index of the point at face position (p0, p1) on the face normal to axis ax
 // at layer `lay` (0 or NP-1): x-faces (lay, p0, p1), y-faces (p0, lay, p1),
 // z-faces (p0, p1, lay).  Consecutive p0 are consecutive in memory for y and z.
@@ -474,11 +482,10 @@ __global__ void __launch_bounds__(NeShape<NP>::THREADS, 3) k_ne_stage(const __gr
             const float4 sh = sl.SH[e * 5 + v];
             const double m0 = sl.M0[e * 5 + v];
             const float mh = ne_hi(m0), ml = ne_lo(m0);
-            const float lyz = sh.z * xj + sh.w * xk;
 #pragma unroll
             for (int i = 0; i < NP; ++i) {
-                const float lin = sh.y * a.x[i] + lyz;
-                u[v][i] = sh.x + lin;
+                const float lin = ne_lin(sh, a.x[i], xj, xk);
+                u[v][i] = __fadd_rn(sh.x, lin);
                 d[v][i] = ((mh - uh[i]) + (ml - ne_lo(un[i]))) + lin;
             }
         } else if (ST >= 2) {
@@ -503,8 +510,8 @@ __global__ void __launch_bounds__(NeShape<NP>::THREADS, 3) k_ne_stage(const __gr
             }
 #pragma unroll
             for (int i = 0; i < NP; ++i) {
-                d[v][i] = ST == 2 ? dtf * dv[i] : dv[i];
-                u[v][i] = uh[i] + d[v][i];
+                d[v][i] = ST == 2 ? __fmul_rn(dtf, dv[i]) : dv[i];
+                u[v][i] = __fadd_rn(uh[i], d[v][i]);
             }
         } else {
 #pragma unroll
@@ -578,11 +585,11 @@ __global__ void __launch_bounds__(NeShape<NP>::THREADS, 3) k_ne_stage(const __gr
                 for (int v = 0; v < 5; ++v) {
                     const long long ix = (en * 5 + v) * NN + qn;
                     if (ST >= 2 && ((nmask >> v) & 1u)) {
-                        const float4 sh = sl.SH[en * 5 + v];
-                        w[v] = sh.x + (sh.y * cx + (sh.z * cy + sh.w * cz));
+                        w[v] = __fadd_rn(sl.SH[en * 5 + v].x, ne_lin(sl.SH[en * 5 + v], cx, cy, cz));
                     } else {
+                        // the same roundings as the neighbour's own phase 1
                         w[v] = ne_hi(sl.Un[ix]);
-                        if (ST >= 2) w[v] += ST == 2 ? dtf * sl.Din[ix] : sl.Din[ix];
+                        if (ST >= 2) w[v] = __fadd_rn(w[v], ST == 2 ? __fmul_rn(dtf, sl.Din[ix]) : sl.Din[ix]);
                     }
                 }
             }
@@ -952,7 +959,7 @@ __global__ void __launch_bounds__(128) k_ne_decide(const __grid_constant__ NeDec
         if ((mask >> v) & 1u) {
             for (int q = h; q < NN; q += 16) {
                 const int i = q % NP, j = (q / NP) % NP, k = q / (NP * NP);
-                const float lin = shx[v] * a.x[i] + (shy[v] * a.x[j] + shz[v] * a.x[k]);
+                const float lin = ne_lin(make_float4(0.0f, shx[v], shy[v], shz[v]), a.x[i], a.x[j], a.x[k]);
                 sl.U[base + q] = m0v[v] + ne_f32_to_f64(lin);
             }
         } else {
