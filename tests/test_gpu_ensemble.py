@@ -108,9 +108,14 @@ def test_ensemble_rejects_bad_members(pkg):
         pkg.abi.dg_ensemble_create([mm.h, mm.h], [U, torch.zeros_like(U)])
 
 
-ORACLE_SPECS = [  # (system, K, n, flux, limiter, learned): both systems, extreme n, a K = 1 axis
-    (0, (3, 2, 2), 2, 0, 0, False),
-    (0, (2, 2, 1), 8, 1, 1, False),
+# (system, K, n, flux, limiter, learned): both systems, extreme n, a K = 1 axis.  The
+# self-periodic axis is on a member without the limiter: there the neighbours' means
+# are the element's own, MinModN's face test reduces to |U0 - face mean| <= 1e-8,
+# and on the smooth wave that gap is zero in exact arithmetic but FP32 rounding of
+# the mixed right-hand side at n = 7, 8 (~1e-7) exceeds it.
+ORACLE_SPECS = [
+    (0, (3, 2, 1), 2, 0, 0, False),
+    (0, (2, 2, 2), 8, 1, 1, False),
     (0, (3, 3, 2), 5, 1, 1, False),
     (1, (3, 2, 2), 3, 1, 1, False),
     (1, (2, 3, 2), 5, 1, 1, True),
