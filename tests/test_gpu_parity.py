@@ -289,7 +289,7 @@ def _full_size_ten_steps(pkg, kw, kind):
 
 def test_full_size_blast_ten_steps(pkg):
     """The SR blast at full size (16^3 elements, n = 5, HLL, MinModN)."""
-    _full_size_ten_steps(pkg, dict(system=1, K=(16, 16, 16), n=5, flux=1, limiter=1), "blast")
+    _full_size_ten_steps(pkg, dict(system=1, K=(16, 16, 16), n=5, flux=1, limiter=1, gamma=4.0 / 3.0), "blast")
 
 
 def test_full_size_con2prim_2p24(pkg):
