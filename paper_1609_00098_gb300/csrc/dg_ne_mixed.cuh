@@ -78,37 +78,39 @@ __device__ __forceinline__ double ne_f32_to_f64(float f)
 }
 
 // ---------------------------------------------------------------------------
-// Launch shape: elements per CTA (EPB) and threads per CTA for NP nodes per axis,
-// and the shared-memory layout of one element (floats, regions 16-byte aligned):
-//   U  stage state sU[5][NN]                    phase 1 .. face fluxes
-//   H  neighbour face traces sH[6][L][5]        halo staging .. face fluxes
-//   F  flux buffers sF[2][2][NN] (y, z; double-buffered over the variables)
-//   LF y/z face lifts sL[2][2][L][5]            face fluxes .. volume term
-// The S(U^n) reduction of stage 1 works in F + LF before the face fluxes, the
-// reduction of the output's summaries in U + H after them.
+// Launch shape: elements per CTA (EPB), threads per CTA and CTAs per SM the
+// registers are sized for, for NP nodes per axis, and the shared-memory layout of
+// one element (floats, regions 16-byte aligned):
+//   U   stage state sU[5][NN]                     phase 1 .. face fluxes
+//   HF  neighbour face traces sH[6][L][5]         halo staging .. face fluxes,
+//       then the flux buffers sF[2][2][NN] (y, z; double-buffered over the variables)
+//   LF  y/z face lifts sL[2][2][L][5]             face fluxes .. volume term
+// The S(U^n) reduction of stage 1 works in HF + LF before the halo staging, the
+// reduction of the output's summaries in U + HF after the volume term.
 template <int NP>
 struct NeShape {
     static constexpr int L = NP * NP;        // x-lines (threads) per element
     static constexpr int NN = NP * NP * NP;
-    static constexpr int EPB = NP == 2 ? 32 : NP == 3 ? 16 : NP == 4 ? 8 : NP == 5 ? 6 : NP == 6 ? 4 : NP == 7 ? 3 : 2;
+    static constexpr int EPB = NP == 2 ? 32 : NP == 3 ? 16 : NP == 4 ? 8 : NP == 5 ? 6 : NP == 6 ? 8 : NP == 7 ? 3 : 2;
     static constexpr int THREADS = (EPB * L + 31) / 32 * 32;
+    static constexpr int MINB = NP == 6 ? 2 : 3;
     static constexpr int R4(int v) { return (v + 3) / 4 * 4; }
     static constexpr int SN_NEED = 35 * L + 60 * NP;  // S(U^n): line partials, then per-(v, k) sums
     static constexpr int SD_NEED = 20 * L + 35 * NP;  // S(output): the same in FP32
+    static constexpr int HF = R4(30 * L > 4 * NN ? 30 * L : 4 * NN);
     static constexpr int F_U = 0;
     static constexpr int F_H = R4(5 * NN);
-    static constexpr int F_F = F_H + R4(30 * L);
-    static constexpr int F_L0 = F_F + R4(4 * NN);
-    static constexpr int F_L = F_L0 + (SN_NEED > F_L0 - F_F + 20 * L ? R4(SN_NEED - (F_L0 - F_F + 20 * L)) : 0);
+    static constexpr int F_F = F_H;
+    static constexpr int F_L = F_H + HF + (SN_NEED > HF + 20 * L ? R4(SN_NEED - (HF + 20 * L)) : 0);
     static constexpr int ELEM_FLOATS = F_L + R4(20 * L);
-    static_assert(SD_NEED <= F_F, "output-summary scratch must fit in U + H");
+    static_assert(SD_NEED <= F_L, "output-summary scratch must fit in U + HF");
     static constexpr size_t SMEM = sizeof(float) * (size_t)ELEM_FLOATS * EPB;
 };
 
 // Elements per CTA of k_ne_stage for n nodes per axis (NeShape<n>::EPB).
 inline int ne_epb(int n)
 {
-    return n == 2 ? 32 : n == 3 ? 16 : n == 4 ? 8 : n == 5 ? 6 : n == 6 ? 4 : n == 7 ? 3 : 2;
+    return n == 2 ? 32 : n == 3 ? 16 : n == 4 ? 8 : n == 5 ? 6 : n == 6 ? 8 : n == 7 ? 3 : 2;
 }
 
 // Error-free FP32 steps for the double-float sums of S(U^n): s + e = a + b exactly
@@ -367,7 +369,7 @@ __device__ __forceinline__ float ne_final_sum(const NeArgs &a, int kind, Q q)
 // -(2/dx_a)(F* - F_L)/w_N, the upper +(2/dx_a)(F* - F_R)/w_0); eq:LLF, eq:HLL,
 // eq:Roe; Sec. 3.4 (SSP-RK3 in the difference form above, CFL maximum).
 template <int NP, int FLX, int ST>
-__global__ void __launch_bounds__(NeShape<NP>::THREADS, 3) k_ne_stage(const __grid_constant__ NeArgs a)
+__global__ void __launch_bounds__(NeShape<NP>::THREADS, NeShape<NP>::MINB) k_ne_stage(const __grid_constant__ NeArgs a)
 {
     using SH = NeShape<NP>;
     constexpr int L = SH::L, NN = SH::NN, EPB = SH::EPB, N1 = NP - 1;
@@ -375,6 +377,7 @@ __global__ void __launch_bounds__(NeShape<NP>::THREADS, 3) k_ne_stage(const __gr
     __shared__ long long sNb[EPB][6];
     __shared__ unsigned sMask[EPB][7];  // own (0) and neighbours' (1 + 2 ax + side) limited variables
     __shared__ unsigned sLamE[EPB];  // per element: max wave speed (bits of a non-negative float)
+    __shared__ float4 sNbSH[EPB][6][5];  // the neighbours' replacement parameters (limited variables)
     __shared__ NeSlot sSlot[EPB];
     __shared__ long long sLoc[EPB];
 
@@ -420,6 +423,13 @@ __global__ void __launch_bounds__(NeShape<NP>::THREADS, 3) k_ne_stage(const __gr
     }
     __syncthreads();
     const unsigned mask = live ? sMask[sub][0] : 0u;
+    // the neighbours' replacement parameters, once per element (read in the halo
+    // staging, after the next barrier)
+    for (int q = ln; lim_in && live && q < 30; q += L) {
+        const int m = q / 5, v = q % 5;
+        const long long en = sNb[sub][m];
+        if (en >= 0 && ((sMask[sub][1 + m] >> v) & 1u)) sNbSH[sub][m][v] = sl.SH[en * 5 + v];
+    }
 
     // ---- phase 1: the stage state of the thread's line: FP32 values for the
     // right-hand side (sU), the accurate difference d = U^s - U^n for the update;
@@ -557,47 +567,6 @@ __global__ void __launch_bounds__(NeShape<NP>::THREADS, 3) k_ne_stage(const __gr
         if (cur) atomicMax(cur, (unsigned long long)__double_as_longlong(ne_f32_to_f64(mx)));
     }
 
-    // ---- halo staging: the neighbours' traces at this thread's six face points,
-    // from shared memory (elements of this CTA), a ghost's exterior state, or
-    // global memory (U^n + D, or a limited variable's replacement)
-    if (live) {
-#pragma unroll
-        for (int m = 0; m < 6; ++m) {
-            const int ax = m >> 1, side = m & 1, layn = side ? 0 : N1;
-            const int qn = ne_face_node<NP>(ax, layn, j, k);
-            const long long en = sNb[sub][m];
-            const long long sn = en + gofs - e0;
-            float w[5];
-            if (en >= 0 && sn >= 0 && sn < EPB && en + gofs < a.nelem) {
-                const float *nU = ne_smem + SH::ELEM_FLOATS * sn + SH::F_U;
-#pragma unroll
-                for (int v = 0; v < 5; ++v) w[v] = nU[v * NN + qn];
-            } else if (en < 0) {
-#pragma unroll
-                for (int v = 0; v < 5; ++v) w[v] = ne_hi(sl.gh.U[((-1 - en) * 5 + v) * NN + qn]);
-            } else {
-                const unsigned nmask = sMask[sub][1 + m];
-                // the face node's (x, y, z) LGL coordinates in the neighbour
-                const float cx = ax == 0 ? a.x[layn] : xj;
-                const float cy = ax == 0 ? xj : ax == 1 ? a.x[layn] : xk;
-                const float cz = ax == 2 ? a.x[layn] : xk;
-#pragma unroll
-                for (int v = 0; v < 5; ++v) {
-                    const long long ix = (en * 5 + v) * NN + qn;
-                    if (ST >= 2 && ((nmask >> v) & 1u)) {
-                        w[v] = __fadd_rn(sl.SH[en * 5 + v].x, ne_lin(sl.SH[en * 5 + v], cx, cy, cz));
-                    } else {
-                        // the same roundings as the neighbour's own phase 1
-                        w[v] = ne_hi(sl.Un[ix]);
-                        if (ST >= 2) w[v] = __fadd_rn(w[v], ST == 2 ? __fmul_rn(dtf, sl.Din[ix]) : sl.Din[ix]);
-                    }
-                }
-            }
-#pragma unroll
-            for (int v = 0; v < 5; ++v) sH[(m * L + ln) * 5 + v] = w[v];
-        }
-    }
-
     // ---- S(U^n) (stage 1 with a limiter), second pass: per (v, k) sums over j
     float *const sQn = sF + 35 * L;  // [5][NP][12]
     if (do_sn) {
@@ -628,8 +597,8 @@ __global__ void __launch_bounds__(NeShape<NP>::THREADS, 3) k_ne_stage(const __gr
             Q[10] = a1;
             Q[11] = a4;
         }
+        __syncthreads();
     }
-    __syncthreads();
     // third pass: the 50 summaries, the reference c added in FP64 (mean and face
     // means of a constant are the constant, its P1 coefficient is zero)
     if (do_sn) {
@@ -660,8 +629,52 @@ __global__ void __launch_bounds__(NeShape<NP>::THREADS, 3) k_ne_stage(const __gr
             const double cv = ne_f32_to_f64(ne_hi(sl.Un[(e * 5 + v) * NN]));
             sl.SN[e * 50 + o] = (kind <= 6 ? cv : 0.0) + (ne_f32_to_f64(h) + ne_f32_to_f64(l));
         }
-        __syncthreads();  // the scratch overlaps the face-lift array
+        __syncthreads();  // the scratch overlaps the halo and face-lift arrays
     }
+
+    // ---- halo staging: the neighbours' traces at this thread's six face points,
+    // from shared memory (elements of this CTA), a ghost's exterior state, or
+    // global memory (U^n + D, or a limited variable's replacement)
+    if (live) {
+#pragma unroll
+        for (int m = 0; m < 6; ++m) {
+            const int ax = m >> 1, side = m & 1, layn = side ? 0 : N1;
+            const int qn = ne_face_node<NP>(ax, layn, j, k);
+            const long long en = sNb[sub][m];
+            const long long sn = en + gofs - e0;
+            float w[5];
+            if (en >= 0 && sn >= 0 && sn < EPB && en + gofs < a.nelem) {
+                const float *nU = ne_smem + SH::ELEM_FLOATS * sn + SH::F_U;
+#pragma unroll
+                for (int v = 0; v < 5; ++v) w[v] = nU[v * NN + qn];
+            } else if (en < 0) {
+#pragma unroll
+                for (int v = 0; v < 5; ++v) w[v] = ne_hi(sl.gh.U[((-1 - en) * 5 + v) * NN + qn]);
+            } else {
+                const unsigned nmask = sMask[sub][1 + m];
+                // the face node's (x, y, z) LGL coordinates in the neighbour
+                const float cx = ax == 0 ? a.x[layn] : xj;
+                const float cy = ax == 0 ? xj : ax == 1 ? a.x[layn] : xk;
+                const float cz = ax == 2 ? a.x[layn] : xk;
+#pragma unroll
+                for (int v = 0; v < 5; ++v) {
+                    const long long ix = (en * 5 + v) * NN + qn;
+                    if (ST >= 2 && ((nmask >> v) & 1u)) {
+                        const float4 sh = sNbSH[sub][m][v];
+                        w[v] = __fadd_rn(sh.x, ne_lin(sh, cx, cy, cz));
+                    } else {
+                        // the same roundings as the neighbour's own phase 1
+                        w[v] = ne_hi(sl.Un[ix]);
+                        if (ST >= 2) w[v] = __fadd_rn(w[v], ST == 2 ? __fmul_rn(dtf, sl.Din[ix]) : sl.Din[ix]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < 5; ++v) sH[(m * L + ln) * 5 + v] = w[v];
+        }
+    }
+
+    __syncthreads();
 
     // ---- face fluxes at the thread's six face points.  x-face lifts belong to the
     // thread's own line and stay in registers; y and z lifts go to sL for the lines
@@ -842,6 +855,7 @@ __global__ void __launch_bounds__(NeShape<NP>::THREADS, 3) k_ne_stage(const __gr
     // volume term's barriers), per-(v, k) sums, then the 50 values
     float *const sP = eb + SH::F_U;          // [5][4][L]
     float *const sQ = eb + SH::F_U + 20 * L;  // [5][NP][7]
+    if (20 * L > SH::F_H) __syncthreads();     // (small n: the partials reach the flux buffers)
     if (live)
 #pragma unroll
         for (int v = 0; v < 5; ++v)
@@ -889,6 +903,11 @@ template <int NP, int FINAL>
 __global__ void __launch_bounds__(128) k_ne_decide(const __grid_constant__ NeDecideArgs a)
 {
     constexpr int NN = NP * NP * NP;
+    __shared__ float sx[MAXN];  // LGL nodes, for the final pass's per-lane coordinates
+    if (FINAL) {
+        if (threadIdx.x < MAXN) sx[threadIdx.x] = a.x[threadIdx.x];
+        __syncthreads();
+    }
     const int lane = threadIdx.x & 31, half = lane >> 4, h = lane & 15;
     const long long ge = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 4;
     const bool live = ge < a.nelem;
@@ -941,7 +960,7 @@ __global__ void __launch_bounds__(128) k_ne_decide(const __grid_constant__ NeDec
         sl.troubled[e] = 0;
     }
     if (!FINAL) return;
-    // U^{n+1} of this element, 16 lanes: U^n + D3, or the replacement
+    // U^{n+1} of this element, 16 lanes, x-line by x-line: U^n + D3, or the replacement
     __syncwarp();
     float shx[5], shy[5], shz[5];
     double m0v[5];
@@ -953,17 +972,28 @@ __global__ void __launch_bounds__(128) k_ne_decide(const __grid_constant__ NeDec
         shz[v] = __shfl_sync(0xffffffffu, s2v, 16 * half + 3 * v);
     }
     if (!live) return;
+    for (int ln = h; ln < NP * NP; ln += 16) {
+        const float xj = sx[ln % NP], xk = sx[ln / NP];
 #pragma unroll
-    for (int v = 0; v < 5; ++v) {
-        const long long base = (e * 5 + v) * NN;
-        if ((mask >> v) & 1u) {
-            for (int q = h; q < NN; q += 16) {
-                const int i = q % NP, j = (q / NP) % NP, k = q / (NP * NP);
-                const float lin = ne_lin(make_float4(0.0f, shx[v], shy[v], shz[v]), a.x[i], a.x[j], a.x[k]);
-                sl.U[base + q] = m0v[v] + ne_f32_to_f64(lin);
+        for (int v = 0; v < 5; ++v) {
+            const long long base = (e * 5 + v) * NN + (long long)ln * NP;
+            double val[NP];
+            if ((mask >> v) & 1u) {
+                const float4 sh = make_float4(0.0f, shx[v], shy[v], shz[v]);
+#pragma unroll
+                for (int i = 0; i < NP; ++i) val[i] = m0v[v] + ne_f32_to_f64(ne_lin(sh, a.x[i], xj, xk));
+            } else {
+#pragma unroll
+                for (int i = 0; i < NP; ++i) val[i] = sl.U[base + i] + ne_f32_to_f64(sl.D3[base + i]);
             }
-        } else {
-            for (int q = h; q < NN; q += 16) sl.U[base + q] = sl.U[base + q] + ne_f32_to_f64(sl.D3[base + q]);
+            if (NP % 2 == 0) {
+                double2 *p2 = reinterpret_cast<double2 *>(sl.U + base);
+#pragma unroll
+                for (int q = 0; q < NP / 2; ++q) p2[q] = make_double2(val[2 * q], val[2 * q + 1]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < NP; ++i) sl.U[base + i] = val[i];
+            }
         }
     }
 }
