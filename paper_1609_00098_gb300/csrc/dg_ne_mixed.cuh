@@ -1012,10 +1012,9 @@ cudaError_t launch_ne_stage_np(int flux, int stage, const NeArgs &a, cudaStream_
     else if (flux == 1) DG_NE_PICK(1);
     else DG_NE_PICK(2);
 #undef DG_NE_PICK
-    if (SH::SMEM > 48 * 1024) {
-        const cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SH::SMEM);
-        if (err != cudaSuccess) return err;
-    }
+    // static + dynamic shared memory exceed 48 KB for every n: opt in
+    const cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SH::SMEM);
+    if (err != cudaSuccess) return err;
     kern<<<grid, SH::THREADS, SH::SMEM, s>>>(a);
     return cudaGetLastError();
 }
