@@ -437,9 +437,9 @@ __global__ void __launch_bounds__(NeShape<NP>::THREADS, NeShape<NP>::MINB) k_ne_
     // node-0 value rounded to FP32), as double-float pairs where the limiter's
     // tests need them (L0 and the end values), FP32 for L1
     float d[5][NP];
-    float u[5][NP];
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
+        float uv[NP];
         const long long base = (e * 5 + v) * NN + (long long)ln * NP;
         double un[NP];
         if (live) {
@@ -495,7 +495,7 @@ __global__ void __launch_bounds__(NeShape<NP>::THREADS, NeShape<NP>::MINB) k_ne_
 #pragma unroll
             for (int i = 0; i < NP; ++i) {
                 const float lin = ne_lin(sh, a.x[i], xj, xk);
-                u[v][i] = __fadd_rn(sh.x, lin);
+                uv[i] = __fadd_rn(sh.x, lin);
                 d[v][i] = ((mh - uh[i]) + (ml - ne_lo(un[i]))) + lin;
             }
         } else if (ST >= 2) {
@@ -521,18 +521,18 @@ __global__ void __launch_bounds__(NeShape<NP>::THREADS, NeShape<NP>::MINB) k_ne_
 #pragma unroll
             for (int i = 0; i < NP; ++i) {
                 d[v][i] = ST == 2 ? __fmul_rn(dtf, dv[i]) : dv[i];
-                u[v][i] = __fadd_rn(uh[i], d[v][i]);
+                uv[i] = __fadd_rn(uh[i], d[v][i]);
             }
         } else {
 #pragma unroll
             for (int i = 0; i < NP; ++i) {
                 d[v][i] = 0.0f;
-                u[v][i] = uh[i];
+                uv[i] = uh[i];
             }
         }
         if (live)
 #pragma unroll
-            for (int i = 0; i < NP; ++i) sU[v * NN + ln * NP + i] = u[v][i];
+            for (int i = 0; i < NP; ++i) sU[v * NN + ln * NP + i] = uv[i];
     }
 
     // CFL maximum of U^n (stage 1): max over nodes and axes of |v_a| + c, per
@@ -543,7 +543,7 @@ __global__ void __launch_bounds__(NeShape<NP>::THREADS, NeShape<NP>::MINB) k_ne_
         for (int i = 0; i < NP; ++i) {
             float w[5];
 #pragma unroll
-            for (int v = 0; v < 5; ++v) w[v] = u[v][i];
+            for (int v = 0; v < 5; ++v) w[v] = sU[v * NN + ln * NP + i];
             float vx, vy, vz, p;
             ne_prims(a.gamma, w, vx, vy, vz, p);
             const float c = sqrtf(a.gamma * p / w[0]);
@@ -725,38 +725,41 @@ __global__ void __launch_bounds__(NeShape<NP>::THREADS, NeShape<NP>::MINB) k_ne_
     // flux (D annihilates constants, so the FP32 rounding scales with the flux
     // variation inside the element), the x derivative in registers, the y and z
     // derivatives through shared memory (sF double-buffered over v)
+    // (the state of the thread's own line and the element's node 0 come from sU;
+    // from iteration v on, variable v's part of sU holds the summary partials)
+    constexpr bool PART_IN_U = 4 * L <= NN;
     float vx[NP], vy[NP], vz[NP], pr[NP];
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
         float w[5];
 #pragma unroll
-        for (int v = 0; v < 5; ++v) w[v] = u[v][i];
+        for (int v = 0; v < 5; ++v) w[v] = sU[v * NN + ln * NP + i];
         ne_prims(a.gamma, w, vx[i], vy[i], vz[i], pr[i]);
     }
-    float vx0, vy0, vz0, pr0;
-    {
-        float w[5];
+    float vx0, vy0, vz0, pr0, u0[5];
 #pragma unroll
-        for (int v = 0; v < 5; ++v) w[v] = sU[v * NN];
-        ne_prims(a.gamma, w, vx0, vy0, vz0, pr0);
-    }
+    for (int v = 0; v < 5; ++v) u0[v] = sU[v * NN];
+    ne_prims(a.gamma, u0, vx0, vy0, vz0, pr0);
     float Dj[NP], Dk[NP];
 #pragma unroll
     for (int l = 0; l < NP; ++l) {
         Dj[l] = a.D[j * NP + l];
         Dk[l] = a.D[k * NP + l];
     }
-    float part[5][4];
+    float part[PART_IN_U ? 1 : 5][4];
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
         float *bF = sF + (v & 1) * 2 * NN;
         float rx, ry, rz;
-        ne_flux3v(v, sU[v * NN], vx0, vy0, vz0, pr0, rx, ry, rz);
+        ne_flux3v(v, u0[v], vx0, vy0, vz0, pr0, rx, ry, rz);
+        float uv[NP];
+#pragma unroll
+        for (int i = 0; i < NP; ++i) uv[i] = sU[v * NN + ln * NP + i];
         float fx[NP];
 #pragma unroll
         for (int i = 0; i < NP; ++i) {
             float f0, f1, f2;
-            ne_flux3v(v, u[v][i], vx[i], vy[i], vz[i], pr[i], f0, f1, f2);
+            ne_flux3v(v, uv[i], vx[i], vy[i], vz[i], pr[i], f0, f1, f2);
             fx[i] = f0 - rx;
             if (live) {
                 bF[ln * NP + i] = f1 - ry;
@@ -842,10 +845,19 @@ __global__ void __launch_bounds__(NeShape<NP>::THREADS, NeShape<NP>::MINB) k_ne_
                     l0 = fmaf(a.w[i], X[i], l0);
                     l1 = fmaf(a.row1[i], X[i], l1);
                 }
-                part[v][0] = l0;
-                part[v][1] = l1;
-                part[v][2] = X[0];
-                part[v][3] = X[N1];
+                if (PART_IN_U) {
+                    // variable v's stage state is no longer read (after this iteration's barrier)
+                    float *P = sU + v * NN + ln;
+                    P[0] = l0;
+                    P[L] = l1;
+                    P[2 * L] = X[0];
+                    P[3 * L] = X[N1];
+                } else {
+                    part[PART_IN_U ? 0 : v][0] = l0;
+                    part[PART_IN_U ? 0 : v][1] = l1;
+                    part[PART_IN_U ? 0 : v][2] = X[0];
+                    part[PART_IN_U ? 0 : v][3] = X[N1];
+                }
             }
         }
     }
@@ -853,18 +865,22 @@ __global__ void __launch_bounds__(NeShape<NP>::THREADS, NeShape<NP>::MINB) k_ne_
 
     // ---- summaries S(Dout) in FP32: line partials (to U + H, last read before the
     // volume term's barriers), per-(v, k) sums, then the 50 values
-    float *const sP = eb + SH::F_U;          // [5][4][L]
-    float *const sQ = eb + SH::F_U + 20 * L;  // [5][NP][7]
-    if (20 * L > SH::F_H) __syncthreads();     // (small n: the partials reach the flux buffers)
-    if (live)
+    // partials of variable v at sU + v * NN (PART_IN_U), else [5][4][L] from U on
+    float *const sP = eb + SH::F_U;
+    constexpr int PSTR = PART_IN_U ? NN : 4 * L;
+    float *const sQ = PART_IN_U ? sF : sL;    // [5][NP][7]; sF and sL are dead by now
+    if (!PART_IN_U) {
+        __syncthreads();  // (small n: the partials reach the flux buffers)
+        if (live)
 #pragma unroll
-        for (int v = 0; v < 5; ++v)
+            for (int v = 0; v < 5; ++v)
 #pragma unroll
-            for (int q = 0; q < 4; ++q) sP[(v * 4 + q) * L + ln] = part[v][q];
+                for (int q = 0; q < 4; ++q) sP[(v * 4 + q) * L + ln] = part[PART_IN_U ? 0 : v][q];
+    }
     __syncthreads();
     for (int r = ln; live && r < 5 * NP; r += L) {
         const int v = r / NP, kk = r % NP;
-        const float *P = sP + v * 4 * L + NP * kk;
+        const float *P = sP + v * PSTR + NP * kk;
         float a0 = 0.0f, a1 = 0.0f, ax0 = 0.0f, axn = 0.0f, a4 = 0.0f;
 #pragma unroll
         for (int jj = 0; jj < NP; ++jj) {
