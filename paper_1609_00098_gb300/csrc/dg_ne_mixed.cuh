@@ -91,7 +91,7 @@ template <int NP>
 struct NeShape {
     static constexpr int L = NP * NP;        // x-lines (threads) per element
     static constexpr int NN = NP * NP * NP;
-    static constexpr int EPB = NP == 2 ? 32 : NP == 3 ? 16 : NP == 4 ? 8 : NP == 5 ? 6 : NP == 6 ? 8 : NP == 7 ? 3 : 2;
+    static constexpr int EPB = NP == 2 ? 32 : NP == 3 ? 16 : NP == 4 ? 8 : NP == 5 ? 6 : NP == 6 ? 7 : NP == 7 ? 3 : 2;
     static constexpr int THREADS = (EPB * L + 31) / 32 * 32;
     static constexpr int MINB = NP == 6 ? 2 : 3;
     static constexpr int R4(int v) { return (v + 3) / 4 * 4; }
@@ -110,7 +110,7 @@ struct NeShape {
 // Elements per CTA of k_ne_stage for n nodes per axis (NeShape<n>::EPB).
 inline int ne_epb(int n)
 {
-    return n == 2 ? 32 : n == 3 ? 16 : n == 4 ? 8 : n == 5 ? 6 : n == 6 ? 8 : n == 7 ? 3 : 2;
+    return n == 2 ? 32 : n == 3 ? 16 : n == 4 ? 8 : n == 5 ? 6 : n == 6 ? 7 : n == 7 ? 3 : 2;
 }
 
 // Error-free FP32 steps for the double-float sums of S(U^n): s + e = a + b exactly
