@@ -299,6 +299,36 @@ __device__ __forceinline__ void ne_face_flux(float g, const float uL[5], const f
     }
 }
 
+// One x-line (NP floats, 8-byte aligned for even NP) to / from shared memory: 64-bit
+// accesses for even NP, whose 24-byte line stride is free of bank conflicts.
+template <int NP>
+__device__ __forceinline__ void ne_st_line(float *p, const float v[NP])
+{
+    if (NP % 2 == 0) {
+#pragma unroll
+        for (int h = 0; h < NP / 2; ++h) reinterpret_cast<float2 *>(p)[h] = make_float2(v[2 * h], v[2 * h + 1]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < NP; ++i) p[i] = v[i];
+    }
+}
+
+template <int NP>
+__device__ __forceinline__ void ne_ld_line(const float *p, float v[NP])
+{
+    if (NP % 2 == 0) {
+#pragma unroll
+        for (int h = 0; h < NP / 2; ++h) {
+            const float2 q = reinterpret_cast<const float2 *>(p)[h];
+            v[2 * h] = q.x;
+            v[2 * h + 1] = q.y;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < NP; ++i) v[i] = p[i];
+    }
+}
+
 // Linear part of a limited variable's replacement at LGL coordinates (x, y, z),
 // sh = {f32(U0), s_x dx/2, s_y dy/2, s_z dz/2}: one fixed rounding sequence, so that
 // every place that evaluates it (own nodes, neighbours' face nodes) gets the same bits.
@@ -460,8 +490,9 @@ __global__ void __launch_bounds__(NeShape<NP>::THREADS, NeShape<NP>::MINB) k_ne_
             for (int i = 0; i < NP; ++i) un[i] = v == 0 ? 1.0 : (v == 4 ? 2.5 : 0.0);
         }
         float uh[NP];
+        if (!(ST >= 2 && ((mask >> v) & 1u)))
 #pragma unroll
-        for (int i = 0; i < NP; ++i) uh[i] = ne_hi(un[i]);
+            for (int i = 0; i < NP; ++i) uh[i] = ne_hi(un[i]);
         if (do_sn) {
             const float c = live ? ne_hi(sl.Un[(e * 5 + v) * NN]) : 0.0f;
             float ah[NP], al[NP];
@@ -489,14 +520,15 @@ __global__ void __launch_bounds__(NeShape<NP>::THREADS, NeShape<NP>::MINB) k_ne_
             }
         }
         if (ST >= 2 && ((mask >> v) & 1u)) {
+            // replaced: U^s = U0 + lin, so d = (U0 - U^n) + lin with U0 - U^n in FP64
+            // (the FP64 pipe is otherwise idle here), rounded once to FP32
             const float4 sh = sl.SH[e * 5 + v];
             const double m0 = sl.M0[e * 5 + v];
-            const float mh = ne_hi(m0), ml = ne_lo(m0);
 #pragma unroll
             for (int i = 0; i < NP; ++i) {
                 const float lin = ne_lin(sh, a.x[i], xj, xk);
                 uv[i] = __fadd_rn(sh.x, lin);
-                d[v][i] = ((mh - uh[i]) + (ml - ne_lo(un[i]))) + lin;
+                d[v][i] = __fadd_rn(ne_hi(m0 - un[i]), lin);
             }
         } else if (ST >= 2) {
             float dv[NP];
@@ -530,9 +562,7 @@ __global__ void __launch_bounds__(NeShape<NP>::THREADS, NeShape<NP>::MINB) k_ne_
                 uv[i] = uh[i];
             }
         }
-        if (live)
-#pragma unroll
-            for (int i = 0; i < NP; ++i) sU[v * NN + ln * NP + i] = uv[i];
+        if (live) ne_st_line<NP>(sU + v * NN + ln * NP, uv);
     }
 
     // CFL maximum of U^n (stage 1): max over nodes and axes of |v_a| + c, per
@@ -729,12 +759,17 @@ __global__ void __launch_bounds__(NeShape<NP>::THREADS, NeShape<NP>::MINB) k_ne_
     // from iteration v on, variable v's part of sU holds the summary partials)
     constexpr bool PART_IN_U = 4 * L <= NN;
     float vx[NP], vy[NP], vz[NP], pr[NP];
+    {
+        float ul[5][NP];
 #pragma unroll
-    for (int i = 0; i < NP; ++i) {
-        float w[5];
+        for (int v = 0; v < 5; ++v) ne_ld_line<NP>(sU + v * NN + ln * NP, ul[v]);
 #pragma unroll
-        for (int v = 0; v < 5; ++v) w[v] = sU[v * NN + ln * NP + i];
-        ne_prims(a.gamma, w, vx[i], vy[i], vz[i], pr[i]);
+        for (int i = 0; i < NP; ++i) {
+            float w[5];
+#pragma unroll
+            for (int v = 0; v < 5; ++v) w[v] = ul[v][i];
+            ne_prims(a.gamma, w, vx[i], vy[i], vz[i], pr[i]);
+        }
     }
     float vx0, vy0, vz0, pr0, u0[5];
 #pragma unroll
@@ -753,18 +788,19 @@ __global__ void __launch_bounds__(NeShape<NP>::THREADS, NeShape<NP>::MINB) k_ne_
         float rx, ry, rz;
         ne_flux3v(v, u0[v], vx0, vy0, vz0, pr0, rx, ry, rz);
         float uv[NP];
-#pragma unroll
-        for (int i = 0; i < NP; ++i) uv[i] = sU[v * NN + ln * NP + i];
-        float fx[NP];
+        ne_ld_line<NP>(sU + v * NN + ln * NP, uv);
+        float fx[NP], fy[NP], fz[NP];
 #pragma unroll
         for (int i = 0; i < NP; ++i) {
             float f0, f1, f2;
             ne_flux3v(v, uv[i], vx[i], vy[i], vz[i], pr[i], f0, f1, f2);
             fx[i] = f0 - rx;
-            if (live) {
-                bF[ln * NP + i] = f1 - ry;
-                bF[NN + ln * NP + i] = f2 - rz;
-            }
+            fy[i] = f1 - ry;
+            fz[i] = f2 - rz;
+        }
+        if (live) {
+            ne_st_line<NP>(bF + ln * NP, fy);
+            ne_st_line<NP>(bF + NN + ln * NP, fz);
         }
         float R[NP];
 #pragma unroll
@@ -781,30 +817,13 @@ __global__ void __launch_bounds__(NeShape<NP>::THREADS, NeShape<NP>::MINB) k_ne_
             for (int i = 0; i < NP; ++i) sy[i] = sz[i] = 0.0f;
 #pragma unroll
             for (int l = 0; l < NP; ++l) {
-                const float *Fy = bF + NP * (l + NP * k);       // F^y(., l, k)
-                const float *Fz = bF + NN + NP * (j + NP * l);  // F^z(., j, l)
-                float fy[NP], fz[NP];
-                if (NP % 2 == 0) {
-#pragma unroll
-                    for (int h = 0; h < NP / 2; ++h) {
-                        const float2 qy = reinterpret_cast<const float2 *>(Fy)[h];
-                        const float2 qz = reinterpret_cast<const float2 *>(Fz)[h];
-                        fy[2 * h] = qy.x;
-                        fy[2 * h + 1] = qy.y;
-                        fz[2 * h] = qz.x;
-                        fz[2 * h + 1] = qz.y;
-                    }
-                } else {
-#pragma unroll
-                    for (int i = 0; i < NP; ++i) {
-                        fy[i] = Fy[i];
-                        fz[i] = Fz[i];
-                    }
-                }
+                float gy[NP], gz[NP];
+                ne_ld_line<NP>(bF + NP * (l + NP * k), gy);       // F^y(., l, k)
+                ne_ld_line<NP>(bF + NN + NP * (j + NP * l), gz);  // F^z(., j, l)
 #pragma unroll
                 for (int i = 0; i < NP; ++i) {
-                    sy[i] = fmaf(Dj[l], fy[i], sy[i]);
-                    sz[i] = fmaf(Dk[l], fz[i], sz[i]);
+                    sy[i] = fmaf(Dj[l], gy[i], sy[i]);
+                    sz[i] = fmaf(Dk[l], gz[i], sz[i]);
                 }
             }
 #pragma unroll
