@@ -63,11 +63,12 @@ def _mesh_kw(w, **extra):
 
 def _config(extra=None):
     w = KH
-    cfg = {"workload": "Newtonian Kelvin-Helmholtz shear layer, 64^3 elements, 6 LGL nodes/axis (56.6M nodes), "
-                       "gamma 5/3, HLL, MinModN, CFL 0.2",
-           "system": "Newtonian Euler", "elements": list(w["K"]), "lgl_nodes_per_axis": w["n"], "nodes": _nodes(w),
+    k, nodes = w["K"][0], _nodes(w)
+    cfg = {"workload": "Newtonian Kelvin-Helmholtz shear layer, %d^3 elements, %d LGL nodes/axis (%.1fM nodes), "
+                       "gamma 5/3, HLL, MinModN, CFL 0.2" % (k, w["n"], nodes / 1e6),
+           "system": "Newtonian Euler", "elements": list(w["K"]), "lgl_nodes_per_axis": w["n"], "nodes": nodes,
            "vars": 5, "flux": "HLL", "limiter": "MinModN", "cfl": w["cfl"], "seed": w["seed"],
-           "l2_between_steps": "inputs larger than L2 (state 2.26 GB per copy; no flush)"}
+           "l2_between_steps": "inputs larger than L2 (state %.2f GB per copy; no flush)" % (nodes * 40 / 1e9)}
     if extra:
         cfg.update(extra)
     return cfg
@@ -371,6 +372,82 @@ def _con2prim_bench(pkg, torch, reps=3):
             "max_rel_diff_pressure": rel}
 
 
+# Arithmetic of one k_stage_mixed launch on the relativistic blast with the learned
+# guess, mean over the three stages of a step, from one ncu capture of three
+# launches: FP64 flops = 2 DFMA + DADD + DMUL, FP32 flops = 2 FFMA + FADD + FMUL
+# (+ twice that for the paired FFMA2 / FADD2 / FMUL2), SASS thread instructions
+# with all predicates true.  Reported only while the kernel's sources hash to
+# their state at capture.
+SR_STAGE_FLOPS = None
+SR_STAGE_SOURCES = ("paper_1609_00098_gb300/csrc/dg_mixed.cuh", "paper_1609_00098_gb300/csrc/dg_physics.cuh",
+                    "paper_1609_00098_gb300/csrc/dg_c2p_net.cuh", "paper_1609_00098_gb300/csrc/dg_internal.h",
+                    "paper_1609_00098_gb300/csrc/dg_api.cu")
+SR_STAGE_SOURCES_SHA256 = ""
+# FMA throughput of this GPU (independent dependent-FMA chains, every SM busy;
+# flops count an FMA as two): FP64 1.20 TFLOP/s, FP32 75.0 TFLOP/s.
+FP64_PEAK_TFLOPS = 1.20
+FP32_PEAK_TFLOPS = 75.0
+
+
+def _sources_match(files, digest):
+    import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest() == digest
+
+
+def _alu_roofline(avg_launch_ms):
+    """FP64- and FP32-pipe roofline of the SR stage kernel: the captured flops of
+    one launch over the live CUDA-event launch time, against the FMA peaks."""
+    out = {"kernel": "k_stage_mixed<5, SR, HLL, learned guess>", "bound": "alu", "unit": "TFLOP/s",
+           "avg_launch_ms": avg_launch_ms, "peak_fp64": FP64_PEAK_TFLOPS, "peak_fp32": FP32_PEAK_TFLOPS,
+           "peak_source": "FMA-chain micro-benchmark on this GPU (measured)",
+           "timing": "CUDA events captured in the timed graph replays"}
+    if SR_STAGE_FLOPS is None or not _sources_match(SR_STAGE_SOURCES, SR_STAGE_SOURCES_SHA256):
+        out.update({"achieved": None, "peak": FP64_PEAK_TFLOPS, "frac": None,
+                    "note": "no flop count captured for the current kernel sources"})
+        return out
+    s = avg_launch_ms / 1e3
+    f64 = SR_STAGE_FLOPS["fp64"] / s / 1e12
+    f32 = SR_STAGE_FLOPS["fp32"] / s / 1e12
+    out.update({"achieved": f64, "peak": FP64_PEAK_TFLOPS, "frac": f64 / FP64_PEAK_TFLOPS,
+                "fp64": {"flops_per_launch": SR_STAGE_FLOPS["fp64"], "achieved": f64,
+                         "frac": f64 / FP64_PEAK_TFLOPS},
+                "fp32": {"flops_per_launch": SR_STAGE_FLOPS["fp32"], "achieved": f32,
+                         "frac": f32 / FP32_PEAK_TFLOPS}})
+    return out
+
+
+def _tc_ab(pkg, torch, args):
+    """Volume contraction of the SR stage kernel on the tensor cores (split-BF16x3
+    mma.sync) vs FP32 FMA, per n: the blast at about 512k nodes, mixed, warm
+    start; mean stage-launch time over 5 graph-replayed steps each."""
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    table = {}
+    for n in range(3, 9):
+        k = max(4, int(round((512000.0 / n ** 3) ** (1.0 / 3.0))))
+        w = dict(BLAST, K=(k, k, k), n=n)
+        setup = pkg.Mesh(precision=0, **_mesh_kw(w))
+        U0 = _state(pkg, torch, w, setup)
+        setup.close()
+        row = {"elements": k ** 3, "nodes": k ** 3 * n ** 3}
+        for key, tc in (("tensor_core_ms", 1), ("fma_ms", 0)):
+            m = pkg.Mesh(precision=1, **_mesh_kw(w))
+            m.set_option(pkg.abi.OPT_TENSOR_CORE_CONTRACTION, tc)
+            U = U0.clone()
+            for _ in range(3):
+                m.rk3_step(U, cfl=w["cfl"])
+            _, prof = _timed_steps(pkg, torch, m, U, w, 5, None, flush=flush)
+            row[key] = prof["stage"][0] / prof["stage"][1]
+            m.close()
+        row["faster"] = "tensor_core" if row["tensor_core_ms"] < row["fma_ms"] else "fma"
+        table[str(n)] = row
+    return {"workload": "SR blast, K^3 elements with K^3 n^3 about 512k nodes, mixed, warm start, HLL, MinModN",
+            "stat": "mean k_stage_mixed launch, CUDA events in graph replays, L2 flushed per step", "per_n": table}
+
+
 def _sr_blast(pkg, torch, args):
     """The relativistic blast (secondary): mixed with the learned guess, mixed
     warm-started, FP64; L2 flushed between steps (its state fits in L2)."""
@@ -394,6 +471,8 @@ def _sr_blast(pkg, torch, args):
         ms, prof = _timed_steps(pkg, torch, m, U, w, steps, None, flush=flush)
         out[key] = {"value": nodes * 5 * steps / (sum(ms) / 1e3), "unit": UNIT, "ms_per_step": sum(ms) / steps,
                     "kernels": _kern(prof), "device_status": m.sync_status()}
+        if key == "mixed_learned":
+            out["alu_roofline"] = _alu_roofline(prof["stage"][0] / prof["stage"][1])
         m.close()
     acc = {}
     for name, use_net in (("learned", net), ("warm_start", None)):
@@ -422,8 +501,9 @@ def _ensemble(pkg, torch, args):
     [3, 8].  NE meshes carry the smooth density wave (LLF, no limiter), SR meshes
     the blast (HLL, MinModN, learned con2prim guess); mixed precision, CFL 0.2.
     Times `ens_steps` steps of (a) the batched per-group launches replayed as one
-    CUDA graph per step, after the launch-shape autotuner, and (b) the same meshes
-    stepped one by one with dg_rk3_step.  The states (2.7 GB each) exceed L2."""
+    CUDA graph per step, after the launch-shape autotuner, with the groups on
+    parallel graph branches and, for comparison, on one chain, and (b) the same
+    meshes stepped one by one with dg_rk3_step.  The states (2.7 GB each) exceed L2."""
     net, _ = _train_guess_net(pkg, torch, BLAST)
     recipe = dg_inputs.ensemble_recipe(5)
     meshes, states = [], []
@@ -457,8 +537,11 @@ def _ensemble(pkg, torch, args):
         return sum(a.elapsed_time(b) for a, b in ev)
 
     for _ in range(3):
-        pkg.abi.dg_ensemble_step(ens, 0.2, use_graph=True)
-    batched_ms = timed(lambda: pkg.abi.dg_ensemble_step(ens, 0.2, use_graph=True))
+        pkg.abi.dg_ensemble_step(ens, 0.2, use_graph=2)
+    serial_ms = timed(lambda: pkg.abi.dg_ensemble_step(ens, 0.2, use_graph=2))
+    for _ in range(3):
+        pkg.abi.dg_ensemble_step(ens, 0.2, use_graph=1)
+    batched_ms = timed(lambda: pkg.abi.dg_ensemble_step(ens, 0.2, use_graph=1))
 
     def one_by_one():
         for m, U in zip(meshes, states):
@@ -478,7 +561,11 @@ def _ensemble(pkg, torch, args):
                         "K in [2,16], n in [3,8], seed 5, mixed precision, CFL 0.2",
             "meshes": len(recipe), "nodes": nodes, "steps": args.ens_steps,
             "batched_graph": {"value": dof / (batched_ms / 1e3), "unit": UNIT,
-                              "ms_per_step": batched_ms / args.ens_steps},
+                              "ms_per_step": batched_ms / args.ens_steps,
+                              "launch": "one CUDA graph per step, each group's launches on its own branch"},
+            "batched_graph_one_chain": {"value": dof / (serial_ms / 1e3), "unit": UNIT,
+                                        "ms_per_step": serial_ms / args.ens_steps,
+                                        "launch": "one CUDA graph per step, the groups one after the other"},
             "per_mesh_launches": {"value": dof / (permesh_ms / 1e3), "unit": UNIT,
                                   "ms_per_step": permesh_ms / args.ens_steps},
             "speedup": permesh_ms / batched_ms, "tune_s": round(tune_s, 3), "groups": groups,
@@ -489,20 +576,16 @@ def _ensemble(pkg, torch, args):
 # stages of a step), from a one-kernel ncu capture of the same kernel on the
 # 32^3-element case of the same problem scaled by the node count (64^3 / 32^3 = 8).
 # Reported only while the kernel's sources still hash to their state at capture.
-TRAFFIC_BYTES_PER_LAUNCH = None
+# (410.6 MB per launch at 32^3, 58.0 B per node.)
+TRAFFIC_BYTES_PER_LAUNCH = 3285009067
 TRAFFIC_SOURCES = ("paper_1609_00098_gb300/csrc/dg_ne_mixed.cuh", "paper_1609_00098_gb300/csrc/dg_internal.h")
-TRAFFIC_SOURCES_SHA256 = ""
+TRAFFIC_SOURCES_SHA256 = "812359cfd4454e06c6e24e612d2851158da07bb1458345509220c01a5d077bfc"
 
 
 def _traffic():
-    import hashlib
-    if TRAFFIC_BYTES_PER_LAUNCH is None:
+    if TRAFFIC_BYTES_PER_LAUNCH is None or not _sources_match(TRAFFIC_SOURCES, TRAFFIC_SOURCES_SHA256):
         return None
-    h = hashlib.sha256()
-    for f in TRAFFIC_SOURCES:
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
-    return TRAFFIC_BYTES_PER_LAUNCH if h.hexdigest() == TRAFFIC_SOURCES_SHA256 else None
+    return TRAFFIC_BYTES_PER_LAUNCH
 
 
 def _design_bytes_per_node_stage(masked_all):
@@ -515,16 +598,8 @@ def _design_bytes_per_node_stage(masked_all):
     return (60.0 + 2 * (60.0 if masked_all else 80.0)) / 3.0
 
 
-def run_ours(args):
-    import torch
-    import paper_1609_00098_gb300 as pkg
-
-    ws, rank, local = _dist()
-    torch.cuda.set_device(local)
-    dist = None
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
+def _headline(pkg, torch, args, ws, local, dist):
+    """The KH workload: mixed (timed), FP64, accuracy, end to end, roofline."""
     w = KH
     nodes = _nodes(w)
     setup = pkg.Mesh(precision=0, **_mesh_kw(w))
@@ -639,12 +714,31 @@ def run_ours(args):
     mesh.close()
     del mesh_state, runs
     torch.cuda.empty_cache()
+    return out
+
+
+def run_ours(args):
+    import torch
+    import paper_1609_00098_gb300 as pkg
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    if args.skip_kh:
+        out = {"metric": METRIC, "unit": UNIT, "n_gpus": ws, "note": "--skip-kh: secondary objects only"}
+    else:
+        out = _headline(pkg, torch, args, ws, local, dist)
     if not args.no_sr:
         out["sr_blast"] = _sr_blast(pkg, torch, args)
     if not args.no_con2prim:
         out["con2prim"] = _con2prim_bench(pkg, torch)
     if not args.no_ensemble:
         out["ensemble"] = _ensemble(pkg, torch, args)
+    if not args.no_tc_ab:
+        out["tc_contraction"] = _tc_ab(pkg, torch, args)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(seconds=args.cpu_seconds)
     if dist:
@@ -731,9 +825,17 @@ def main():
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-sr", action="store_true")
     ap.add_argument("--no-con2prim", action="store_true")
+    ap.add_argument("--no-tc-ab", action="store_true")
+    ap.add_argument("--kh-k", type=int, default=KH["K"][0],
+                    help="elements per axis of the KH problem (smaller for profiling captures)")
+    ap.add_argument("--skip-kh", action="store_true",
+                    help="time only the secondary objects (profiling captures of their kernels)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.kh_k < 1:
+        ap.error("--kh-k must be >= 1")
+    KH["K"] = (args.kh_k,) * 3
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -231,10 +231,13 @@ dg_status dg_rhs_static(const dg_mesh_desc *desc, const double *U, double *dUdt,
 
 /* Per-mesh options of the mixed-precision path (no effect on the FP64 path,
  * which always follows the oracle's arithmetic).
- *   DG_OPT_TENSOR_CORE_CONTRACTION (default 1): 1 evaluates the volume
- *     contraction sum_l D_il F_l (Sec. 3.1, eq:405) on the tensor cores as
- *     split-BF16x3 products accumulated in FP32; 0 uses FP32 FMA on the CUDA
- *     cores.  Both are FP32-accurate.
+ *   DG_OPT_TENSOR_CORE_CONTRACTION (default 0): 1 evaluates the volume
+ *     contraction sum_l D_il F_l (Sec. 3.1, eq:405) of the relativistic (and
+ *     Newtonian MRS-limited) stage kernel on the tensor cores as split-BF16x3
+ *     products accumulated in FP32; 0 uses FP32 FMA on the CUDA cores.  Both
+ *     are FP32-accurate; FMA is the faster of the two for every n = 3..8 on
+ *     this GPU.  The Newtonian stage kernel of the other limiters contracts
+ *     with FMA only and ignores the option.
  *   DG_OPT_C2P_KAPPA_SWITCH (default 10): the conditioning estimate tau/(rho eps)
  *     above which the FP32 con2prim result is finished by FP64 Newton on the FP64
  *     state (it also bounds W^2 for the FP32 wave speeds); in [1, 1e30].
@@ -285,8 +288,13 @@ void dg_ensemble_destroy(dg_ensemble *ens);
  * and both volume contractions, and keep the fastest.  Synchronises `stream`. */
 dg_status dg_ensemble_tune(dg_ensemble *ens, void *stream);
 /* One SSP-RK3 step of every mesh (Sec. 3.4) with dt = cfl dx_min / lambda_max of
- * that mesh.  use_graph != 0: from the second step on, the step's launches are
- * captured once into a CUDA graph (again when cfl changes) and replayed. */
+ * that mesh.  Each group's launches run on a stream of the ensemble's own, forked
+ * from `stream` and joined back to it, so that different groups' kernels overlap.
+ * use_graph = 1 or 2: from the second step on, the step's launches are captured
+ * once into a CUDA graph (again when cfl or use_graph changes) and replayed; with
+ * 2 the graph runs the groups one after the other on a single chain instead (the
+ * same results, for comparison).  use_graph = 0: direct launches.
+ * Errors: DG_ERR_ARG for cfl <= 0 or use_graph outside 0..2. */
 dg_status dg_ensemble_step(dg_ensemble *ens, double cfl, int use_graph, void *stream);
 /* Groups and, for group g, info = (n, system, flux, limiter, meshes, elements,
  * elements per CTA, tensor-core contraction 0/1). */

@@ -298,7 +298,10 @@ def dg_ensemble_tune(ens, stream=None):
 
 
 def dg_ensemble_step(ens, cfl, use_graph=True, stream=None):
-    _check(load().dg_ensemble_step(ens, float(cfl), 1 if use_graph else 0, _stream(stream)))
+    """use_graph: False/0 direct launches, True/1 graph with the groups on parallel
+    branches, 2 graph with the groups on one chain."""
+    g = int(use_graph) if not isinstance(use_graph, bool) else (1 if use_graph else 0)
+    _check(load().dg_ensemble_step(ens, float(cfl), g, _stream(stream)))
 
 
 def dg_ensemble_num_groups(ens) -> int:

@@ -655,7 +655,7 @@ dg_status dg_mesh_create(const dg_mesh_desc *d, dg_mesh **out)
     const size_t state = sizeof(double) * (size_t)E * 5 * m->nn;
     const bool mixed = d->precision == DG_PRECISION_MIXED;
     m->kappa_sw = 10.0f;
-    m->tc_contract = 1;
+    m->tc_contract = 0;
     m->epb = 1;
     cudaError_t st = cudaSuccess;
     st = st ? st : cudaMalloc(&m->W1, state);

@@ -91,6 +91,10 @@ struct dg_ensemble {
     long long steps = 0;
     cudaGraphExec_t exec = nullptr;
     double graph_cfl = 0.0;
+    int graph_mode = 0;                  // use_graph of the captured graph
+    std::vector<cudaStream_t> branch;    // one stream per group: its launches run beside the other groups'
+    std::vector<cudaEvent_t> done;       // per group: end of its part of a phase
+    cudaEvent_t fork = nullptr;          // start of a phase on the step's stream
 };
 
 using namespace dg;
@@ -283,53 +287,81 @@ MixedArgs stage_args_for(const EnsGroup &g, const MeshSlot *slots, int stage)
     return a;
 }
 
-// One step of the ensemble.  SR groups: CFL pass, then per stage the stage kernel
-// and the limiter.  Newtonian groups: the delta-form step, whose stage 1 takes the
-// CFL maximum itself, so their stage 1 runs before the batched dt; then per stage
-// the decision pass (the last one writes U^{n+1}).
-cudaError_t launch_step(dg_ensemble *en, double cfl, bool first, cudaStream_t s)
+// The two phases of a group's step.  Before the batched dt: the SR CFL pass, or the
+// Newtonian delta-form stage 1 (which takes the CFL maximum itself).  After it:
+// SR: per stage the stage kernel and the limiter; Newtonian: the decision pass
+// after stage 1, then stages 2 and 3 with their decision passes (the last one
+// writes U^{n+1}).  A group's launches touch only its own meshes.
+cudaError_t group_pre_dt(EnsGroup &g, bool first, cudaStream_t s)
+{
+    if (g.system == 0) return launch_ne_stage(g.n, g.flux, 1, g.ne_proto[0], s);
+    CflArgs c = g.cproto;
+    c.slots = first ? g.d_cfl_first : g.d_cfl;
+    return launch_cfl_batch(g.system, c, g.nchunks, s);
+}
+
+cudaError_t group_stage(EnsGroup &g, bool first, int st, cudaStream_t s)
+{
+    cudaError_t e = cudaSuccess;
+    if (g.system == 0) {
+        if (st > 0) e = launch_ne_stage(g.n, g.flux, st + 1, g.ne_proto[st], s);
+        if (e == cudaSuccess && (st == 2 || g.limiter)) e = launch_ne_decide(g.n, st == 2, g.ne_dproto[st], s);
+        return e;
+    }
+    MixedArgs a = stage_args_for(g, (first && st == 0) ? g.d_stage_first : g.d_stage[st], st);
+    if (g.pgiven && st == 0) a.netImg = nullptr;  // stage 1 takes the CFL pass's primitives
+    e = launch_stage_mixed(g.n, g.system, g.flux, a, s);
+    if (e == cudaSuccess && g.limiter) {
+        LimitMixedArgs l = g.lproto;
+        l.slots = g.d_limit[st];
+        e = launch_limit_mixed(g.n, g.system, l, s);
+    }
+    return e;
+}
+
+// One step of the ensemble: the per-mesh lambda reset, every group's pre-dt
+// phase, the batched dt, every group's stages.  concurrent: each group's phase
+// runs on its own stream, forked from and joined back to s by events (in a
+// captured graph: parallel branches), so that the groups' launches overlap and
+// one launch's last wave does not idle the GPU.  Otherwise everything runs on s,
+// stage by stage across the groups.  Both orders give the same bits: no data
+// crosses groups.
+cudaError_t launch_step(dg_ensemble *en, double cfl, bool first, bool concurrent, cudaStream_t s)
 {
     const int count = (int)en->meshes.size();
     const unsigned blocks = (unsigned)((count + 127) / 128);
+    const int G = (int)en->groups.size();
     k_lam_zero<<<blocks, 128, 0, s>>>(en->d_dt, count);
     cudaError_t e = cudaGetLastError();
-    for (EnsGroup &g : en->groups) {
-        if (e != cudaSuccess) return e;
-        if (g.system == 0) {
-            e = launch_ne_stage(g.n, g.flux, 1, g.ne_proto[0], s);
-            continue;
+    auto fan_out = [&](auto &&body) -> cudaError_t {
+        cudaError_t r = cudaEventRecord(en->fork, s);
+        for (int i = 0; i < G && r == cudaSuccess; ++i) {
+            r = cudaStreamWaitEvent(en->branch[i], en->fork, 0);
+            if (r == cudaSuccess) r = body(en->groups[i], en->branch[i]);
+            if (r == cudaSuccess) r = cudaEventRecord(en->done[i], en->branch[i]);
+            if (r == cudaSuccess) r = cudaStreamWaitEvent(s, en->done[i], 0);
         }
-        CflArgs c = g.cproto;
-        c.slots = first ? g.d_cfl_first : g.d_cfl;
-        e = launch_cfl_batch(g.system, c, g.nchunks, s);
+        return r;
+    };
+    if (e == cudaSuccess) {
+        if (concurrent) {
+            e = fan_out([&](EnsGroup &g, cudaStream_t b) { return group_pre_dt(g, first, b); });
+        } else {
+            for (int i = 0; i < G && e == cudaSuccess; ++i) e = group_pre_dt(en->groups[i], first, s);
+        }
     }
     if (e != cudaSuccess) return e;
     k_dt_batch<<<blocks, 128, 0, s>>>(en->d_dt, count, cfl);
     e = cudaGetLastError();
-    for (int st = 0; st < 3 && e == cudaSuccess; ++st) {
-        for (EnsGroup &g : en->groups) {
-            if (g.system != 0) continue;
-            if (st > 0) e = launch_ne_stage(g.n, g.flux, st + 1, g.ne_proto[st], s);
-            if (e == cudaSuccess && (st == 2 || g.limiter)) e = launch_ne_decide(g.n, st == 2, g.ne_dproto[st], s);
-            if (e != cudaSuccess) return e;
-        }
-        for (EnsGroup &g : en->groups) {
-            if (g.system == 0) continue;
-            MixedArgs a = stage_args_for(g, (first && st == 0) ? g.d_stage_first : g.d_stage[st], st);
-            if (g.pgiven && st == 0) {  // stage 1 takes the CFL pass's primitives
-                a.netImg = nullptr;
-            }
-            e = launch_stage_mixed(g.n, g.system, g.flux, a, s);
-            if (e != cudaSuccess) return e;
-        }
-        for (EnsGroup &g : en->groups) {
-            if (!g.limiter || g.system == 0) continue;
-            LimitMixedArgs l = g.lproto;
-            l.slots = g.d_limit[st];
-            e = launch_limit_mixed(g.n, g.system, l, s);
-            if (e != cudaSuccess) return e;
-        }
-    }
+    if (e != cudaSuccess) return e;
+    if (concurrent)
+        return fan_out([&](EnsGroup &g, cudaStream_t b) {
+            cudaError_t r = cudaSuccess;
+            for (int st = 0; st < 3 && r == cudaSuccess; ++st) r = group_stage(g, first, st, b);
+            return r;
+        });
+    for (int st = 0; st < 3 && e == cudaSuccess; ++st)
+        for (int i = 0; i < G && e == cudaSuccess; ++i) e = group_stage(en->groups[i], first, st, s);
     return e;
 }
 
@@ -384,6 +416,15 @@ dg_status dg_ensemble_create(dg_mesh *const *meshes, double *const *U, int count
     std::vector<DtSlot> dts;
     for (dg_mesh *m : en->meshes) dts.push_back(DtSlot{m->lam, m->dt, m->dxmin});
     if (e == cudaSuccess) e = upload(&en->d_dt, dts);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&en->fork, cudaEventDisableTiming);
+    for (size_t i = 0; i < en->groups.size() && e == cudaSuccess; ++i) {
+        cudaStream_t b = nullptr;
+        cudaEvent_t d = nullptr;
+        e = cudaStreamCreateWithFlags(&b, cudaStreamNonBlocking);
+        if (e == cudaSuccess) en->branch.push_back(b);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&d, cudaEventDisableTiming);
+        if (e == cudaSuccess) en->done.push_back(d);
+    }
     if (e != cudaSuccess) {
         dg_ensemble_destroy(en);
         return cuda_fail(e);
@@ -396,6 +437,9 @@ void dg_ensemble_destroy(dg_ensemble *en)
 {
     if (!en) return;
     if (en->exec) cudaGraphExecDestroy(en->exec);
+    for (cudaStream_t b : en->branch) cudaStreamDestroy(b);
+    for (cudaEvent_t d : en->done) cudaEventDestroy(d);
+    if (en->fork) cudaEventDestroy(en->fork);
     for (EnsGroup &g : en->groups) free_group(g);
     cudaFree(en->d_dt);
     delete en;
@@ -461,11 +505,12 @@ dg_status dg_ensemble_step(dg_ensemble *en, double cfl, int use_graph, void *str
     cudaStream_t s = (cudaStream_t)stream;
     const bool first = en->steps == 0;
     cudaError_t e = cudaSuccess;
+    if (use_graph < 0 || use_graph > 2) return set_error(DG_ERR_ARG, "use_graph must be 0, 1 or 2");
     if (!use_graph || first) {
         // the first step has no pressure guesses yet and runs directly
-        e = launch_step(en, cfl, first, s);
+        e = launch_step(en, cfl, first, use_graph != 2, s);
     } else {
-        if (en->exec && en->graph_cfl != cfl) {
+        if (en->exec && (en->graph_cfl != cfl || en->graph_mode != use_graph)) {
             cudaGraphExecDestroy(en->exec);
             en->exec = nullptr;
         }
@@ -478,7 +523,7 @@ dg_status dg_ensemble_step(dg_ensemble *en, double cfl, int use_graph, void *str
             if (e != cudaSuccess) return cuda_fail(e);
             e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed);
             if (e == cudaSuccess) {
-                const cudaError_t el = launch_step(en, cfl, false, cap);
+                const cudaError_t el = launch_step(en, cfl, false, use_graph == 1, cap);
                 e = cudaStreamEndCapture(cap, &graph);
                 if (e == cudaSuccess) e = el;
             }
@@ -487,6 +532,7 @@ dg_status dg_ensemble_step(dg_ensemble *en, double cfl, int use_graph, void *str
             cudaStreamDestroy(cap);
             if (e != cudaSuccess) return cuda_fail(e);
             en->graph_cfl = cfl;
+            en->graph_mode = use_graph;
         }
         e = cudaGraphLaunch(en->exec, s);
     }

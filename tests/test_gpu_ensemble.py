@@ -62,7 +62,9 @@ def _run_ensemble(pkg, meshes, states, steps, tune):
             pkg.abi.dg_ensemble_tune(ens)
         groups = pkg.abi.dg_ensemble_groups(ens)
         for k in range(steps):
-            pkg.abi.dg_ensemble_step(ens, 0.2, use_graph=(k % 2 == 1) or k >= 2)
+            # direct launches, graph with the groups on parallel branches, graph with
+            # the groups on one chain: the same bits
+            pkg.abi.dg_ensemble_step(ens, 0.2, use_graph=(0, 1, 2, 1)[k % 4])
         dt = torch.empty(len(meshes), dtype=torch.float64, device="cuda")
         pkg.abi.dg_ensemble_dt(ens, dt)
         torch.cuda.synchronize()
@@ -162,3 +164,16 @@ def test_ensemble_matches_oracle(pkg, net):
         _, ref = om.norms(Uo[i], np.zeros_like(Uo[i]))
         rel = d / np.maximum(ref, 1e-2 * ref.max())
         assert np.all(rel <= 1e-6), (i, ORACLE_SPECS[i], rel)
+
+
+def test_ensemble_step_rejects_bad_arguments(pkg, net):
+    em, es = _make(pkg, net)
+    ens = pkg.abi.dg_ensemble_create([m.h for m in em], es)
+    try:
+        for cfl, mode in ((0.0, 1), (0.2, 3), (0.2, -1)):
+            with pytest.raises(pkg.abi.DGError):
+                pkg.abi.dg_ensemble_step(ens, cfl, use_graph=mode)
+    finally:
+        pkg.abi.dg_ensemble_destroy(ens)
+        for m in em:
+            m.close()
