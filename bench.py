@@ -378,11 +378,14 @@ def _con2prim_bench(pkg, torch, reps=3):
 # (+ twice that for the paired FFMA2 / FADD2 / FMUL2), SASS thread instructions
 # with all predicates true.  Reported only while the kernel's sources hash to
 # their state at capture.
-SR_STAGE_FLOPS = None
+# The same capture's pipe utilisation (ncu, % of peak sustained while active, mean
+# of the three launches) is reported beside the flop fractions.
+SR_STAGE_FLOPS = {"fp64": 18911529, "fp32": 348447061}
+SR_STAGE_PIPES = {"fp64_pipe_pct": 35.2, "fma_pipe_pct": 13.9, "alu_pipe_pct": 22.1, "tensor_pipe_pct": 4.6,
+                  "issue_active_pct": 40.8}
 SR_STAGE_SOURCES = ("paper_1609_00098_gb300/csrc/dg_mixed.cuh", "paper_1609_00098_gb300/csrc/dg_physics.cuh",
-                    "paper_1609_00098_gb300/csrc/dg_c2p_net.cuh", "paper_1609_00098_gb300/csrc/dg_internal.h",
-                    "paper_1609_00098_gb300/csrc/dg_api.cu")
-SR_STAGE_SOURCES_SHA256 = ""
+                    "paper_1609_00098_gb300/csrc/dg_c2p_net.cuh", "paper_1609_00098_gb300/csrc/dg_internal.h")
+SR_STAGE_SOURCES_SHA256 = "7be83b600abe32cecc03612f7194d9fd7c3ccdec0bdf6b83044c9607c9c458d7"
 # FMA throughput of this GPU (independent dependent-FMA chains, every SM busy;
 # flops count an FMA as two): FP64 1.20 TFLOP/s, FP32 75.0 TFLOP/s.
 FP64_PEAK_TFLOPS = 1.20
@@ -413,6 +416,7 @@ def _alu_roofline(avg_launch_ms):
     f64 = SR_STAGE_FLOPS["fp64"] / s / 1e12
     f32 = SR_STAGE_FLOPS["fp32"] / s / 1e12
     out.update({"achieved": f64, "peak": FP64_PEAK_TFLOPS, "frac": f64 / FP64_PEAK_TFLOPS,
+                "ncu_pipes": SR_STAGE_PIPES,
                 "fp64": {"flops_per_launch": SR_STAGE_FLOPS["fp64"], "achieved": f64,
                          "frac": f64 / FP64_PEAK_TFLOPS},
                 "fp32": {"flops_per_launch": SR_STAGE_FLOPS["fp32"], "achieved": f32,
@@ -465,6 +469,8 @@ def _sr_blast(pkg, torch, args):
         m = pkg.Mesh(precision=precision, **_mesh_kw(w))
         if use_net is not None:
             m.set_c2p_net(use_net)
+        if precision:
+            m.set_option(pkg.abi.OPT_TENSOR_CORE_CONTRACTION, 0)  # FP32 FMA (faster at every n: tc_contraction)
         U = U0.clone()
         for _ in range(max(3, args.warmup)):
             m.rk3_step(U, cfl=w["cfl"])
@@ -495,14 +501,32 @@ def _sr_blast(pkg, torch, args):
     return out
 
 
+def _hbm_peak():
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(peaks["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs (measured)"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _ensemble_roofline(nodes, ms_per_step):
+    """Whole-step HBM roofline of the batched ensemble: the survey's 64 B per
+    dof-update (320 B per node-step) over the graph-timed step."""
+    peak, src = _hbm_peak()
+    achieved = 320.0 * nodes / (ms_per_step / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "bytes_per_step": 320.0 * nodes, "rule": "64 B per dof-update over the graph-timed step",
+            "peak_source": src}
+
+
 def _ensemble(pkg, torch, args):
     """Ragged ensemble (untimed setup): 256 meshes from the seeded recipe -- system
     NE or SR with probability 1/2, K uniform in [2, 16] per axis, n uniform in
     [3, 8].  NE meshes carry the smooth density wave (LLF, no limiter), SR meshes
     the blast (HLL, MinModN, learned con2prim guess); mixed precision, CFL 0.2.
     Times `ens_steps` steps of (a) the batched per-group launches replayed as one
-    CUDA graph per step, after the launch-shape autotuner, with the groups on
-    parallel graph branches and, for comparison, on one chain, and (b) the same
+    CUDA graph per step, after the launch-shape autotuner, with the groups one
+    after the other and, for comparison, on parallel graph branches, and (b) the same
     meshes stepped one by one with dg_rk3_step.  The states (2.7 GB each) exceed L2."""
     net, _ = _train_guess_net(pkg, torch, BLAST)
     recipe = dg_inputs.ensemble_recipe(5)
@@ -538,7 +562,7 @@ def _ensemble(pkg, torch, args):
 
     for _ in range(3):
         pkg.abi.dg_ensemble_step(ens, 0.2, use_graph=2)
-    serial_ms = timed(lambda: pkg.abi.dg_ensemble_step(ens, 0.2, use_graph=2))
+    branches_ms = timed(lambda: pkg.abi.dg_ensemble_step(ens, 0.2, use_graph=2))
     for _ in range(3):
         pkg.abi.dg_ensemble_step(ens, 0.2, use_graph=1)
     batched_ms = timed(lambda: pkg.abi.dg_ensemble_step(ens, 0.2, use_graph=1))
@@ -562,13 +586,14 @@ def _ensemble(pkg, torch, args):
             "meshes": len(recipe), "nodes": nodes, "steps": args.ens_steps,
             "batched_graph": {"value": dof / (batched_ms / 1e3), "unit": UNIT,
                               "ms_per_step": batched_ms / args.ens_steps,
-                              "launch": "one CUDA graph per step, each group's launches on its own branch"},
-            "batched_graph_one_chain": {"value": dof / (serial_ms / 1e3), "unit": UNIT,
-                                        "ms_per_step": serial_ms / args.ens_steps,
-                                        "launch": "one CUDA graph per step, the groups one after the other"},
+                              "launch": "one CUDA graph per step, the groups one after the other"},
+            "batched_graph_parallel_branches": {"value": dof / (branches_ms / 1e3), "unit": UNIT,
+                                                "ms_per_step": branches_ms / args.ens_steps,
+                                                "launch": "one CUDA graph per step, each group on its own branch"},
             "per_mesh_launches": {"value": dof / (permesh_ms / 1e3), "unit": UNIT,
                                   "ms_per_step": permesh_ms / args.ens_steps},
             "speedup": permesh_ms / batched_ms, "tune_s": round(tune_s, 3), "groups": groups,
+            "roofline": _ensemble_roofline(nodes, batched_ms / args.ens_steps),
             "device_status": status}
 
 

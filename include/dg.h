@@ -288,12 +288,12 @@ void dg_ensemble_destroy(dg_ensemble *ens);
  * and both volume contractions, and keep the fastest.  Synchronises `stream`. */
 dg_status dg_ensemble_tune(dg_ensemble *ens, void *stream);
 /* One SSP-RK3 step of every mesh (Sec. 3.4) with dt = cfl dx_min / lambda_max of
- * that mesh.  Each group's launches run on a stream of the ensemble's own, forked
- * from `stream` and joined back to it, so that different groups' kernels overlap.
- * use_graph = 1 or 2: from the second step on, the step's launches are captured
- * once into a CUDA graph (again when cfl or use_graph changes) and replayed; with
- * 2 the graph runs the groups one after the other on a single chain instead (the
- * same results, for comparison).  use_graph = 0: direct launches.
+ * that mesh.  use_graph = 0: direct launches on `stream`.  1: from the second step
+ * on, the step's launches are captured once into a CUDA graph (again when cfl or
+ * use_graph changes) and replayed.  2: as 1, but each group's launches run on a
+ * stream of the ensemble's own, forked from `stream` and joined back to it (in the
+ * graph: parallel branches), so that different groups' kernels overlap; the same
+ * results (slower on the GPUs measured; kept for comparison).
  * Errors: DG_ERR_ARG for cfl <= 0 or use_graph outside 0..2. */
 dg_status dg_ensemble_step(dg_ensemble *ens, double cfl, int use_graph, void *stream);
 /* Groups and, for group g, info = (n, system, flux, limiter, meshes, elements,

@@ -298,8 +298,8 @@ def dg_ensemble_tune(ens, stream=None):
 
 
 def dg_ensemble_step(ens, cfl, use_graph=True, stream=None):
-    """use_graph: False/0 direct launches, True/1 graph with the groups on parallel
-    branches, 2 graph with the groups on one chain."""
+    """use_graph: False/0 direct launches, True/1 graph with the groups one after the
+    other, 2 graph with the groups on parallel branches."""
     g = int(use_graph) if not isinstance(use_graph, bool) else (1 if use_graph else 0)
     _check(load().dg_ensemble_step(ens, float(cfl), g, _stream(stream)))
 

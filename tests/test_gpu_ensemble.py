@@ -62,8 +62,8 @@ def _run_ensemble(pkg, meshes, states, steps, tune):
             pkg.abi.dg_ensemble_tune(ens)
         groups = pkg.abi.dg_ensemble_groups(ens)
         for k in range(steps):
-            # direct launches, graph with the groups on parallel branches, graph with
-            # the groups on one chain: the same bits
+            # direct launches, graph with the groups on one chain, graph with the
+            # groups on parallel branches: the same bits
             pkg.abi.dg_ensemble_step(ens, 0.2, use_graph=(0, 1, 2, 1)[k % 4])
         dt = torch.empty(len(meshes), dtype=torch.float64, device="cuda")
         pkg.abi.dg_ensemble_dt(ens, dt)
