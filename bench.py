@@ -173,26 +173,12 @@ def _rel_l2(torch, w3, a, b):
     return (d / torch.clamp(r, min=1e-2 * float(r.max()))).cpu().tolist()
 
 
-def _timed_steps(pkg, torch, mesh, U, w, steps, dist, flush=None):
-    """Graph-replayed steps, each bracketed by CUDA events on the replay stream, with
-    the library's per-kernel events captured into the same graph (external event
-    nodes): kernel durations come from the very replays that are timed."""
-    pkg.abi.dg_profile_enable(mesh.h, True)
-    graph = torch.cuda.CUDAGraph()
-    side = torch.cuda.Stream()
-    side.wait_stream(torch.cuda.current_stream())
-    with torch.cuda.stream(side):
-        mesh.rk3_step(U, cfl=w["cfl"])  # one more warm step on the capture stream
-    torch.cuda.current_stream().wait_stream(side)
-    torch.cuda.synchronize()
-    pkg.abi.dg_profile_read(mesh.h)  # drop the eager warm step's events
-    with torch.cuda.graph(graph):
-        mesh.rk3_step(U, cfl=w["cfl"])
-    torch.cuda.synchronize()
+def _replay(torch, graph, steps, dist, flush, after=None):
+    """`steps` replays of `graph`, each bracketed by CUDA events on the replay stream
+    (L2 flushed before each when `flush` is given, outside the events)."""
     stream = torch.cuda.current_stream()
     s_ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     e_ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
-    prof = {}
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -202,18 +188,54 @@ def _timed_steps(pkg, torch, mesh, U, w, steps, dist, flush=None):
         s_ev[k].record(stream)
         graph.replay()
         e_ev[k].record(stream)
-        torch.cuda.synchronize()
+        if after is not None:
+            torch.cuda.synchronize()
+            after()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    return [s.elapsed_time(e) for s, e in zip(s_ev, e_ev)]
+
+
+def _capture(pkg, torch, mesh, U, w):
+    graph = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        mesh.rk3_step(U, cfl=w["cfl"])  # one more warm step on the capture stream
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    pkg.abi.dg_profile_read(mesh.h)  # drop the eager warm step's events, if any
+    with torch.cuda.graph(graph):
+        mesh.rk3_step(U, cfl=w["cfl"])
+    torch.cuda.synchronize()
+    return graph
+
+
+def _timed_steps(pkg, torch, mesh, U, w, steps, dist, flush=None):
+    """Graph-replayed steps, timed twice: (1) the step alone, each replay bracketed
+    by CUDA events on the replay stream: the step time; (2) the same steps with
+    the library's per-kernel events captured into the graph (external event
+    nodes), so that kernel durations come from replays of the step that is timed.
+    Returns (step times of 1, per-kernel totals of 2, step times of 2): the
+    difference of the step times is what the event nodes cost."""
+    graph = _capture(pkg, torch, mesh, U, w)
+    step_ms = _replay(torch, graph, steps, dist, flush)
+    del graph
+    pkg.abi.dg_profile_enable(mesh.h, True)
+    graph = _capture(pkg, torch, mesh, U, w)
+    prof = {}
+
+    def collect():
         for c, (ms, n) in pkg.abi.dg_profile_read(mesh.h).items():
             acc = prof.setdefault(c, [0.0, 0])
             acc[0] += ms
             acc[1] += n
-    if dist:
-        dist.barrier()
-    step_ms = [s.elapsed_time(e) for s, e in zip(s_ev, e_ev)]
+    prof_ms = _replay(torch, graph, steps, dist, flush, after=collect)
     pkg.abi.dg_profile_enable(mesh.h, False)
     del graph  # before the mesh that owns the graph's events goes
     torch.cuda.synchronize()
-    return step_ms, prof
+    return step_ms, prof, prof_ms
 
 
 def _kern(prof):
@@ -407,7 +429,7 @@ def _alu_roofline(avg_launch_ms):
     out = {"kernel": "k_stage_mixed<5, SR, HLL, learned guess>", "bound": "alu", "unit": "TFLOP/s",
            "avg_launch_ms": avg_launch_ms, "peak_fp64": FP64_PEAK_TFLOPS, "peak_fp32": FP32_PEAK_TFLOPS,
            "peak_source": "FMA-chain micro-benchmark on this GPU (measured)",
-           "timing": "CUDA events captured in the timed graph replays"}
+           "timing": "CUDA events captured as graph nodes into replays of the timed step (second pass of the same steps)"}
     if SR_STAGE_FLOPS is None or not _sources_match(SR_STAGE_SOURCES, SR_STAGE_SOURCES_SHA256):
         out.update({"achieved": None, "peak": FP64_PEAK_TFLOPS, "frac": None,
                     "note": "no flop count captured for the current kernel sources"})
@@ -443,7 +465,7 @@ def _tc_ab(pkg, torch, args):
             U = U0.clone()
             for _ in range(3):
                 m.rk3_step(U, cfl=w["cfl"])
-            _, prof = _timed_steps(pkg, torch, m, U, w, 5, None, flush=flush)
+            _, prof, _ = _timed_steps(pkg, torch, m, U, w, 5, None, flush=flush)
             row[key] = prof["stage"][0] / prof["stage"][1]
             m.close()
         row["faster"] = "tensor_core" if row["tensor_core_ms"] < row["fma_ms"] else "fma"
@@ -474,8 +496,9 @@ def _sr_blast(pkg, torch, args):
         U = U0.clone()
         for _ in range(max(3, args.warmup)):
             m.rk3_step(U, cfl=w["cfl"])
-        ms, prof = _timed_steps(pkg, torch, m, U, w, steps, None, flush=flush)
+        ms, prof, pms = _timed_steps(pkg, torch, m, U, w, steps, None, flush=flush)
         out[key] = {"value": nodes * 5 * steps / (sum(ms) / 1e3), "unit": UNIT, "ms_per_step": sum(ms) / steps,
+                    "ms_per_step_with_kernel_events": sum(pms) / steps,
                     "kernels": _kern(prof), "device_status": m.sync_status()}
         if key == "mixed_learned":
             out["alu_roofline"] = _alu_roofline(prof["stage"][0] / prof["stage"][1])
@@ -645,13 +668,13 @@ def _headline(pkg, torch, args, ws, local, dist):
         torch.cuda.synchronize()
         if m.sync_status() != 0:
             raise RuntimeError("warm-up steps reported a device error")
-        ms, prof = _timed_steps(pkg, torch, m, U, w, args.steps if key == "mixed" else args.fp64_steps, dist)
-        runs[key] = (m, ms, prof, m.sync_status(), U)
+        ms, prof, pms = _timed_steps(pkg, torch, m, U, w, args.steps if key == "mixed" else args.fp64_steps, dist)
+        runs[key] = (m, ms, prof, m.sync_status(), U, pms)
     clk = clocks.stop()
-    mesh, step_ms, prof, status, mesh_state = runs["mixed"]
+    mesh, step_ms, prof, status, mesh_state, prof_step_ms = runs["mixed"]
     total_ms = max_over_ranks(float(sum(step_ms)), dist)
     value = whole_job_rate(nodes, ws, args.steps, total_ms)
-    f_mesh, f_ms, f_prof, f_status, _ = runs["fp64"]
+    f_mesh, f_ms, f_prof, f_status, _, _ = runs["fp64"]
     f_total = max_over_ranks(float(sum(f_ms)), dist)
     f_value = whole_job_rate(nodes, ws, args.fp64_steps, f_total)
     f_mesh.close()
@@ -719,6 +742,7 @@ def _headline(pkg, torch, args, ws, local, dist):
                 "steps": args.e2e_steps},
         "gpu_launches": launches,
         "kernels": _kern(prof),
+        "ms_per_step_with_kernel_events": max_over_ranks(float(sum(prof_step_ms)), dist) / args.steps,
         "roofline": {"kernel": "k_ne_stage (fused RHS of eq:411 + SSP-RK3 stage difference + limiter summaries)",
                      "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": _traffic(),
@@ -728,7 +752,7 @@ def _headline(pkg, torch, args, ws, local, dist):
                      "design_bytes_per_launch": bytes_design,
                      "design_frac": bytes_design / stage_avg_s / 1e9 / hbm_peak,
                      "avg_launch_ms": stage_avg_s * 1e3, "launches_timed": int(st_n),
-                     "timing": "CUDA events captured in the timed graph replays",
+                     "timing": "CUDA events captured as graph nodes into replays of the timed step (second pass of the same steps)",
                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks else "fallback"},
         "step_roofline": {"ceiling_dof_updates_per_s": hbm_peak * 1e9 / 64.0,
                           "frac": value / (hbm_peak * 1e9 / 64.0),

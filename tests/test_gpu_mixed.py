@@ -152,6 +152,32 @@ def test_mixed_kh_close_to_oracle(pkg):
     assert np.all(d <= 1e-6), d
 
 
+@pytest.mark.parametrize("n,flux,limiter,K", [(3, 0, 2, (5, 4, 3)), (7, 1, 2, (3, 3, 2)), (4, 2, 1, (9, 2, 3)),
+                                             (8, 1, 1, (2, 3, 2))])
+def test_mixed_ne_difference_form(pkg, n, flux, limiter, K):
+    """The Newtonian difference-form step (SSP-RK3 of Sec. 3.4 written in stage
+    differences, the limiter's summaries by linearity, Sec. 3.3.1-3.3.2) with
+    MinMod and MinModN, LLF, HLL and Roe, odd and even n, element counts that are
+    not multiples of the elements per CTA: five shear-layer steps within the
+    1e-6 bar of the oracle, and the last stage's troubled flags equal."""
+    import torch
+    kw = dict(lo=(-0.5,) * 3, hi=(0.5,) * 3, gamma=5 / 3)
+    om, gm = _pair(pkg, 0, K, n, flux, limiter, **kw)
+    U = om.from_prim(di.kh_ne(om.coords(), seed=4))
+    Ug = _gpu(U)
+    tg = torch.zeros(om.E, dtype=torch.uint8, device="cuda")
+    for _ in range(5):
+        h = om.cfl_dt(U, 0.2)
+        to = np.zeros(om.E, dtype=np.uint8)
+        U = om.rk3_step(U, h, to)
+        gm.rk3_step(Ug, dt=h, troubled=tg)
+    assert gm.sync_status() == 0
+    d = _rel_l2(om, Ug.cpu().numpy(), U)
+    assert np.all(d <= 1e-6), d
+    if limiter == 2:
+        assert np.all(tg.cpu().numpy() == 0x1f) and np.all(to == 0x1f)  # MinMod limits every variable
+
+
 def test_mixed_conservation(pkg):
     """FP64 state: totals drift only by the FP32 rounding of the fluxes and of the
     stage increments (relative to the largest total)."""
