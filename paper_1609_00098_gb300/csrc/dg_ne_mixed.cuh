@@ -329,6 +329,17 @@ __device__ __forceinline__ void ne_ld_line(const float *p, float v[NP])
     }
 }
 
+// Bulk prefetch of [p, p + bytes) into L2 (a hint: no data reaches the SM).  The
+// range is shrunk to 16-byte boundaries so that nothing outside it is touched.
+__device__ __forceinline__ void ne_prefetch_l2(const void *p, unsigned long long bytes)
+{
+    unsigned long long a;
+    asm("cvta.to.global.u64 %0, %1;" : "=l"(a) : "l"(p));
+    const unsigned long long lo = (a + 15ull) & ~15ull, hi = (a + bytes) & ~15ull;
+    if (hi > lo)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(lo), "r"((unsigned)(hi - lo)) : "memory");
+}
+
 // Linear part of a limited variable's replacement at LGL coordinates (x, y, z),
 // sh = {f32(U0), s_x dx/2, s_y dy/2, s_z dz/2}: one fixed rounding sequence, so that
 // every place that evaluates it (own nodes, neighbours' face nodes) gets the same bits.
@@ -441,9 +452,15 @@ __global__ void __launch_bounds__(NeShape<NP>::THREADS, NeShape<NP>::MINB) k_ne_
     const float xj = a.x[j], xk = a.x[k];
 
     if (t < EPB) sLamE[t] = 0u;
+    // the element's U^n (and below, the difference of its variables that are not
+    // limited) on its way to L2 while the neighbour tables are built: phase 1's
+    // loads then wait on L2, not on DRAM
+    if (live && ln == L - 1) ne_prefetch_l2(sl.Un + e * 5 * NN, sizeof(double) * 5 * NN);
     for (int q = ln; live && q < 7; q += L) {
         if (q == 6) {
-            sMask[sub][0] = lim_in ? sl.mask[e] : 0u;
+            const unsigned mo = lim_in ? sl.mask[e] : 0u;
+            sMask[sub][0] = mo;
+            if (ST >= 2 && mo != 0x1fu) ne_prefetch_l2(sl.Din + e * 5 * NN, sizeof(float) * 5 * NN);
         } else {
             const int ax = q >> 1, side = q & 1;
             const long long en = elem_neighbour_bc(e, sl.K, ax, side ? 1 : -1, sl.gh);
