@@ -113,7 +113,9 @@ dg_status dg_primitives(dg_mesh *mesh, const double *U, double *P, void *stream)
 
 /* Semi-discrete right-hand side dU/dt of eq:411 (volume term by tensor-product
  * differentiation, eq:405; surface term with the numerical flux lifted into the
- * boundary nodes).  U and dUdt must not alias. */
+ * boundary nodes).  U and dUdt must not alias.  Mixed-precision Newtonian meshes
+ * move U in 16-byte pieces: U must be 16-byte aligned (cudaMalloc and PyTorch
+ * allocations are), else DG_ERR_ARG. */
 dg_status dg_rhs(dg_mesh *mesh, const double *U, double *dUdt, void *stream);
 
 /* CFL step of Sec. 3.4: *dt = cfl * dx_min / lambda_max, dx_min the smallest
@@ -127,7 +129,10 @@ dg_status dg_compute_dt(dg_mesh *mesh, const double *U, double cfl, double *dt, 
  * cfl > 0: dt is the CFL step of Un, computed on the device inside the step;
  * cfl <= 0: the host value dt is used.  dt_used (device, 1 double, may be NULL)
  * receives the step taken.  troubled (device, E bytes, may be NULL) receives the
- * bitmask of limited variables of the last stage. */
+ * bitmask of limited variables of the last stage.  Mixed-precision Newtonian
+ * meshes (other than with DG_LIMITER_MRS) run the step in the equivalent
+ * difference form D_s = U_s - Un (FP32 differences, FP64 Un and Un+1) and need U
+ * 16-byte aligned (else DG_ERR_ARG). */
 dg_status dg_rk3_step(dg_mesh *mesh, double *U, double dt, double cfl, double *dt_used,
                       unsigned char *troubled, void *stream);
 
@@ -278,8 +283,8 @@ dg_status dg_mesh_set_c2p_net(dg_mesh *mesh, const dg_c2p_net *net);
  * meshes one by one with the same per-group options.  Device-side failures set
  * each mesh's status word (dg_sync_status per mesh).
  * Errors: DG_ERR_ARG for NULL or repeated meshes/states, FP64 meshes, or meshes on
- * another device, meshes with the moment limiter (DG_LIMITER_MRS); DG_ERR_CUDA for
- * allocation failures. */
+ * another device, meshes with the moment limiter (DG_LIMITER_MRS), Newtonian
+ * states that are not 16-byte aligned; DG_ERR_CUDA for allocation failures. */
 typedef struct dg_ensemble dg_ensemble;
 dg_status dg_ensemble_create(dg_mesh *const *meshes, double *const *U, int count, dg_ensemble **out);
 void dg_ensemble_destroy(dg_ensemble *ens);

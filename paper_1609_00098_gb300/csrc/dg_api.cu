@@ -344,6 +344,7 @@ NeSlot ne_slot(const dg_mesh *m)
     NeSlot sl;
     std::memset(&sl, 0, sizeof(sl));
     sl.gh = m->gh;
+    sl.err = m->err;
     const int n = m->d.n;
     for (int ax = 0; ax < 3; ++ax) {
         sl.K[ax] = m->d.K[ax];
@@ -764,9 +765,12 @@ dg_status dg_rhs(dg_mesh *m, const double *U, double *dUdt, void *stream)
 {
     if (dg_status s = check_mesh(m)) return s;
     if (!U || !dUdt || U == dUdt) return fail(DG_ERR_ARG, "U and dUdt must be distinct, non-NULL");
+    const bool ne_mixed = m->d.precision == DG_PRECISION_MIXED && m->d.system == 0;
+    if (ne_mixed && (reinterpret_cast<uintptr_t>(U) & 15u))
+        return fail(DG_ERR_ARG, "the mixed Newtonian path needs U 16-byte aligned");
     cudaStream_t s = (cudaStream_t)stream;
     if (m->gh.mask) DG_LAUNCH(m, s, PROF_OTHER, launch_exterior(m, 0.0, nullptr, 0.0, s));
-    if (m->d.precision == DG_PRECISION_MIXED && m->d.system == 0) {
+    if (ne_mixed) {
         NeArgs a = ne_args(m);
         a.one.Un = U;
         a.one.rhs = dUdt;
@@ -926,8 +930,11 @@ dg_status dg_rk3_step(dg_mesh *m, double *U, double dt, double cfl, double *dt_u
     const bool cflmode = cfl > 0.0;
     if (!cflmode && !(dt > 0.0)) return fail(DG_ERR_ARG, "need dt > 0 or cfl > 0");
     cudaStream_t s = (cudaStream_t)stream;
-    if (m->d.precision == DG_PRECISION_MIXED && m->d.system == 0 && m->d.limiter != DG_LIMITER_MRS)
+    if (m->d.precision == DG_PRECISION_MIXED && m->d.system == 0 && m->d.limiter != DG_LIMITER_MRS) {
+        if (reinterpret_cast<uintptr_t>(U) & 15u)
+            return fail(DG_ERR_ARG, "the mixed Newtonian path needs U 16-byte aligned");
         return rk3_step_ne(m, U, dt, cfl, dt_used, troubled, s);
+    }
     if (m->d.precision == DG_PRECISION_MIXED) return rk3_step_mixed(m, U, dt, cfl, dt_used, troubled, s);
     const bool sr = m->d.system == 1;
     const bool lim = m->d.limiter != 0;

@@ -386,6 +386,8 @@ dg_status dg_ensemble_create(dg_mesh *const *meshes, double *const *U, int count
         if (meshes[i]->gh.mask) return set_error(DG_ERR_ARG, "the ensemble advances periodic meshes only");
         if (meshes[i]->d.limiter == DG_LIMITER_MRS)
             return set_error(DG_ERR_ARG, "the ensemble runs the minmod limiters only, not the moment limiter");
+        if (meshes[i]->d.system == 0 && (reinterpret_cast<uintptr_t>(U[i]) & 15u))
+            return set_error(DG_ERR_ARG, "the mixed Newtonian path needs U 16-byte aligned");
         for (int j = 0; j < i; ++j)
             if (meshes[j] == meshes[i] || U[j] == U[i]) return set_error(DG_ERR_ARG, "meshes and states must be distinct");
     }

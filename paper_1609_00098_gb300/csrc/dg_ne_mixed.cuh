@@ -102,8 +102,16 @@ struct NeShape {
     static constexpr int F_H = R4(5 * NN);
     static constexpr int F_F = F_H;
     static constexpr int F_L = F_H + HF + (SN_NEED > HF + 20 * L ? R4(SN_NEED - (HF + 20 * L)) : 0);
-    static constexpr int ELEM_FLOATS = F_L + R4(20 * L);
+    // stages 2, 3: the element's U^n (FP64) lands by one bulk copy at F_H, over the
+    // halo, flux and lift arrays (free until phase 1 has read it), its difference by
+    // another over U; the copies move whole elements, 16-byte multiples for even NP
+    static constexpr bool STAGE = NP % 2 == 0;
+    static constexpr int F_S = F_H;
+    static constexpr int ELEM_BASE = F_L + R4(20 * L);
+    static constexpr int ELEM_FLOATS = STAGE && F_S + 10 * NN > ELEM_BASE ? F_S + 10 * NN : ELEM_BASE;
     static_assert(SD_NEED <= F_L, "output-summary scratch must fit in U + HF");
+    static_assert(!STAGE || (40 * NN) % 16 == 0 && (ELEM_FLOATS * 4) % 16 == 0 && (F_S * 4) % 16 == 0,
+                  "bulk copies need 16-byte sizes and addresses");
     static constexpr size_t SMEM = sizeof(float) * (size_t)ELEM_FLOATS * EPB;
 };
 
@@ -148,6 +156,7 @@ struct NeSlot {
     double *SN;                // stage 1 with a limiter: S(U^n) [e][5][10] (FP64), else nullptr
     float *SD;                 // with a limiter: S of Dout [e][5][10] (FP32), else nullptr
     unsigned long long *lam;   // stage 1 with CFL: max wave speed (bits of a double), else nullptr
+    unsigned int *err;         // the mesh's sticky status word (ERRBIT_TIMEOUT)
     const double *dt_ptr;      // device dt, or nullptr (host dt)
     double dt;
     int K[3];
@@ -329,6 +338,50 @@ __device__ __forceinline__ void ne_ld_line(const float *p, float v[NP])
     }
 }
 
+// One-shot transaction barrier in shared memory for the element's bulk copies: one
+// thread initialises it (arrival count `count`), issues the copies, each with its
+// byte count, and arrives; every thread of the element polls its first phase.
+__device__ __forceinline__ void ne_bar_init(uint64_t *bar, unsigned count)
+{
+    const uint32_t b = (uint32_t)__cvta_generic_to_shared(bar);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(b), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void ne_bulk_load(void *dst, const void *src, unsigned bytes, uint64_t *bar)
+{
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    const uint32_t b = (uint32_t)__cvta_generic_to_shared(bar);
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(b),
+                 "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(d),
+                 "l"(src), "r"(bytes), "r"(b)
+                 : "memory");
+}
+
+__device__ __forceinline__ void ne_bar_arrive(uint64_t *bar)
+{
+    const uint32_t b = (uint32_t)__cvta_generic_to_shared(bar);
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(b) : "memory");
+}
+
+// Poll the first phase at most `limit` times; false if it has not completed.
+__device__ __forceinline__ bool ne_bar_wait(uint64_t *bar, int limit)
+{
+    const uint32_t b = (uint32_t)__cvta_generic_to_shared(bar);
+    for (int i = 0; i < limit; ++i) {
+        uint32_t ok;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(ok)
+                     : "r"(b)
+                     : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+constexpr int NE_COPY_POLLS = 1 << 20;
+
 // Bulk prefetch of [p, p + bytes) into L2 (a hint: no data reaches the SM).  The
 // range is shrunk to 16-byte boundaries so that nothing outside it is touched.
 __device__ __forceinline__ void ne_prefetch_l2(const void *p, unsigned long long bytes)
@@ -421,6 +474,7 @@ __global__ void __launch_bounds__(NeShape<NP>::THREADS, NeShape<NP>::MINB) k_ne_
     __shared__ float4 sNbSH[EPB][6][5];  // the neighbours' replacement parameters (limited variables)
     __shared__ NeSlot sSlot[EPB];
     __shared__ long long sLoc[EPB];
+    __shared__ uint64_t sBar[EPB];  // the element's bulk copies (stages 2, 3, even NP)
 
     const int t = threadIdx.x;
     const int sub_raw = t / L, ln = t % L, j = ln % NP, k = ln / NP;
@@ -452,15 +506,29 @@ __global__ void __launch_bounds__(NeShape<NP>::THREADS, NeShape<NP>::MINB) k_ne_
     const float xj = a.x[j], xk = a.x[k];
 
     if (t < EPB) sLamE[t] = 0u;
-    // the element's U^n (and below, the difference of its variables that are not
-    // limited) on its way to L2 while the neighbour tables are built: phase 1's
-    // loads then wait on L2, not on DRAM
-    if (live && ln == L - 1) ne_prefetch_l2(sl.Un + e * 5 * NN, sizeof(double) * 5 * NN);
+    // (U^n and the differences are 16-byte aligned: the library allocates the
+    // differences, and its entry points refuse a caller's U that is not)
+    constexpr bool STAGED = ST >= 2 && SH::STAGE;
+    if (live && ln == L - 1) {
+        if (STAGED) {
+            // stages 2, 3: the element's U^n and, unless every variable is limited,
+            // its difference, into shared memory by two bulk copies that run while
+            // the neighbour tables are built
+            ne_bar_init(&sBar[sub], 2);
+            ne_bulk_load(eb + SH::F_S, sl.Un + e * 5 * NN, 40u * NN, &sBar[sub]);
+            const unsigned mo = lim_in ? sl.mask[e] : 0u;
+            if (mo != 0x1fu) ne_bulk_load(eb + SH::F_U, sl.Din + e * 5 * NN, 20u * NN, &sBar[sub]);
+            else ne_bar_arrive(&sBar[sub]);
+        } else {
+            // the element's U^n on its way to L2 while the neighbour tables are built
+            ne_prefetch_l2(sl.Un + e * 5 * NN, sizeof(double) * 5 * NN);
+        }
+    }
     for (int q = ln; live && q < 7; q += L) {
         if (q == 6) {
             const unsigned mo = lim_in ? sl.mask[e] : 0u;
             sMask[sub][0] = mo;
-            if (ST >= 2 && mo != 0x1fu) ne_prefetch_l2(sl.Din + e * 5 * NN, sizeof(float) * 5 * NN);
+            if (ST >= 2 && !STAGED && mo != 0x1fu) ne_prefetch_l2(sl.Din + e * 5 * NN, sizeof(float) * 5 * NN);
         } else {
             const int ax = q >> 1, side = q & 1;
             const long long en = elem_neighbour_bc(e, sl.K, ax, side ? 1 : -1, sl.gh);
@@ -483,13 +551,26 @@ __global__ void __launch_bounds__(NeShape<NP>::THREADS, NeShape<NP>::MINB) k_ne_
     // stage 1 with a limiter: line partials of S(U^n) on U^n - c (c = the element's
     // node-0 value rounded to FP32), as double-float pairs where the limiter's
     // tests need them (L0 and the end values), FP32 for L1
+    if (STAGED && live && !ne_bar_wait(&sBar[sub], NE_COPY_POLLS)) {
+        // flag it, and give the copies one more bounded wait before their regions are reused
+        atomicOr(sl.err, ERRBIT_TIMEOUT);
+        ne_bar_wait(&sBar[sub], NE_COPY_POLLS);
+    }
     float d[5][NP];
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
         float uv[NP];
         const long long base = (e * 5 + v) * NN + (long long)ln * NP;
         double un[NP];
-        if (live) {
+        if (live && STAGED) {
+            const double2 *p2 = reinterpret_cast<const double2 *>(eb + SH::F_S) + (v * NN + ln * NP) / 2;
+#pragma unroll
+            for (int h = 0; h < NP / 2; ++h) {
+                const double2 q = p2[h];
+                un[2 * h] = q.x;
+                un[2 * h + 1] = q.y;
+            }
+        } else if (live) {
             if (NP % 2 == 0) {
                 const double2 *p2 = reinterpret_cast<const double2 *>(sl.Un + base);
 #pragma unroll
@@ -549,7 +630,8 @@ __global__ void __launch_bounds__(NeShape<NP>::THREADS, NeShape<NP>::MINB) k_ne_
             }
         } else if (ST >= 2) {
             float dv[NP];
-            const float *src = sl.Din + base;
+            // staged: the difference sits where this line's stage state goes
+            const float *src = STAGED ? sU + v * NN + ln * NP : sl.Din + base;
             if (live) {
                 if (NP % 2 == 0) {
                     const float2 *p2 = reinterpret_cast<const float2 *>(src);

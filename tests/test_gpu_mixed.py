@@ -178,6 +178,31 @@ def test_mixed_ne_difference_form(pkg, n, flux, limiter, K):
         assert np.all(tg.cpu().numpy() == 0x1f) and np.all(to == 0x1f)  # MinMod limits every variable
 
 
+def test_mixed_ne_state_not_16_byte_aligned_is_refused(pkg):
+    """The mixed Newtonian kernels move the FP64 state in 16-byte pieces (vector
+    loads and stores, bulk copies into shared memory), so a caller's U that starts
+    8 bytes past a 16-byte boundary is refused with DG_ERR_ARG before anything is
+    launched; the same state at an aligned address steps normally."""
+    import torch
+    kw = dict(lo=(-0.5,) * 3, hi=(0.5,) * 3, gamma=5 / 3)
+    om, gm = _pair(pkg, 0, (4, 3, 2), 6, 1, 1, **kw)
+    U0 = om.from_prim(di.kh_ne(om.coords(), seed=5))
+    buf = torch.empty(U0.size + 1, dtype=torch.float64, device="cuda")
+    Ub = buf[1:].view(U0.shape)
+    Ub.copy_(_gpu(U0))
+    assert Ub.data_ptr() % 16 == 8
+    h = om.cfl_dt(U0, 0.2)
+    for call in (lambda: gm.rk3_step(Ub, dt=h), lambda: gm.rhs(Ub)):
+        with pytest.raises(pkg.abi.DGError) as ei:
+            call()
+        assert ei.value.status == pkg.abi.DG_ERR_ARG
+    with pytest.raises(pkg.abi.DGError):
+        pkg.abi.dg_ensemble_create([gm.h], [Ub])
+    Ua = _gpu(U0)
+    gm.rk3_step(Ua, dt=h)
+    assert gm.sync_status() == 0
+
+
 def test_mixed_conservation(pkg):
     """FP64 state: totals drift only by the FP32 rounding of the fluxes and of the
     stage increments (relative to the largest total)."""
