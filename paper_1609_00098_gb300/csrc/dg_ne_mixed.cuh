@@ -486,10 +486,15 @@ __global__ void __launch_bounds__(NeShape<NP>::THREADS, NeShape<NP>::MINB) k_ne_
     // element: the first mesh's, so that per-slot settings, the same for all meshes
     // of a launch, are read consistently by every thread).  Single-mesh and batch
     // launches run this one code path, so they give the same bits.
-    if (sub_raw < EPB && ln == 0) {
+    if (sub_raw < EPB) {
+        // (the slot is copied word by word across the element's threads)
+        constexpr int W = (int)(sizeof(NeSlot) / sizeof(unsigned long long));
+        static_assert(sizeof(NeSlot) % sizeof(unsigned long long) == 0, "slot words");
         const int m = (a.slots && live) ? ne_find_slot(a.elem0, a.nslots, ge) : 0;
-        sSlot[sub] = a.slots ? a.slots[m] : a.one;
-        sLoc[sub] = live ? (a.slots ? ge - a.elem0[m] : ge) : 0;
+        const unsigned long long *src = reinterpret_cast<const unsigned long long *>(a.slots ? &a.slots[m] : &a.one);
+        unsigned long long *dst = reinterpret_cast<unsigned long long *>(&sSlot[sub]);
+        for (int w = ln; w < W; w += L) dst[w] = src[w];
+        if (ln == 0) sLoc[sub] = live ? (a.slots ? ge - a.elem0[m] : ge) : 0;
     }
     __syncthreads();
     const NeSlot &sl = sSlot[sub];
@@ -539,7 +544,7 @@ __global__ void __launch_bounds__(NeShape<NP>::THREADS, NeShape<NP>::MINB) k_ne_
     __syncthreads();
     const unsigned mask = live ? sMask[sub][0] : 0u;
     // the neighbours' replacement parameters, once per element (read in the halo
-    // staging, after the next barrier)
+    // staging, after the next barrier; their loads overlap the wait for the copies)
     for (int q = ln; lim_in && live && q < 30; q += L) {
         const int m = q / 5, v = q % 5;
         const long long en = sNb[sub][m];
