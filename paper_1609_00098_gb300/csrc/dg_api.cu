@@ -365,6 +365,9 @@ NeArgs ne_args(const dg_mesh *m)
     a.nelem = m->E;
     a.gamma = (float)m->d.gamma;
     for (int i = 0; i < MAXN * MAXN; ++i) a.D[i] = (float)m->T.D[i];
+    const int n = m->d.n;
+    for (int i = 0; i < n; ++i)
+        for (int l = 0; l < n; ++l) a.DT[l * n + i] = a.D[i * n + l];
     for (int i = 0; i < MAXN; ++i) {
         a.x[i] = (float)m->T.x[i];
         a.w[i] = (float)m->T.w[i];

@@ -174,6 +174,7 @@ struct NeArgs {
     float cb;                  // D_{s+1} = cb (D_s + dt R)
     float gamma;
     float D[MAXN * MAXN];      // differentiation matrix, D[i * NP + l]
+    alignas(8) float DT[MAXN * MAXN];  // its transpose, DT[l * NP + i] (node pairs as 64-bit words)
     float x[MAXN], w[MAXN], row1[MAXN];
     float wh[MAXN], wl[MAXN];  // LGL weights as FP32 pairs (w = wh + wl to ~2^-48)
 };
@@ -907,27 +908,71 @@ __global__ void __launch_bounds__(NeShape<NP>::THREADS, NeShape<NP>::MINB) k_ne_
             ne_st_line<NP>(bF + NN + ln * NP, fz);
         }
         float R[NP];
+        if constexpr (NP % 2 == 0) {
+            // node pairs (i, i + 1) in paired FP32 FMAs: the same per-node FMA chain
+            float2 s2[NP / 2];
 #pragma unroll
-        for (int i = 0; i < NP; ++i) {
-            float s = 0.0f;
+            for (int h = 0; h < NP / 2; ++h) s2[h] = make_float2(0.0f, 0.0f);
 #pragma unroll
-            for (int l = 0; l < NP; ++l) s = fmaf(a.D[i * NP + l], fx[l], s);
-            R[i] = -sl.g[0] * s;
+            for (int l = 0; l < NP; ++l) {
+                const float2 f2 = make_float2(fx[l], fx[l]);
+#pragma unroll
+                for (int h = 0; h < NP / 2; ++h)
+                    s2[h] = __ffma2_rn(*reinterpret_cast<const float2 *>(&a.DT[l * NP + 2 * h]), f2, s2[h]);
+            }
+#pragma unroll
+            for (int h = 0; h < NP / 2; ++h) {
+                R[2 * h] = -sl.g[0] * s2[h].x;
+                R[2 * h + 1] = -sl.g[0] * s2[h].y;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < NP; ++i) {
+                float s = 0.0f;
+#pragma unroll
+                for (int l = 0; l < NP; ++l) s = fmaf(a.D[i * NP + l], fx[l], s);
+                R[i] = -sl.g[0] * s;
+            }
         }
         __syncthreads();
         if (live) {
             float sy[NP], sz[NP];
+            if constexpr (NP % 2 == 0) {
+                // node pairs in paired FP32 FMAs, straight from the 64-bit line loads
+                float2 sy2[NP / 2], sz2[NP / 2];
 #pragma unroll
-            for (int i = 0; i < NP; ++i) sy[i] = sz[i] = 0.0f;
+                for (int h = 0; h < NP / 2; ++h) sy2[h] = sz2[h] = make_float2(0.0f, 0.0f);
 #pragma unroll
-            for (int l = 0; l < NP; ++l) {
-                float gy[NP], gz[NP];
-                ne_ld_line<NP>(bF + NP * (l + NP * k), gy);       // F^y(., l, k)
-                ne_ld_line<NP>(bF + NN + NP * (j + NP * l), gz);  // F^z(., j, l)
+                for (int l = 0; l < NP; ++l) {
+                    const float2 *gy2 = reinterpret_cast<const float2 *>(bF + NP * (l + NP * k));       // F^y(., l, k)
+                    const float2 *gz2 = reinterpret_cast<const float2 *>(bF + NN + NP * (j + NP * l));  // F^z(., j, l)
+                    const float2 dj2 = make_float2(Dj[l], Dj[l]), dk2 = make_float2(Dk[l], Dk[l]);
 #pragma unroll
-                for (int i = 0; i < NP; ++i) {
-                    sy[i] = fmaf(Dj[l], gy[i], sy[i]);
-                    sz[i] = fmaf(Dk[l], gz[i], sz[i]);
+                    for (int h = 0; h < NP / 2; ++h) {
+                        sy2[h] = __ffma2_rn(dj2, gy2[h], sy2[h]);
+                        sz2[h] = __ffma2_rn(dk2, gz2[h], sz2[h]);
+                    }
+                }
+#pragma unroll
+                for (int h = 0; h < NP / 2; ++h) {
+                    sy[2 * h] = sy2[h].x;
+                    sy[2 * h + 1] = sy2[h].y;
+                    sz[2 * h] = sz2[h].x;
+                    sz[2 * h + 1] = sz2[h].y;
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < NP; ++i) sy[i] = sz[i] = 0.0f;
+#pragma unroll
+                for (int l = 0; l < NP; ++l) {
+                    float gy[NP], gz[NP];
+                    ne_ld_line<NP>(bF + NP * (l + NP * k), gy);       // F^y(., l, k)
+                    ne_ld_line<NP>(bF + NN + NP * (j + NP * l), gz);  // F^z(., j, l)
+#pragma unroll
+                    for (int i = 0; i < NP; ++i) {
+                        sy[i] = fmaf(Dj[l], gy[i], sy[i]);
+                        sz[i] = fmaf(Dk[l], gz[i], sz[i]);
+                    }
                 }
             }
 #pragma unroll
