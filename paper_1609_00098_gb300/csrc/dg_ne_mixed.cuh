@@ -476,6 +476,11 @@ __global__ void __launch_bounds__(NeShape<NP>::THREADS, NeShape<NP>::MINB) k_ne_
     __shared__ NeSlot sSlot[EPB];
     __shared__ long long sLoc[EPB];
     __shared__ uint64_t sBar[EPB];  // the element's bulk copies (stages 2, 3, even NP)
+    __shared__ float4 sOwnSH[EPB][5];  // the element's own replacement parameters (staged stages)
+    __shared__ double sOwnM0[EPB][5];
+    // (U^n and the differences are 16-byte aligned: the library allocates the
+    // differences, and its entry points refuse a caller's U that is not)
+    constexpr bool STAGED = ST >= 2 && SH::STAGE;
 
     const int t = threadIdx.x;
     const int sub_raw = t / L, ln = t % L, j = ln % NP, k = ln / NP;
@@ -496,6 +501,8 @@ __global__ void __launch_bounds__(NeShape<NP>::THREADS, NeShape<NP>::MINB) k_ne_
         unsigned long long *dst = reinterpret_cast<unsigned long long *>(&sSlot[sub]);
         for (int w = ln; w < W; w += L) dst[w] = src[w];
         if (ln == 0) sLoc[sub] = live ? (a.slots ? ge - a.elem0[m] : ge) : 0;
+        // nine arrivals: three from the staging thread, one per neighbour
+        if (STAGED && ln == L - 1) ne_bar_init(&sBar[sub], 9);
     }
     __syncthreads();
     const NeSlot &sl = sSlot[sub];
@@ -512,17 +519,20 @@ __global__ void __launch_bounds__(NeShape<NP>::THREADS, NeShape<NP>::MINB) k_ne_
     const float xj = a.x[j], xk = a.x[k];
 
     if (t < EPB) sLamE[t] = 0u;
-    // (U^n and the differences are 16-byte aligned: the library allocates the
-    // differences, and its entry points refuse a caller's U that is not)
-    constexpr bool STAGED = ST >= 2 && SH::STAGE;
     if (live && ln == L - 1) {
         if (STAGED) {
-            // stages 2, 3: the element's U^n and, unless every variable is limited,
-            // its difference, into shared memory by two bulk copies that run while
-            // the neighbour tables are built
-            ne_bar_init(&sBar[sub], 2);
+            // stages 2, 3: the element's U^n, its own replacement parameters and,
+            // unless every variable is limited, its difference, into shared memory
+            // by bulk copies that run while the neighbour tables are built; the
+            // means U0 (40 bytes, not a bulk-copy size) by plain loads before the
+            // last arrival, which publishes them
             ne_bulk_load(eb + SH::F_S, sl.Un + e * 5 * NN, 40u * NN, &sBar[sub]);
+            if (lim_in) ne_bulk_load(&sOwnSH[sub][0], sl.SH + e * 5, 5u * sizeof(float4), &sBar[sub]);
+            else ne_bar_arrive(&sBar[sub]);
             const unsigned mo = lim_in ? sl.mask[e] : 0u;
+            if (lim_in)
+#pragma unroll
+                for (int v = 0; v < 5; ++v) sOwnM0[sub][v] = sl.M0[e * 5 + v];
             if (mo != 0x1fu) ne_bulk_load(eb + SH::F_U, sl.Din + e * 5 * NN, 20u * NN, &sBar[sub]);
             else ne_bar_arrive(&sBar[sub]);
         } else {
@@ -539,6 +549,12 @@ __global__ void __launch_bounds__(NeShape<NP>::THREADS, NeShape<NP>::MINB) k_ne_
             const int ax = q >> 1, side = q & 1;
             const long long en = elem_neighbour_bc(e, sl.K, ax, side ? 1 : -1, sl.gh);
             sNb[sub][q] = en;
+            if (STAGED) {
+                // the neighbour's replacement parameters (all five; the masks say
+                // which are read) on the element's barrier
+                if (lim_in && en >= 0) ne_bulk_load(&sNbSH[sub][q][0], sl.SH + en * 5, 5u * sizeof(float4), &sBar[sub]);
+                else ne_bar_arrive(&sBar[sub]);
+            }
             sMask[sub][1 + q] = (lim_in && en >= 0) ? sl.mask[en] : 0u;
         }
     }
@@ -546,7 +562,7 @@ __global__ void __launch_bounds__(NeShape<NP>::THREADS, NeShape<NP>::MINB) k_ne_
     const unsigned mask = live ? sMask[sub][0] : 0u;
     // the neighbours' replacement parameters, once per element (read in the halo
     // staging, after the next barrier; their loads overlap the wait for the copies)
-    for (int q = ln; lim_in && live && q < 30; q += L) {
+    for (int q = ln; !STAGED && lim_in && live && q < 30; q += L) {
         const int m = q / 5, v = q % 5;
         const long long en = sNb[sub][m];
         if (en >= 0 && ((sMask[sub][1 + m] >> v) & 1u)) sNbSH[sub][m][v] = sl.SH[en * 5 + v];
@@ -626,8 +642,8 @@ __global__ void __launch_bounds__(NeShape<NP>::THREADS, NeShape<NP>::MINB) k_ne_
         if (ST >= 2 && ((mask >> v) & 1u)) {
             // replaced: U^s = U0 + lin, so d = (U0 - U^n) + lin with U0 - U^n in FP64
             // (the FP64 pipe is otherwise idle here), rounded once to FP32
-            const float4 sh = sl.SH[e * 5 + v];
-            const double m0 = sl.M0[e * 5 + v];
+            const float4 sh = STAGED ? sOwnSH[sub][v] : sl.SH[e * 5 + v];
+            const double m0 = STAGED ? sOwnM0[sub][v] : sl.M0[e * 5 + v];
 #pragma unroll
             for (int i = 0; i < NP; ++i) {
                 const float lin = ne_lin(sh, a.x[i], xj, xk);
