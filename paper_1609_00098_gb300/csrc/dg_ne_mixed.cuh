@@ -470,7 +470,7 @@ __global__ void __launch_bounds__(NeShape<NP>::THREADS, NeShape<NP>::MINB) k_ne_
     constexpr int L = SH::L, NN = SH::NN, EPB = SH::EPB, N1 = NP - 1;
     extern __shared__ __align__(16) float ne_smem[];
     __shared__ long long sNb[EPB][6];
-    __shared__ unsigned sMask[EPB][7];  // own (0) and neighbours' (1 + 2 ax + side) limited variables
+    __shared__ unsigned sMask[EPB][7];  // neighbours' limited variables (1 + 2 ax + side)
     __shared__ unsigned sLamE[EPB];  // per element: max wave speed (bits of a non-negative float)
     __shared__ float4 sNbSH[EPB][6][5];  // the neighbours' replacement parameters (limited variables)
     __shared__ NeSlot sSlot[EPB];
@@ -504,6 +504,7 @@ __global__ void __launch_bounds__(NeShape<NP>::THREADS, NeShape<NP>::MINB) k_ne_
         // nine arrivals: three from the staging thread, one per neighbour
         if (STAGED && ln == L - 1) ne_bar_init(&sBar[sub], 9);
     }
+    if (t < EPB) sLamE[t] = 0u;
     __syncthreads();
     const NeSlot &sl = sSlot[sub];
     const long long e = sLoc[sub];                              // element index within its mesh
@@ -518,7 +519,6 @@ __global__ void __launch_bounds__(NeShape<NP>::THREADS, NeShape<NP>::MINB) k_ne_
     const float dtf = (ST >= 2 && live) ? (float)(sl.dt_ptr ? *sl.dt_ptr : sl.dt) : 0.0f;
     const float xj = a.x[j], xk = a.x[k];
 
-    if (t < EPB) sLamE[t] = 0u;
     if (live && ln == L - 1) {
         if (STAGED) {
             // stages 2, 3: the element's U^n, its own replacement parameters and,
@@ -540,11 +540,13 @@ __global__ void __launch_bounds__(NeShape<NP>::THREADS, NeShape<NP>::MINB) k_ne_
             ne_prefetch_l2(sl.Un + e * 5 * NN, sizeof(double) * 5 * NN);
         }
     }
+    // The neighbour table and masks are read in the halo staging, after the barrier
+    // that ends phase 1; phase 1 itself needs only the element's own mask, which
+    // every thread loads (staged stages: while the copies are in flight).
     for (int q = ln; live && q < 7; q += L) {
         if (q == 6) {
-            const unsigned mo = lim_in ? sl.mask[e] : 0u;
-            sMask[sub][0] = mo;
-            if (ST >= 2 && !STAGED && mo != 0x1fu) ne_prefetch_l2(sl.Din + e * 5 * NN, sizeof(float) * 5 * NN);
+            if (ST >= 2 && !STAGED && lim_in && sl.mask[e] != 0x1fu)
+                ne_prefetch_l2(sl.Din + e * 5 * NN, sizeof(float) * 5 * NN);
         } else {
             const int ax = q >> 1, side = q & 1;
             const long long en = elem_neighbour_bc(e, sl.K, ax, side ? 1 : -1, sl.gh);
@@ -558,10 +560,10 @@ __global__ void __launch_bounds__(NeShape<NP>::THREADS, NeShape<NP>::MINB) k_ne_
             sMask[sub][1 + q] = (lim_in && en >= 0) ? sl.mask[en] : 0u;
         }
     }
-    __syncthreads();
-    const unsigned mask = live ? sMask[sub][0] : 0u;
+    const unsigned mask = (live && lim_in) ? sl.mask[e] : 0u;
+    if (!STAGED) __syncthreads();  // the loop below reads the neighbour table
     // the neighbours' replacement parameters, once per element (read in the halo
-    // staging, after the next barrier; their loads overlap the wait for the copies)
+    // staging, after the next barrier)
     for (int q = ln; !STAGED && lim_in && live && q < 30; q += L) {
         const int m = q / 5, v = q % 5;
         const long long en = sNb[sub][m];
