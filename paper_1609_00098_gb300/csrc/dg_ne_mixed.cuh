@@ -580,6 +580,11 @@ __global__ void __launch_bounds__(NeShape<NP>::THREADS, NeShape<NP>::MINB) k_ne_
         atomicOr(sl.err, ERRBIT_TIMEOUT);
         ne_bar_wait(&sBar[sub], NE_COPY_POLLS);
     }
+    // stage 1 with a limiter: the reference values c_v (node 0 of the element,
+    // rounded to FP32), all five loads at once
+    float cref[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) cref[v] = (do_sn && live) ? ne_hi(sl.Un[(e * 5 + v) * NN]) : 0.0f;
     float d[5][NP];
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
@@ -616,7 +621,7 @@ __global__ void __launch_bounds__(NeShape<NP>::THREADS, NeShape<NP>::MINB) k_ne_
 #pragma unroll
             for (int i = 0; i < NP; ++i) uh[i] = ne_hi(un[i]);
         if (do_sn) {
-            const float c = live ? ne_hi(sl.Un[(e * 5 + v) * NN]) : 0.0f;
+            const float c = cref[v];
             float ah[NP], al[NP];
 #pragma unroll
             for (int i = 0; i < NP; ++i) {
@@ -779,7 +784,8 @@ __global__ void __launch_bounds__(NeShape<NP>::THREADS, NeShape<NP>::MINB) k_ne_
                 }
                 h *= 0.25f;
             }
-            const double cv = ne_f32_to_f64(ne_hi(sl.Un[(e * 5 + v) * NN]));
+            const float cf = v == 0 ? cref[0] : v == 1 ? cref[1] : v == 2 ? cref[2] : v == 3 ? cref[3] : cref[4];
+            const double cv = ne_f32_to_f64(cf);
             sl.SN[e * 50 + o] = (kind <= 6 ? cv : 0.0) + (ne_f32_to_f64(h) + ne_f32_to_f64(l));
         }
         __syncthreads();  // the scratch overlaps the halo and face-lift arrays
