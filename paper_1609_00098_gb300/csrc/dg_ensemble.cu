@@ -324,9 +324,9 @@ cudaError_t group_stage(EnsGroup &g, bool first, int st, cudaStream_t s)
 // the groups.  concurrent: each group's phase runs on its own stream instead,
 // forked from and joined back to s by events (in a captured graph: parallel
 // branches), so that the groups' launches overlap.  Both orders give the same
-// bits: no data crosses groups.  (On the 256-mesh recipe the branches were 12 %
-// slower than the single chain: kernels of different groups then share SMs and
-// L2 and slow each other more than the chain's per-launch tails cost.)
+// bits: no data crosses groups.  (On the 256-mesh recipe the two orders run within
+// about 1 % of each other: the launches' tails that the branches overlap are a
+// small part of a step.)
 cudaError_t launch_step(dg_ensemble *en, double cfl, bool first, bool concurrent, cudaStream_t s)
 {
     const int count = (int)en->meshes.size();
