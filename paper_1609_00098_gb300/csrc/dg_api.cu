@@ -410,10 +410,10 @@ NeDecideSlot ne_decide_slot(const dg_mesh *m)
     sl.SH = m->ne_SH;
     for (int ax = 0; ax < 3; ++ax) {
         sl.K[ax] = m->d.K[ax];
-        sl.tvb[ax] = m->d.tvb_M * m->dx[ax] * m->dx[ax];
-        sl.inv_dx[ax] = 1.0 / m->dx[ax];
-        sl.beta_dx[ax] = m->d.beta / m->dx[ax];
-        sl.hdx[ax] = 0.5 * m->dx[ax];
+        sl.tvb_f[ax] = (float)(m->d.tvb_M * m->dx[ax] * m->dx[ax]);
+        sl.two_inv_dx_f[ax] = (float)(2.0 / m->dx[ax]);
+        sl.beta_dx_f[ax] = (float)(m->d.beta / m->dx[ax]);
+        sl.hdx_f[ax] = (float)(0.5 * m->dx[ax]);
     }
     return sl;
 }

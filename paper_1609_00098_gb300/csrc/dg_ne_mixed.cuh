@@ -192,8 +192,17 @@ struct NeDecideSlot {
     double *U;                 // final pass: U^{n+1} = U^n + D3 (in place), replaced where limited
     const float *D3;
     int K[3];
-    double tvb[3], inv_dx[3], beta_dx[3], hdx[3];
+    float tvb_f[3], two_inv_dx_f[3], beta_dx_f[3], hdx_f[3];  // M dx^2, 2/dx, beta/dx, dx/2
 };
+
+// minmod of three FP32 values: the one of least magnitude if all have one sign, else 0
+__device__ __forceinline__ float ne_minmod3f(float a1, float a2, float a3)
+{
+    const bool pos = (a1 > 0.0f) & (a2 > 0.0f) & (a3 > 0.0f);
+    const bool neg = (a1 < 0.0f) & (a2 < 0.0f) & (a3 < 0.0f);
+    const float m = fminf(fabsf(a1), fminf(fabsf(a2), fabsf(a3)));
+    return pos ? m : neg ? -m : 0.0f;
+}
 
 // Per-launch arguments of the decision pass.
 struct NeDecideArgs {
@@ -1125,7 +1134,8 @@ __global__ void __launch_bounds__(128) k_ne_decide(const __grid_constant__ NeDec
     const long long e = live ? (a.slots ? ge - a.elem0[slot] : ge) : 0;
     const double c = a.scale_dt ? (sl.dt_ptr ? *sl.dt_ptr : sl.dt) : 1.0;
     int flag = 0;
-    double slope = 0.0, U0 = 0.0;
+    double U0 = 0.0;
+    float shl = 0.0f;
     if (live && h < 15 && a.limiter) {
         const int v = h / 3, ax = h % 3;
         auto S = [&](long long el, int kind) {
@@ -1135,15 +1145,23 @@ __global__ void __launch_bounds__(128) k_ne_decide(const __grid_constant__ NeDec
         U0 = S(e, 0);
         const double U0m = S(elem_neighbour(e, sl.K, ax, -1), 0);
         const double U0p = S(elem_neighbour(e, sl.K, ax, +1), 0);
+        const double dm = U0 - U0m, dp = U0p - U0;
         flag = a.limiter == 2;
         if (a.limiter == 1) {
+            // the face tests in FP64 (tolerance 1e-8 on O(U) values)
             const double ulo = S(e, 1 + 2 * ax), uhi = S(e, 2 + 2 * ax);
-            const double vl = U0 - minmod3_bits(U0 - ulo, U0 - U0m, U0p - U0);
-            const double vr = U0 + minmod3_bits(uhi - U0, U0 - U0m, U0p - U0);
+            const double vl = U0 - minmod3_bits(U0 - ulo, dm, dp);
+            const double vr = U0 + minmod3_bits(uhi - U0, dm, dp);
             if (abs_gt(vl - ulo, 1e-8) || abs_gt(vr - uhi, 1e-8)) flag = 1;
         }
-        const double s1 = 2.0 * S(e, 7 + ax) * sl.inv_dx[ax];
-        slope = abs_le(s1, sl.tvb[ax]) ? s1 : minmod3_bits(s1, (U0p - U0) * sl.beta_dx[ax], (U0 - U0m) * sl.beta_dx[ax]);
+        // the slope candidates of eq:MinModB from their FP64 differences, rounded to
+        // FP32 (the replacement's slopes are FP32): the products and the pick on the
+        // FP32 pipe
+        const float s1 = ne_hi(S(e, 7 + ax)) * sl.two_inv_dx_f[ax];
+        const float slope = fabsf(s1) <= sl.tvb_f[ax]
+                                ? s1
+                                : ne_minmod3f(s1, ne_hi(dp) * sl.beta_dx_f[ax], ne_hi(dm) * sl.beta_dx_f[ax]);
+        shl = slope * sl.hdx_f[ax];
     }
     const unsigned fb = (__ballot_sync(0xffffffffu, flag) >> (16 * half)) & 0x7fffu;
     unsigned mask = 0;
@@ -1151,7 +1169,6 @@ __global__ void __launch_bounds__(128) k_ne_decide(const __grid_constant__ NeDec
     for (int v = 0; v < 5; ++v)
         if ((fb >> (3 * v)) & 7u) mask |= 1u << v;
     // replacement parameters: lane 3 v of the half gathers the slopes of v
-    const float shl = ne_hi(slope * sl.hdx[h % 3]);
     const float s1v = __shfl_down_sync(0xffffffffu, shl, 1);
     const float s2v = __shfl_down_sync(0xffffffffu, shl, 2);
     if (live && a.limiter) {
