@@ -1149,10 +1149,10 @@ __global__ void __launch_bounds__(128) k_ne_decide(const __grid_constant__ NeDec
         flag = a.limiter == 2;
         if (a.limiter == 1) {
             // the face tests in FP64 (tolerance 1e-8 on O(U) values)
-            const double ulo = S(e, 1 + 2 * ax), uhi = S(e, 2 + 2 * ax);
-            const double vl = U0 - minmod3_bits(U0 - ulo, dm, dp);
-            const double vr = U0 + minmod3_bits(uhi - U0, dm, dp);
-            if (abs_gt(vl - ulo, 1e-8) || abs_gt(vr - uhi, 1e-8)) flag = 1;
+            // (|U0 - m - ulo| with a = U0 - ulo is |a - minmod(a, ...)|: zero when the
+            // minmod keeps a, one FP64 difference otherwise; likewise at the upper face)
+            const double al = U0 - S(e, 1 + 2 * ax), au = S(e, 2 + 2 * ax) - U0;
+            if (abs_gt(al - minmod3_bits(al, dm, dp), 1e-8) || abs_gt(au - minmod3_bits(au, dm, dp), 1e-8)) flag = 1;
         }
         // the slope candidates of eq:MinModB from their FP64 differences, rounded to
         // FP32 (the replacement's slopes are FP32): the products and the pick on the
