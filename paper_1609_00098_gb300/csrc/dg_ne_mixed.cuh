@@ -489,7 +489,7 @@ __global__ void __launch_bounds__(NeShape<NP>::THREADS, NeShape<NP>::MINB) k_ne_
     __shared__ double sOwnM0[EPB][5];
     // (U^n and the differences are 16-byte aligned: the library allocates the
     // differences, and its entry points refuse a caller's U that is not)
-    constexpr bool STAGED = ST >= 2 && SH::STAGE;
+    constexpr bool STAGED = ST >= 1 && SH::STAGE;
 
     const int t = threadIdx.x;
     const int sub_raw = t / L, ln = t % L, j = ln % NP, k = ln / NP;
@@ -542,7 +542,7 @@ __global__ void __launch_bounds__(NeShape<NP>::THREADS, NeShape<NP>::MINB) k_ne_
             if (lim_in)
 #pragma unroll
                 for (int v = 0; v < 5; ++v) sOwnM0[sub][v] = sl.M0[e * 5 + v];
-            if (mo != 0x1fu) ne_bulk_load(eb + SH::F_U, sl.Din + e * 5 * NN, 20u * NN, &sBar[sub]);
+            if (ST >= 2 && mo != 0x1fu) ne_bulk_load(eb + SH::F_U, sl.Din + e * 5 * NN, 20u * NN, &sBar[sub]);
             else ne_bar_arrive(&sBar[sub]);
         } else {
             // the element's U^n on its way to L2 while the neighbour tables are built
@@ -593,7 +593,13 @@ __global__ void __launch_bounds__(NeShape<NP>::THREADS, NeShape<NP>::MINB) k_ne_
     // rounded to FP32), all five loads at once
     float cref[5];
 #pragma unroll
-    for (int v = 0; v < 5; ++v) cref[v] = (do_sn && live) ? ne_hi(sl.Un[(e * 5 + v) * NN]) : 0.0f;
+    for (int v = 0; v < 5; ++v)
+        cref[v] = (do_sn && live) ? ne_hi(STAGED ? reinterpret_cast<const double *>(eb + SH::F_S)[v * NN]
+                                                 : sl.Un[(e * 5 + v) * NN])
+                                  : 0.0f;
+    // staged stage 1: the S(U^n) line partials wait in registers until every line
+    // has read its U^n (their scratch lies over the staged copy)
+    float snp[STAGED && ST == 1 ? 5 : 1][7];
     float d[5][NP];
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
@@ -644,7 +650,16 @@ __global__ void __launch_bounds__(NeShape<NP>::THREADS, NeShape<NP>::MINB) k_ne_
                 ne_df_fma(l0h, l0l, a.wh[i], a.wl[i], ah[i], al[i]);
                 l1 = fmaf(a.row1[i], ah[i] + al[i], l1);
             }
-            if (live) {
+            if (STAGED) {
+                float *q = snp[STAGED && ST == 1 ? v : 0];
+                q[0] = l0h;
+                q[1] = l0l;
+                q[2] = l1;
+                q[3] = ah[0];
+                q[4] = al[0];
+                q[5] = ah[N1];
+                q[6] = al[N1];
+            } else if (live) {
                 float *P = sF + v * 7 * L + ln;
                 P[0 * L] = l0h;
                 P[1 * L] = l0l;
@@ -736,6 +751,14 @@ __global__ void __launch_bounds__(NeShape<NP>::THREADS, NeShape<NP>::MINB) k_ne_
 
     // ---- S(U^n) (stage 1 with a limiter), second pass: per (v, k) sums over j
     float *const sQn = sF + 35 * L;  // [5][NP][12]
+    if (STAGED && ST == 1 && do_sn) {
+        if (live)
+#pragma unroll
+            for (int v = 0; v < 5; ++v)
+#pragma unroll
+                for (int q = 0; q < 7; ++q) sF[v * 7 * L + q * L + ln] = snp[STAGED && ST == 1 ? v : 0][q];
+        __syncthreads();
+    }
     if (do_sn) {
         for (int r = ln; live && r < 5 * NP; r += L) {
             const int v = r / NP, kk = r % NP;
