@@ -45,10 +45,10 @@ BLAST = dict(system=1, K=(16, 16, 16), n=5, flux=1, limiter=1, gamma=4.0 / 3.0, 
 KH_SAMPLE_K = (16, 16, 16)   # the CPU oracle's bounded sample of the KH workload
 METRIC = "DG-RK3 dof-updates/s on 1 GB300: plain FP64 vs mixed+learned at equal L2 error"
 UNIT = "dof-updates/s"
-# Compulsory HBM bytes per node of one stage launch as the survey's roofline model
+# Compulsory HBM bytes per node of one stage launch in the FP64-state roofline model
 # counts them (FP64 stage states): stage 1 reads U^n and writes U^1 (80 B), stages 2
 # and 3 read U_s and U^n and write U_{s+1} (120 B each): 320 B per node-step.
-SURVEY_BYTES_PER_NODE_STAGE = (80.0 + 120.0 + 120.0) / 3.0
+FP64_STATE_BYTES_PER_NODE_STAGE = (80.0 + 120.0 + 120.0) / 3.0
 
 
 def _nodes(w):
@@ -533,7 +533,7 @@ def _hbm_peak():
 
 
 def _ensemble_roofline(nodes, ms_per_step):
-    """Whole-step HBM roofline of the batched ensemble: the survey's 64 B per
+    """Whole-step HBM roofline of the batched ensemble: the FP64-state model's 64 B per
     dof-update (320 B per node-step) over the graph-timed step."""
     peak, src = _hbm_peak()
     achieved = 320.0 * nodes / (ms_per_step / 1e3) / 1e9
@@ -733,7 +733,7 @@ def _headline(pkg, torch, args, ws, local, dist):
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     st_ms, st_n = prof["stage"]
     stage_avg_s = (st_ms / st_n) / 1e3
-    bytes_8d = SURVEY_BYTES_PER_NODE_STAGE * nodes
+    bytes_8d = FP64_STATE_BYTES_PER_NODE_STAGE * nodes
     bytes_design = _design_bytes_per_node_stage(True) * nodes
     achieved = bytes_8d / stage_avg_s / 1e9
     launches = int(sum(v[1] for v in prof.values()))
@@ -758,8 +758,8 @@ def _headline(pkg, torch, args, ws, local, dist):
         "roofline": {"kernel": "k_ne_stage (fused RHS of eq:411 + SSP-RK3 stage difference + limiter summaries)",
                      "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": _traffic(),
-                     "bytes_per_launch": bytes_8d, "bytes_per_node": SURVEY_BYTES_PER_NODE_STAGE,
-                     "bytes_rule": "survey roofline model: FP64 stage states, 320 B per node-step, mean 106.7 B per "
+                     "bytes_per_launch": bytes_8d, "bytes_per_node": FP64_STATE_BYTES_PER_NODE_STAGE,
+                     "bytes_rule": "FP64-state roofline model: FP64 stage states, 320 B per node-step, mean 106.7 B per "
                                    "node and stage launch",
                      "design_bytes_per_launch": bytes_design,
                      "design_frac": bytes_design / stage_avg_s / 1e9 / hbm_peak,
