@@ -45,9 +45,9 @@ BLAST = dict(system=1, K=(16, 16, 16), n=5, flux=1, limiter=1, gamma=4.0 / 3.0, 
 KH_SAMPLE_K = (16, 16, 16)   # the CPU oracle's bounded sample of the KH workload
 METRIC = "DG-RK3 dof-updates/s on 1 GB300: plain FP64 vs mixed+learned at equal L2 error"
 UNIT = "dof-updates/s"
-# Compulsory HBM bytes per node of one stage launch in the FP64-state roofline model
-# counts them (FP64 stage states): stage 1 reads U^n and writes U^1 (80 B), stages 2
-# and 3 read U_s and U^n and write U_{s+1} (120 B each): 320 B per node-step.
+# Compulsory HBM bytes per node of one stage launch in the roofline model with FP64
+# stage states: stage 1 reads U^n and writes U^1 (80 B), stages 2 and 3 read U_s and
+# U^n and write U_{s+1} (120 B each): 320 B per node-step, 64 B per dof-update.
 FP64_STATE_BYTES_PER_NODE_STAGE = (80.0 + 120.0 + 120.0) / 3.0
 
 
