@@ -1208,40 +1208,58 @@ __global__ void __launch_bounds__(128) k_ne_decide(const __grid_constant__ NeDec
         sl.troubled[e] = 0;
     }
     if (!FINAL) return;
-    // U^{n+1} of this element, 16 lanes, x-line by x-line: U^n + D3, or the replacement
-    __syncwarp();
-    float shx[5], shy[5], shz[5];
-    double m0v[5];
-#pragma unroll
-    for (int v = 0; v < 5; ++v) {
-        m0v[v] = __shfl_sync(0xffffffffu, U0, 16 * half + 3 * v);
-        shx[v] = __shfl_sync(0xffffffffu, shl, 16 * half + 3 * v);
-        shy[v] = __shfl_sync(0xffffffffu, s1v, 16 * half + 3 * v);
-        shz[v] = __shfl_sync(0xffffffffu, s2v, 16 * half + 3 * v);
+    // U^{n+1} of the warp's two elements: 2 x NP^2 x-lines x 5 variables, each
+    // (line, variable) a task of NP nodes, dealt to the 32 lanes in turn (U^n + D3,
+    // or the replacement); the FP64 pipe then runs with nearly all lanes busy
+    constexpr int TASKS = 2 * NP * NP * 5;
+    __shared__ double sM0[4][2][5];  // per warp of the CTA: the two elements' parameters
+    __shared__ float sSHp[4][2][5][3];
+    __shared__ unsigned sMk[4][2];
+    __shared__ long long sE[4][2];
+    __shared__ int sLive[4][2];
+    __shared__ double *sUp[4][2];      // the elements' meshes (a batch may mix meshes)
+    __shared__ const float *sD3p[4][2];
+    const int w = threadIdx.x >> 5;
+    if (h < 15 && h % 3 == 0) {
+        const int v = h / 3;
+        sM0[w][half][v] = U0;
+        sSHp[w][half][v][0] = shl;
+        sSHp[w][half][v][1] = s1v;
+        sSHp[w][half][v][2] = s2v;
     }
-    if (!live) return;
-    for (int ln = h; ln < NP * NP; ln += 16) {
-        const float xj = sx[ln % NP], xk = sx[ln / NP];
+    if (h == 0) {
+        sMk[w][half] = mask;
+        sE[w][half] = e;
+        sLive[w][half] = live ? 1 : 0;
+        sUp[w][half] = sl.U;
+        sD3p[w][half] = sl.D3;
+    }
+    __syncwarp();
+    for (int tk = lane; tk < TASKS; tk += 32) {
+        const int el = tk / (NP * NP * 5), rem = tk % (NP * NP * 5);
+        const int v = rem / (NP * NP), ln = rem % (NP * NP);  // consecutive lanes: consecutive lines
+        if (!sLive[w][el]) continue;
+        const long long base = (sE[w][el] * 5 + v) * NN + (long long)ln * NP;
+        double *const Ue = sUp[w][el];
+        const float *const D3e = sD3p[w][el];
+        double val[NP];
+        if ((sMk[w][el] >> v) & 1u) {
+            const float4 sh = make_float4(0.0f, sSHp[w][el][v][0], sSHp[w][el][v][1], sSHp[w][el][v][2]);
+            const float xj = sx[ln % NP], xk = sx[ln / NP];
+            const double m0 = sM0[w][el][v];
 #pragma unroll
-        for (int v = 0; v < 5; ++v) {
-            const long long base = (e * 5 + v) * NN + (long long)ln * NP;
-            double val[NP];
-            if ((mask >> v) & 1u) {
-                const float4 sh = make_float4(0.0f, shx[v], shy[v], shz[v]);
+            for (int i = 0; i < NP; ++i) val[i] = m0 + ne_f32_to_f64(ne_lin(sh, a.x[i], xj, xk));
+        } else {
 #pragma unroll
-                for (int i = 0; i < NP; ++i) val[i] = m0v[v] + ne_f32_to_f64(ne_lin(sh, a.x[i], xj, xk));
-            } else {
+            for (int i = 0; i < NP; ++i) val[i] = Ue[base + i] + ne_f32_to_f64(D3e[base + i]);
+        }
+        if (NP % 2 == 0) {
+            double2 *p2 = reinterpret_cast<double2 *>(Ue + base);
 #pragma unroll
-                for (int i = 0; i < NP; ++i) val[i] = sl.U[base + i] + ne_f32_to_f64(sl.D3[base + i]);
-            }
-            if (NP % 2 == 0) {
-                double2 *p2 = reinterpret_cast<double2 *>(sl.U + base);
+            for (int q = 0; q < NP / 2; ++q) p2[q] = make_double2(val[2 * q], val[2 * q + 1]);
+        } else {
 #pragma unroll
-                for (int q = 0; q < NP / 2; ++q) p2[q] = make_double2(val[2 * q], val[2 * q + 1]);
-            } else {
-#pragma unroll
-                for (int i = 0; i < NP; ++i) sl.U[base + i] = val[i];
-            }
+            for (int i = 0; i < NP; ++i) Ue[base + i] = val[i];
         }
     }
 }
