@@ -792,8 +792,10 @@ __global__ void __launch_bounds__(NeShape<NP>::THREADS, NeShape<NP>::MINB) k_ne_
     // third pass: the 50 summaries, the reference c added in FP64 (mean and face
     // means of a constant are the constant, its P1 coefficient is zero)
     if (do_sn) {
-        for (int o = ln; live && o < 50; o += L) {
-            const int v = o / 10, kind = o % 10;
+        // kind-major over the element's lines: the double-float kinds 0-4 all in the
+        // first round, and neighbouring lanes on the same kind
+        for (int t3 = ln; live && t3 < 50; t3 += L) {
+            const int kind = t3 / 5, v = t3 % 5, o = v * 10 + kind;
             const float *Q = sQn + v * NP * 12;
             float h = 0.0f, l = 0.0f;
             if (kind == 5 || kind == 6) {
