@@ -1126,8 +1126,8 @@ __global__ void __launch_bounds__(NeShape<NP>::THREADS, NeShape<NP>::MINB) k_ne_
         Q[6] = P[N1];
     }
     __syncthreads();
-    for (int o = ln; live && o < 50; o += L) {
-        const int v = o / 10, kind = o % 10;
+    for (int t3 = ln; live && t3 < 50; t3 += L) {  // kind-major: neighbouring lanes on one kind
+        const int kind = t3 / 5, v = t3 % 5, o = v * 10 + kind;
         const float *Q = sQ + v * NP * 7;
         sl.SD[e * 50 + o] = ne_final_sum<NP>(a, kind, [&](int kk, int src) { return Q[kk * 7 + src]; });
     }
