@@ -639,7 +639,7 @@ def _ensemble(pkg, torch, args):
 # (409.9 MB per launch at 32^3, 57.9 B per node.)
 TRAFFIC_BYTES_PER_LAUNCH = 3278921728
 TRAFFIC_SOURCES = ("paper_1609_00098_gb300/csrc/dg_ne_mixed.cuh", "paper_1609_00098_gb300/csrc/dg_internal.h")
-TRAFFIC_SOURCES_SHA256 = "8cec47e4fae4094513930e004c75bec0f3df0de87be92bb1d5427d3d04c72a50"
+TRAFFIC_SOURCES_SHA256 = "928009d63844bea80667eac0b920880fcf0f00e65b95e5a8b361ac589a65d41d"
 
 
 def _traffic():

@@ -23,15 +23,19 @@
 // Summaries of U^s = U^n + D are S(U^n) + S(D): S(U^n) is formed once per step by
 // stage 1 from U^n shifted by a per-element reference, as double-float (compensated
 // FP32) sums where the limiter's face tests need them (mean and face means), the
-// reference added in FP64; S(D) in FP32.  The limiter's decisions are then taken in
-// FP64 on those summaries.
+// reference added in FP64; S(D) in FP32.  The limiter's face tests are then taken
+// in FP64 on those summaries, its slope candidates from FP64 differences rounded to
+// FP32 (the precision the replacement stores).
 //
 // Work split of k_ne_stage: one thread per x-line (j, k) of an element, NP nodes;
-// a CTA holds NeShape<NP>::EPB consecutive elements.  The x derivative is taken in
-// registers with D as compile-time-indexed kernel parameters (constant operands);
-// the y and z derivatives read fluxes of other threads' lines from shared memory.
-// Face points are split evenly: at its face position (j, k) a thread takes one
-// point of every (axis, side), the neighbours' traces staged first so that the
+// a CTA holds NeShape<NP>::EPB consecutive elements.  For even NP each element's
+// U^n (and in stages 2 and 3 its difference and replacement parameters, and its
+// neighbours' replacement parameters) arrive in shared memory by bulk asynchronous
+// copies issued at the start of the kernel, on a transaction barrier per element.
+// The x derivative is taken in registers (node pairs in paired FP32 FMAs for even
+// NP); the y and z derivatives read fluxes of other threads' lines from shared
+// memory.  Face points are split evenly: at its face position (j, k) a thread takes
+// one point of every (axis, side), the neighbours' traces staged first so that the
 // flux phase runs without divergence.
 #pragma once
 
