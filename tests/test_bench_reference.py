@@ -33,3 +33,26 @@ def test_reference_arm_json_line():
 
 def test_timing_rules_on_the_command_line():
     assert _run("--impl", "reference", "--steps", "1", "--warmup", "2").returncode == 2
+
+
+def test_captured_counters_follow_the_kernel_sources(monkeypatch):
+    """The DRAM traffic and the SR stage kernel's flop counts come from ncu captures
+    of the committed kernels; they are reported only while the kernels' sources
+    hash as they did at capture, and dropped (null) once a source changes."""
+    assert bench._traffic() == bench.TRAFFIC_BYTES_PER_LAUNCH
+    roof = bench._alu_roofline(0.2)
+    assert roof["bound"] == "alu" and roof["fp64"]["flops_per_launch"] == bench.SR_STAGE_FLOPS["fp64"]
+    assert abs(roof["frac"] - bench.SR_STAGE_FLOPS["fp64"] / 0.2e-3 / 1e12 / bench.FP64_PEAK_TFLOPS) < 1e-12
+    monkeypatch.setattr(bench, "TRAFFIC_SOURCES_SHA256", "0" * 64)
+    monkeypatch.setattr(bench, "SR_STAGE_SOURCES_SHA256", "0" * 64)
+    assert bench._traffic() is None
+    assert bench._alu_roofline(0.2)["achieved"] is None
+
+
+def test_roofline_arithmetic():
+    """64 B per dof-update in the FP64-state model: 320 B per node-step, a mean of
+    106.7 B per node and stage launch; the ensemble's HBM fraction is those bytes
+    over the step time against the measured peak."""
+    assert abs(bench.FP64_STATE_BYTES_PER_NODE_STAGE * 3 - 320.0) < 1e-12
+    r = bench._ensemble_roofline(1_000_000, 1.0)
+    assert abs(r["achieved"] - 320.0) < 1e-9 and abs(r["frac"] - 320.0 / r["peak"]) < 1e-12
