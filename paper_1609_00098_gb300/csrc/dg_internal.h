@@ -11,13 +11,27 @@ constexpr int MAXN = 8;  // largest LGL node count per axis
 
 __host__ __device__ constexpr int round_up32(int v) { return (v + 31) / 32 * 32; }
 
+// element coordinates of e (32-bit divisions while e fits, which 64-bit division
+// on the GPU, a long software sequence, is not needed for)
+__host__ __device__ inline void elem_coords(long long e, const int K[3], int ec[3])
+{
+    if (e <= 0x7fffffffLL) {
+        const int ei = (int)e, q = ei / K[0];
+        ec[0] = ei - q * K[0];
+        ec[2] = q / K[1];
+        ec[1] = q - ec[2] * K[1];
+    } else {
+        ec[0] = (int)(e % K[0]);
+        ec[1] = (int)((e / K[0]) % K[1]);
+        ec[2] = (int)(e / ((long long)K[0] * K[1]));
+    }
+}
+
 // periodic neighbour of element e along axis a in direction s = +-1
 __host__ __device__ inline long long elem_neighbour(long long e, const int K[3], int a, int s)
 {
     int ec[3];
-    ec[0] = (int)(e % K[0]);
-    ec[1] = (int)((e / K[0]) % K[1]);
-    ec[2] = (int)(e / ((long long)K[0] * K[1]));
+    elem_coords(e, K, ec);
     ec[a] = (ec[a] + s + K[a]) % K[a];
     return ec[0] + (long long)K[0] * (ec[1] + (long long)K[1] * ec[2]);
 }
@@ -39,9 +53,7 @@ struct Ghosts {
 __host__ __device__ inline long long elem_neighbour_bc(long long e, const int K[3], int a, int s, const Ghosts &G)
 {
     int ec[3];
-    ec[0] = (int)(e % K[0]);
-    ec[1] = (int)((e / K[0]) % K[1]);
-    ec[2] = (int)(e / ((long long)K[0] * K[1]));
+    elem_coords(e, K, ec);
     const int c = ec[a] + s;
     if (((G.mask >> a) & 1) && (c < 0 || c >= K[a])) {
         const int b = (a + 1) % 3, d = (a + 2) % 3;
