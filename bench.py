@@ -407,7 +407,7 @@ SR_STAGE_PIPES = {"fp64_pipe_pct": 35.2, "fma_pipe_pct": 13.9, "alu_pipe_pct": 2
                   "issue_active_pct": 40.8}
 SR_STAGE_SOURCES = ("paper_1609_00098_gb300/csrc/dg_mixed.cuh", "paper_1609_00098_gb300/csrc/dg_physics.cuh",
                     "paper_1609_00098_gb300/csrc/dg_c2p_net.cuh", "paper_1609_00098_gb300/csrc/dg_internal.h")
-SR_STAGE_SOURCES_SHA256 = "7be83b600abe32cecc03612f7194d9fd7c3ccdec0bdf6b83044c9607c9c458d7"
+SR_STAGE_SOURCES_SHA256 = "8d675640bc064200bd0ad8de38aa766def3ba352f8d371be08a4ad4bbbc41120"
 # FMA throughput of this GPU (independent dependent-FMA chains, every SM busy;
 # flops count an FMA as two): FP64 1.20 TFLOP/s, FP32 75.0 TFLOP/s.
 FP64_PEAK_TFLOPS = 1.20
@@ -637,9 +637,9 @@ def _ensemble(pkg, torch, args):
 # 32^3-element case of the same problem scaled by the node count (64^3 / 32^3 = 8).
 # Reported only while the kernel's sources still hash to their state at capture.
 # (409.9 MB per launch at 32^3, 57.9 B per node.)
-TRAFFIC_BYTES_PER_LAUNCH = 3278921728
+TRAFFIC_BYTES_PER_LAUNCH = 3279075328
 TRAFFIC_SOURCES = ("paper_1609_00098_gb300/csrc/dg_ne_mixed.cuh", "paper_1609_00098_gb300/csrc/dg_internal.h")
-TRAFFIC_SOURCES_SHA256 = "928009d63844bea80667eac0b920880fcf0f00e65b95e5a8b361ac589a65d41d"
+TRAFFIC_SOURCES_SHA256 = "42857d56f61128c660a25c5d395e9ac4a28b16bd9045e88fc35285650472e399"
 
 
 def _traffic():
