@@ -501,7 +501,15 @@ def _sr_blast(pkg, torch, args):
                     "ms_per_step_with_kernel_events": sum(pms) / steps,
                     "kernels": _kern(prof), "device_status": m.sync_status()}
         if key == "mixed_learned":
-            out["alu_roofline"] = _alu_roofline(prof["stage"][0] / prof["stage"][1])
+            roof = _alu_roofline(prof["stage"][0] / prof["stage"][1])
+            # the event nodes stretch these short launches: the same launch time scaled
+            # to the step time measured without them
+            scaled = prof["stage"][0] / prof["stage"][1] * (sum(ms) / sum(pms))
+            roof["avg_launch_ms_scaled_to_plain_step"] = scaled
+            if roof.get("fp64"):
+                roof["fp64"]["frac_scaled"] = roof["fp64"]["frac"] * roof["avg_launch_ms"] / scaled
+                roof["fp32"]["frac_scaled"] = roof["fp32"]["frac"] * roof["avg_launch_ms"] / scaled
+            out["alu_roofline"] = roof
         m.close()
     acc = {}
     for name, use_net in (("learned", net), ("warm_start", None)):
