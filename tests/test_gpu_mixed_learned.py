@@ -1,5 +1,5 @@
 """Mixed-precision path with the learned con2prim starting guess computed inside
-the stage kernel (dg_mesh_set_c2p_net).  Newton stays the judge, so the same
+the stage kernel (dg_mesh_set_c2p_net).  Newton still decides the result, so the same
 bars as the warm-started mixed path hold: within 1e-6 relative L2 (per conserved
 variable, norm floored at 1 % of the largest) of the FP64 oracle after 10 blast
 steps, for a trained network and for an untrained one."""
