@@ -334,6 +334,23 @@ def test_mixed_roe(pkg):
     assert np.all(d <= 1e-6), d
 
 
+def test_mixed_ab3_newtonian(pkg):
+    """Adams-Bashforth on a mixed Newtonian mesh: the right-hand side of the
+    difference-form kernel (dg_rhs) and its start-up steps (two SSP-RK3 steps in
+    difference form), the combination in FP64; ten shear-layer steps within the
+    1e-6 bar of the oracle's AB3 (Sec. 3.4)."""
+    om, gm = _pair(pkg, 0, (4, 3, 3), 6, 1, 1, lo=(-0.5,) * 3, hi=(0.5,) * 3, gamma=5 / 3)
+    U = om.from_prim(di.kh_ne(om.coords(), seed=2))
+    dt = 0.5 * om.cfl_dt(U, 0.2)
+    Uo = om.ab3_run(U, 10, dt)
+    Ug = _gpu(U)
+    for _ in range(10):
+        gm.ab3_step(Ug, dt)
+    assert gm.sync_status() == 0
+    d = _rel_l2(om, Ug.cpu().numpy(), Uo)
+    assert np.all(d <= 1e-6), d
+
+
 def test_mixed_ab3(pkg):
     """Adams-Bashforth on a mixed mesh (mixed right-hand side, FP64 combination):
     ten blast steps within the 1e-6 bar of the oracle's AB3."""
