@@ -870,8 +870,8 @@ __global__ void __launch_bounds__(NeShape<NP>::THREADS, NeShape<NP>::MINB) k_ne_
             for (int v = 0; v < 5; ++v) sH[(m * L + ln) * 5 + v] = w[v];
         }
     }
-
-    __syncthreads();
+    // (no barrier: each thread reads back only its own halo entries, and the face
+    // fluxes write only lifts that are read after the next barrier)
 
     // ---- face fluxes at the thread's six face points.  x-face lifts belong to the
     // thread's own line and stay in registers; y and z lifts go to sL for the lines
