@@ -16,7 +16,7 @@ library is measured on):
   * ``blast_sr``: spherical relativistic blast, rho=10, p=13.33 for r<0.3 else
     rho=1, p=1e-6, v=0, with 1% seeded density noise;
   * ``kh_ne``: Kelvin-Helmholtz shear layer, Newtonian;
-  * ``isentropic_vortex``: eq:isen_vortex (Sec. 6.3.1), Newtonian, at any t;
+  * ``isentropic_vortex``: eq:isen_vortex (Sec. 6.2.1), Newtonian, at any t;
   * ``riemann_1d``: the Riemann problems of tab:Riemann_Problems (Sec. 6.1);
   * ``c2p_samples``: random primitive states for con2prim;
   * ``ensemble_recipe``: the (system, K, n) list of a ragged ensemble.

@@ -100,7 +100,7 @@ def newtonian_sample(x, t, rl, ul, pl, rr, ur, pr, g, xd=0.0):
 
 # ---------------------------------------------------------------------------
 # Special-relativistic ideal gas, flow normal to the discontinuity (no tangential
-# velocity), as in the shock tubes of tab:Riemann_Problems (Sec. 6.2.1).  Units
+# velocity), as in the shock tubes of tab:Riemann_Problems (Sec. 6.1.3).  Units
 # with c = 1; h = 1 + g p / ((g - 1) rho), c_s^2 = g p / (rho h), W = 1/sqrt(1 - v^2).
 #
 # Rarefaction: the flow is isentropic (p = K rho^g) and, across a fan facing

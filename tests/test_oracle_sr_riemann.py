@@ -1,11 +1,11 @@
 """Pins of the special-relativistic exact Riemann solver (oracle/exact_riemann.py)
 and, through it, of the oracle's SR shock path on the paper's shock tubes
-(tab:Riemann_Problems, Sec. 6.2.1, tab:RE_sod).
+(tab:Riemann_Problems, Sec. 6.1.3, tab:RE_sod).
 
 The solver is checked against the physics, not against itself: the shock states
 satisfy the relativistic Rankine-Hugoniot conditions, the whole solution (fans
 included) satisfies the integral conservation law, the Newtonian limit agrees
-with the Newtonian exact solver, and the wave data match what Sec. 6.2.1 states
+with the Newtonian exact solver, and the wave data match what Sec. 6.1.3 states
 about the two shock tubes."""
 import math
 
@@ -117,7 +117,7 @@ def test_sr_newtonian_limit():
 
 
 def test_sr_shock_tubes_match_the_papers_description():
-    """Sec. 6.2.1: in shock tube 1 the flow reaches a mildly relativistic speed of
+    """Sec. 6.1.3: in shock tube 1 the flow reaches a mildly relativistic speed of
     about 0.7; in shock tube 2 the shock moves at about 0.986 (a Lorentz factor of
     about 6) and the dense shell between contact and shock is about 0.01 wide at
     t = 0.4."""

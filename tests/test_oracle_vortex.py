@@ -1,5 +1,5 @@
 """Pins of the oracle's analytic outer boundaries (exterior states from an exact
-solution, Sec. 3.4) with the isentropic vortex of eq:isen_vortex (Sec. 6.3.1):
+solution, Sec. 3.4) with the isentropic vortex of eq:isen_vortex (Sec. 6.2.1):
 the problem data satisfy the Euler equations, the paper's error table
 (tab:IsenVortexConvergence) is reproduced, SSP-RK3 keeps third order in time with
 time-dependent exterior states (stage times t, t + dt, t + dt/2), and a uniform
